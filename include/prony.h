@@ -1,0 +1,159 @@
+/*
+ * prony.h -- C ABI of the GB300 (sm_103a) multivariate matrix-pencil Prony library.
+ *
+ * Method: N. Bosner, "Parallel Prony's method with multivariate matrix pencil
+ * approach and its numerical aspect", arXiv 2012.11430.  The problem (Section 1,
+ * Eq. 1): given samples of the exponential sum
+ *     f(k) = sum_{j=1}^m c_j exp(-2 pi i <t_j, k>),   k in Z^d,
+ * recover the nodes t_j in [0,1)^d and the coefficients c_j != 0.  The library
+ * runs Algorithm 1 with the block power method for the SVD (Algorithm 3) on
+ * the GPU: Toeplitz products T V, T^* U (T = [f(k-h)], k,h in I_n={0..n}^d),
+ * S_l = U^* T_l V Sigma^{-1} (Eq. generateSl), the joint diagonalisation of a
+ * random combination C_mu (Eq. diagonalizeSl), t from the principal logarithm,
+ * and c from the Vandermonde least-squares problem (Eq. ls_probl).
+ *
+ * Conventions for every call:
+ *   - Sample grid: complex128 values on {-n..n+1}^d, (2n+2)^d entries, row-major
+ *     (last coordinate fastest); point x is at linear index
+ *     sum_l (x_l + n) (2n+2)^(d-1-l).  Every matrix entry the method needs,
+ *     f(k-h) and f(k-h+e_l) for k,h in I_n, lies on this grid.
+ *   - Host-pointer calls are synchronous; the library copies inputs to the
+ *     device and results back.  `*_dev` calls take device pointers and a CUDA
+ *     stream (cudaStream_t passed as void*) and return when the results are
+ *     written (they synchronise that stream).
+ *   - All buffers are owned by the caller.  The context owns its device
+ *     workspace (grown on demand and reused), its stream and its caches.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Return value: a prony_status.  Per-problem outcomes are in prony_info.
+ *     PRONY_ERANK (detected rank below m) still fills every output.
+ *   - No call ever aborts the process, traps on the GPU or falls back to a CPU
+ *     implementation; every device loop is bounded and reports PRONY_ENOCONV.
+ */
+#ifndef PRONY_H
+#define PRONY_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } prony_c128;     /* interleaved complex128 */
+typedef struct prony_ctx prony_ctx;
+
+typedef enum {
+  PRONY_OK = 0,
+  PRONY_EINVAL = -1,    /* bad argument (sizes, NULL pointer, unsupported precision) */
+  PRONY_ERANK = -2,     /* detected numerical rank of T is below m (outputs still filled) */
+  PRONY_ENOCONV = -3,   /* an iteration hit its cap (power method, eigen-QR, Jacobi) */
+  PRONY_ENAN = -4,      /* non-finite input samples or intermediate results */
+  PRONY_ECUDA = -5,     /* CUDA runtime error (message: prony_last_error) */
+  PRONY_ENOMEM = -6     /* device allocation failed */
+} prony_status;
+
+/* Arithmetic of the Toeplitz block products (the small steps are FP64 always).
+ *   PRONY_FP32   : complex64 operands, FP32 FMA on the CUDA cores.
+ *   PRONY_BF16X3 : FP32 operands split into three BF16 parts, six tensor-core
+ *                  products (tcgen05.mma kind::f16), FP32 accumulation.
+ *   PRONY_TF32X3 : FP32 operands split into TF32 hi+lo, three tensor-core
+ *                  products (tcgen05.mma kind::tf32), FP32 accumulation.
+ *   PRONY_BF16X2 : BF16 hi+lo split, three tensor-core products. */
+typedef enum { PRONY_FP32 = 0, PRONY_BF16X3 = 1, PRONY_TF32X3 = 2, PRONY_BF16X2 = 3 } prony_precision;
+
+typedef struct {
+  int precision;            /* prony_precision */
+  int oversample_p;         /* r0 = m + p columns in Algorithm 3; < 0: p = m (Section 5) */
+  double tol_rank;          /* rank tolerance of the pivoted QR (Section 2.2); <= 0: default */
+  double tol_power;         /* stop when ||R_k||_F <= tol_power ||T||_F (Algorithm 3); <= 0: default */
+  int max_iter;             /* cap on power iterations; <= 0: default 30 */
+  unsigned long long seed;  /* Philox4x64-10 key for mu, V_0 */
+  int rank_mode;            /* 0: use the given m (rank detected and reported); 1: use the detected rank */
+} prony_opts;
+
+typedef struct {
+  int status;               /* prony_status of this problem */
+  int rank_detected;        /* rank from the pivoted QR of the first T^* U block (Section 2.2) */
+  int rank_used;            /* number of terms returned (m, or the detected rank with rank_mode 1) */
+  int power_iters;          /* iterations k of Algorithm 3 */
+  double power_resid;       /* ||R_k||_F / ||T||_F at exit */
+  double ls_resid;          /* ||A^T c - f||_2 / ||f||_2 (Section 5 accuracy estimate) */
+  double sigma_ratio;       /* sigma_m / sigma_1 */
+  double normT;             /* ||T||_F (closed form from the grid) */
+} prony_info;
+
+/* Fill *opts with defaults (PRONY_BF16X3 if the tensor-core path is built, p = m). */
+void prony_default_opts(prony_opts* opts);
+const char* prony_status_string(int status);
+/* Message of the last PRONY_ECUDA / PRONY_ENOMEM on this host thread. */
+const char* prony_last_error(void);
+
+/* Create a context on CUDA device `device` (its own non-blocking stream). */
+int prony_ctx_create(prony_ctx** ctx, int device);
+int prony_ctx_destroy(prony_ctx* ctx);
+
+/* Algorithm 1 for one problem.  samples: (2n+2)^d grid (see above).  d >= 1,
+ * n >= 1, 1 <= m <= (n+1)^d, m <= 64.  opts may be NULL (defaults).
+ * Outputs: t_out[m*d] (row j = t_j, components in [0,1)), c_out[m]; the pairs
+ * are sorted lexicographically by t.  info may be NULL. */
+int prony_solve(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m,
+                const prony_opts* opts, double* t_out, prony_c128* c_out, prony_info* info);
+
+/* Steps 1-3 of Algorithm 1: the d matrices S_l = U^* T_l V Sigma^{-1} (Eq. generateSl)
+ * in the phase-canonical basis (each singular pair u_i, v_i multiplied by
+ * e^{-i theta_i}, theta_i = arg of the largest-modulus entry of v_i, lowest
+ * index on ties).  S_out[d*m*m]: S_l row-major at offset l*m*m.
+ * sigma_out[m]: leading singular values, descending.  U_out, V_out (nullable):
+ * N x m column-major singular vectors in the same basis. */
+int prony_build_S(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m,
+                  const prony_opts* opts, prony_c128* S_out, double* sigma_out,
+                  prony_c128* U_out, prony_c128* V_out, prony_info* info);
+
+/* Eq. 1 at K integer points: f_out[q] = sum_j c_j exp(-2 pi i <t_j, k_q>).
+ * t[m*d] row-major, c[m], k[K*d] row-major.  Phases reduced in FP64. */
+int prony_eval(prony_ctx* ctx, const double* t, const prony_c128* c, int m, int d,
+               const int* k, int K, prony_c128* f_out);
+
+/* Many independent problems of uneven (d, n, m) (same d for all in this version).
+ * sample_off[p]: offset (in prony_c128) of problem p's grid inside `samples`;
+ * out_off[p]: offset (in terms) of its results: t_out[(out_off[p]+j)*d + l],
+ * c_out[out_off[p]+j].  infos[P] nullable.  Returns the worst status. */
+int prony_solve_batched(prony_ctx* ctx, int P, const int* d, const int* n, const int* m,
+                        const long long* sample_off, const prony_c128* samples,
+                        const long long* out_off, double* t_out, prony_c128* c_out,
+                        prony_info* infos, const prony_opts* opts);
+
+/* Device-pointer twin of prony_solve_batched: samples, t_out, c_out are device
+ * pointers; d, n, m, sample_off, out_off, infos are host arrays. */
+int prony_solve_batched_dev(prony_ctx* ctx, int P, const int* d, const int* n, const int* m,
+                            const long long* sample_off, const prony_c128* samples_dev,
+                            const long long* out_off, double* t_out_dev, prony_c128* c_out_dev,
+                            prony_info* infos, const prony_opts* opts, void* stream);
+
+/* Exponential-sum forward on device data (single precision results, FP64 phases):
+ * f[q] = sum_j c_j exp(-2 pi i <t_j, k_q>) for the integer points of the box
+ * {lo_l .. lo_l + len_l - 1}, row-major.  t_dev: m*d float64, c_dev: m complex64
+ * (float2), f_dev: prod(len) complex64.  (Section 1, Eq. 1.) */
+int prony_expsum_fwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev, int m, int d,
+                         const int* lo, const int* len, void* f_dev, void* stream);
+
+/* Vector-Jacobian product of the exponential sum over the same box: given
+ * g = dL/d(conj f) as complex64 (L real; for L = sum |f - y|^2, g = f - y),
+ * writes grad_t[m*d] (float64) = dL/dt and grad_c[m] (complex64) =
+ * dL/dRe c + i dL/dIm c.  The exponentials are recomputed, not stored. */
+int prony_expsum_bwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev, int m, int d,
+                         const int* lo, const int* len, const void* g_dev,
+                         double* grad_t_dev, void* grad_c_dev, void* stream);
+
+/* The Toeplitz block product used by the power iterations, exposed for testing:
+ * Y[k, j] = sum_{h in I_n} F(k - h) X[h, j] for k in the box {0..L-1}^d
+ * (L = n+1: T X; L = n+2: the rows of T, T_1..T_d at once), where F = f
+ * (adjoint = 0) or F(x) = conj f(-x) (adjoint = 1, i.e. T^* X).
+ * grid_dev: (2n+2)^d complex128 samples; X_dev: N x r complex64 column-major
+ * (N = (n+1)^d, leading dimension N); Y_dev: L^d x r complex64 column-major
+ * (leading dimension L^d).  precision: prony_precision. */
+int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int n,
+                          const void* X_dev, int r, int L, int adjoint, int precision,
+                          void* Y_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRONY_H */

@@ -1,0 +1,229 @@
+// Shared definitions of the Prony CUDA library (device side and launchers).
+//
+// Layout in HBM (one workspace per context, grown on demand; all problems of a
+// batch side by side, offsets in ProbDesc):
+//   grid64  complex128 samples of every problem, (2n+2)^d each (input copy)
+//   gF, gH  complex64 copies of F(x) = f(x) and F(x) = conj f(-x) on the same
+//           grid (the Toeplitz functions of T and T^*), (2n+2)^d each
+//   V, U, B1, B2   N x r0 complex64, column-major, leading dimension N
+//   Y       (n+2)^d x r0 complex64 column-major: rows of T V over the box
+//           {0..n+1}^d, which holds T V (rows k in I_n) and every T_l V
+//           (rows k + e_l) of Eq. generateSl at once
+//   small   per-problem FP64 / FP32 workspace for the r0 x r0 and m x m steps
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PRONY_RMAX 128        // max columns r0 = m + p
+#define PRONY_MMAX 64         // max terms m
+#define PRONY_DMAX 4          // max dimension d
+
+struct ProbDesc {
+  int d, n, m, r0;            // dimension, grid size, terms, power-method width
+  int N, Next, G, Gd;         // (n+1)^d, (n+2)^d, 2n+2, (2n+2)^d
+  long long grid;             // offset (elements) of the problem's grid in grid64 / gF / gH
+  long long xoff;             // offset (elements) of its N x r0 blocks in the X buffers
+  long long yoff;             // offset (elements) of its Next x r0 block in Y
+  long long soff;             // offset (bytes) of its small workspace
+  long long ooff;             // offset (terms) of its results in the packed t / c outputs
+};
+
+// Per-problem iteration state, device resident.
+struct ProbState {
+  int wu, wv;                 // current widths of U and V
+  int w_in, w_out;            // widths of the pending X -> X M product (set by the Cholesky step)
+  int iter;                   // power iterations done
+  int done;                   // 1: stopped, later iterations skip this problem
+  int status;                 // prony_status
+  int rank_det;               // detected rank (pivoted QR of the first T^* U)
+  int rank_used;
+  int nonfinite;
+  double normT2;              // ||T||_F^2 (closed form)
+  double normf2;              // ||f||_2^2 over I_n
+  double resid2;              // ||R_k||_F^2
+  double resid2_prev;
+  double ls_num2;             // ||A^T c - f||^2
+  double sigma_ratio;
+};
+
+// Small per-problem workspace: byte offsets inside the block at ProbDesc::soff.
+// LDR >= every r0 of the batch, LDM >= every m (leading dimensions of the blocks).
+struct SmallLay {
+  int LDR, LDM;
+  long long gram;    // LDR x LDR double2  Gram of a tall block
+  long long mapm;    // LDR x LDR float2   P R^{-1} of the last Cholesky step
+  long long q;       // LDR x LDM double2  Q = U^* T V
+  long long mproj;   // d x LDR x LDM double2  U^* T_l V
+  long long uq;      // LDR x LDM double2  left singular vectors of Q
+  long long vq;      // LDM x LDM double2  right singular vectors of Q
+  long long sigma;   // LDM double
+  long long S;       // d x LDM x LDM double2
+  long long t;       // LDM x DMAX double
+  long long rhs;     // LDM double2
+  long long c;       // LDM double2
+  long long phase;   // LDM double2
+  long long argmx;   // LDM u64
+  long long bytes;
+};
+
+inline SmallLay make_small_lay(int LDR, int LDM, int dmax) {
+  SmallLay L;
+  L.LDR = LDR;
+  L.LDM = LDM;
+  long long o = 0;
+  auto take = [&](long long b) { long long r = o; o += (b + 15) / 16 * 16; return r; };
+  L.gram = take(16LL * LDR * LDR);
+  L.mapm = take(8LL * LDR * LDR);
+  L.q = take(16LL * LDR * LDM);
+  L.mproj = take(16LL * dmax * LDR * LDM);
+  L.uq = take(16LL * LDR * LDM);
+  L.vq = take(16LL * LDM * LDM);
+  L.sigma = take(8LL * LDM);
+  L.S = take(16LL * dmax * LDM * LDM);
+  L.t = take(8LL * LDM * PRONY_DMAX);
+  L.rhs = take(16LL * LDM);
+  L.c = take(16LL * LDM);
+  L.phase = take(16LL * LDM);
+  L.argmx = take(8LL * LDM);
+  L.bytes = (o + 255) / 256 * 256;
+  return L;
+}
+
+// Every device pointer a kernel may need, passed by value.
+struct Dev {
+  const ProbDesc* P;
+  ProbState* st;
+  int nprob;
+  int maxN, maxNext, maxGd, maxR0, maxM, maxD;
+  const double2* grid64;
+  float2* gF;
+  float2* gH;
+  float2* V;
+  float2* U;
+  float2* B1;
+  float2* B2;
+  float2* Y;
+  char* small;
+  SmallLay L;
+};
+
+// ----------------------------------------------------------------------------- complex helpers
+__host__ __device__ inline float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ inline double cabsd(double2 a) { return hypot(a.x, a.y); }
+__device__ inline double2 cdiv(double2 a, double2 b) {  // Smith's algorithm
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, den = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  }
+  double r = b.x / b.y, den = b.x * r + b.y;
+  return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+}
+__device__ inline double2 csqrtd(double2 a) {
+  double r = hypot(a.x, a.y);
+  if (r == 0.0) return make_double2(0.0, 0.0);
+  double sx = sqrt(0.5 * (r + fabs(a.x)));
+  if (a.x >= 0.0) return make_double2(sx, a.y / (2.0 * sx));
+  return make_double2(fabs(a.y) / (2.0 * sx), a.y >= 0.0 ? sx : -sx);
+}
+
+// ----------------------------------------------------------------------------- index maps
+// Row r of I_n (row-major, (n+1)^d rows) -> row of the box {0..L-1}^d after adding
+// the unit vector e_shift (shift < 0: none).
+__device__ inline int map_row(int r, int n, int d, int L, int shift) {
+  int idx = 0, mul = 1, rem = r;
+  for (int l = d - 1; l >= 0; --l) {
+    int k = rem % (n + 1);
+    rem /= (n + 1);
+    if (l == shift) k += 1;
+    idx += k * mul;
+    mul *= L;
+  }
+  return idx;
+}
+
+// ----------------------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror, Shaw (SC'11).  Draw convention: key = (seed, stream),
+// counter = (index, 0, 0, 0); u = ((w >> 11) + 0.5) 2^-53; complex normal
+// z = sqrt(-log u0) exp(2 pi i u1).
+#define PRONY_STREAM_MU 0x4D55ull
+#define PRONY_STREAM_V0 0x5630ull
+__host__ __device__ inline void philox4x64(uint64_t ctr[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+    uint64_t hi0 = __umul64hi(M0, ctr[0]), lo0 = M0 * ctr[0];
+    uint64_t hi1 = __umul64hi(M1, ctr[2]), lo1 = M1 * ctr[2];
+#else
+    unsigned __int128 p0 = (unsigned __int128)M0 * ctr[0], p1 = (unsigned __int128)M1 * ctr[2];
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0, hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+#endif
+    uint64_t c0 = hi1 ^ ctr[1] ^ k0, c2 = hi0 ^ ctr[3] ^ k1;
+    ctr[0] = c0; ctr[1] = lo1; ctr[2] = c2; ctr[3] = lo0;
+    k0 += W0; k1 += W1;
+  }
+}
+__host__ __device__ inline double philox_u01(uint64_t w) { return ((double)(w >> 11) + 0.5) * 1.1102230246251565e-16; }
+
+// t in [0,1) as a 64-bit binary fraction: <t, k> mod 1 is then exact integer arithmetic.
+__device__ inline uint64_t frac64(double t) {
+  double f = t - floor(t);
+  // f * 2^64, split to keep all 53 bits
+  uint64_t hi = (uint64_t)(f * 4294967296.0);
+  double rem = f * 4294967296.0 - (double)hi;
+  uint64_t lo = (uint64_t)(rem * 4294967296.0);
+  return (hi << 32) + lo;
+}
+
+// ----------------------------------------------------------------------------- launchers
+enum WidthSel { W_R0 = 0, W_U = 1, W_V = 2, W_M = 3, W_IN = 4, W_OUT = 5 };
+enum BufSel { BUF_V = 0, BUF_U = 1, BUF_B1 = 2, BUF_B2 = 3, BUF_Y = 4 };
+
+// kernels_tall.cu
+void launch_prep(const Dev& D, cudaStream_t s);
+void launch_init_v0(const Dev& D, unsigned long long seed, cudaStream_t s);
+void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_t s);
+// out[a][b] (+)= sum_{r in I_n} conj(X[map(r), a]) Z[map(r), b]; X, Z buffers with row shifts
+void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
+                 long long out_off, int out_ld, cudaStream_t s);
+// OUT[r, j] = sum_a X[r, a] M[a][j] - (zbuf >= 0 ? Z[r, j] : 0) for r in I_n; M in the small workspace
+// (float2 at mapm, ld RMAX) or double2 (m_double, at m_off with ld MMAX).  norm_only: accumulate
+// ||OUT||^2 into st.resid2 and do not store.
+void launch_apply(const Dev& D, int xbuf, int xw, int outw, long long m_off, int m_double, int zbuf,
+                  int outbuf, int norm_only, cudaStream_t s);
+void launch_argmax(const Dev& D, int buf, cudaStream_t s);
+void launch_rhs(const Dev& D, int resid, cudaStream_t s);
+void launch_gather_out(const Dev& D, double* t_out, double2* c_out, cudaStream_t s);
+void launch_copy_cols(const Dev& D, int buf, int w_sel, double2* out, cudaStream_t s);
+void launch_expsum_fwd(const double* t, const float2* c, int m, int d, const int* lo, const int* len,
+                       long long K, float2* f, cudaStream_t s);
+void launch_expsum_bwd(const double* t, const float2* c, int m, int d, const int* lo, const int* len,
+                       long long K, const float2* g, double* acc, cudaStream_t s);
+void launch_expsum_bwd_finish(const double* acc, int m, int d, double* gt, float2* gc, cudaStream_t s);
+void launch_eval_points(const double* t, const double2* c, int m, int d, const int* k, int K, double2* f,
+                        cudaStream_t s);
+
+// kernels_toeplitz.cu
+struct ToeplitzJob { int prob, mt, ks, nks; };
+void launch_zero_buf(const Dev& D, int buf, int wsel, int y_ext, cudaStream_t s);
+void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int xbuf, int wsel,
+                     int ybuf, int y_ext, int maxw, int precision, cudaStream_t s);
+
+// kernels_small.cu
+enum QrMode { QR_PLAIN = 0, QR_DROP = 1, QR_RANK = 2 };
+void launch_chol(const Dev& D, int wsel, int target, int mode, double tol, int rank_mode, cudaStream_t s);
+void launch_svd_S(const Dev& D, cudaStream_t s);
+void launch_canon(const Dev& D, cudaStream_t s);
+void launch_eig_t(const Dev& D, unsigned long long seed, cudaStream_t s);
+void launch_solve_c(const Dev& D, cudaStream_t s);
+void launch_check(const Dev& D, double tol_power, int max_iter, int* all_done, cudaStream_t s);
+void launch_reset_done(const Dev& D, cudaStream_t s);

@@ -1,0 +1,616 @@
+// Data-parallel kernels over the rows of one or many problems: grid preparation,
+// Philox starting block, tall-skinny Gram and products of the block power method
+// (Algorithm 3), the Vandermonde right-hand side conj(A) f and the LS residual
+// (Eq. ls_probl), and the exponential sum of Eq. 1 with its vector-Jacobian product.
+#include "common.cuh"
+
+namespace {
+
+__device__ inline const ProbDesc& prob(const Dev& D, int p) { return D.P[p]; }
+
+__device__ inline float2* buf_base(const Dev& D, int buf, const ProbDesc& p, int& ld) {
+  switch (buf) {
+    case BUF_V: ld = p.N; return D.V + p.xoff;
+    case BUF_U: ld = p.N; return D.U + p.xoff;
+    case BUF_B1: ld = p.N; return D.B1 + p.xoff;
+    case BUF_B2: ld = p.N; return D.B2 + p.xoff;
+    default: ld = p.Next; return D.Y + p.yoff;
+  }
+}
+
+__device__ inline int width_of(const ProbState& s, const ProbDesc& p, int sel) {
+  switch (sel) {
+    case W_R0: return p.r0;
+    case W_U: return s.wu;
+    case W_V: return s.wv;
+    case W_M: return p.m;
+    case W_IN: return s.w_in;
+    default: return s.w_out;
+  }
+}
+
+// Row of buffer `buf` holding row r of I_n (Y is laid out over the box {0..n+1}^d).
+__device__ inline int buf_row(int buf, const ProbDesc& p, int r, int shift) {
+  return buf == BUF_Y ? map_row(r, p.n, p.d, p.n + 2, shift) : r;
+}
+
+template <typename T>
+__device__ inline T block_sum(T v, T* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (threadIdx.x < 32) {
+    r = (l < (int)(blockDim.x >> 5)) ? sh[l] : (T)0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// ----------------------------------------------------------------------------- grid prep
+__global__ void k_state_init(Dev D) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= D.nprob) return;
+  ProbState s = {};
+  s.wu = D.P[p].r0;
+  s.wv = D.P[p].r0;
+  s.rank_det = -1;
+  s.rank_used = D.P[p].m;
+  s.resid2_prev = -1.0;
+  D.st[p] = s;
+}
+
+// gF = f, gH(x) = conj f(-x) (zero where -x leaves the grid); ||T||_F^2 by the
+// multiplicity of each difference (prod_l (n+1-|x_l|)), ||f||^2 over I_n, finiteness.
+__global__ void k_prep(Dev D) {
+  __shared__ double sh[32];
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  double accT = 0.0, accF = 0.0;
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.Gd; i += gridDim.x * blockDim.x) {
+    int rem = i, mir = 0, mul = 1;
+    double w = 1.0;
+    bool inT = true, inI = true, mvalid = true;
+    for (int l = p.d - 1; l >= 0; --l) {
+      int dig = rem % p.G;
+      rem /= p.G;
+      int x = dig - p.n;
+      int ax = x < 0 ? -x : x;
+      if (ax > p.n) inT = false; else w *= (double)(p.n + 1 - ax);
+      if (x < 0 || x > p.n) inI = false;
+      int md = 2 * p.n - dig;  // digit of -x
+      if (md < 0) mvalid = false;
+      mir += md * mul;
+      mul *= p.G;
+    }
+    double2 f = D.grid64[p.grid + i];
+    if (!isfinite(f.x) || !isfinite(f.y)) bad = 1;
+    D.gF[p.grid + i] = make_float2((float)f.x, (float)f.y);
+    float2 h = make_float2(0.f, 0.f);
+    if (mvalid) {
+      double2 fm = D.grid64[p.grid + mir];
+      h = make_float2((float)fm.x, -(float)fm.y);
+    }
+    D.gH[p.grid + i] = h;
+    double a2 = f.x * f.x + f.y * f.y;
+    if (inT) accT += w * a2;
+    if (inI) accF += a2;
+  }
+  double sT = block_sum(accT, sh);
+  if (threadIdx.x == 0) atomicAdd(&D.st[pi].normT2, sT);
+  double sF = block_sum(accF, sh);
+  if (threadIdx.x == 0) atomicAdd(&D.st[pi].normf2, sF);
+  if (bad) atomicOr(&D.st[pi].nonfinite, 1);
+}
+
+// V_0 entry (i, j) = complex normal from Philox counter i*r0 + j (Algorithm 3 start block).
+__global__ void k_init_v0(Dev D, unsigned long long seed) {
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  long long total = (long long)p.N * p.r0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    int row = (int)(q / p.r0), col = (int)(q % p.r0);
+    uint64_t c[4] = {(uint64_t)q, 0, 0, 0};
+    philox4x64(c, seed, PRONY_STREAM_V0);
+    float u0 = (float)philox_u01(c[0]), u1 = (float)philox_u01(c[1]);
+    float r = sqrtf(-logf(u0)), sn, cs;
+    sincospif(2.0f * u1, &sn, &cs);
+    D.V[p.xoff + (long long)col * p.N + row] = make_float2(r * cs, r * sn);
+  }
+}
+
+__global__ void k_zero_small(Dev D, long long off, long long bytes) {
+  const ProbDesc& p = D.P[blockIdx.y];
+  unsigned int* b = (unsigned int*)(D.small + p.soff + off);
+  for (long long i = blockIdx.x * blockDim.x + threadIdx.x; i < bytes / 4; i += gridDim.x * blockDim.x) b[i] = 0u;
+}
+
+// ----------------------------------------------------------------------------- tall-skinny Gram
+constexpr int GRAM_ROWS = 32;       // rows staged per pass
+constexpr int GRAM_CHUNK = 256;     // rows per block
+
+__global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
+                                              long long out_off, int out_ld) {
+  extern __shared__ float2 smem[];
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  const ProbState& s = D.st[pi];
+  if (s.done) return;
+  const int a = width_of(s, p, xw), b = width_of(s, p, zw);
+  const int r_begin = blockIdx.x * GRAM_CHUNK;
+  if (r_begin >= p.N || a <= 0 || b <= 0) return;
+  const int r_end = min(p.N, r_begin + GRAM_CHUNK);
+  float2* Xs = smem;                              // [a][GRAM_ROWS]
+  float2* Zs = smem + PRONY_RMAX * GRAM_ROWS;     // [b][GRAM_ROWS]
+  int ldx, ldz;
+  const float2* X = buf_base(D, xbuf, p, ldx);
+  const float2* Z = buf_base(D, zbuf, p, ldz);
+  const int na = (a + 3) >> 2, nb = (b + 3) >> 2, ntile = na * nb;
+  constexpr int TPT = 4;  // tiles per thread (up to 32 x 32 tiles)
+  float2 acc[TPT][4][4];
+#pragma unroll
+  for (int t = 0; t < TPT; ++t)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[t][i][j] = make_float2(0.f, 0.f);
+
+  for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < PRONY_RMAX * GRAM_ROWS; idx += blockDim.x) {
+      int rr = idx % GRAM_ROWS, col = idx / GRAM_ROWS;
+      int r = r0 + rr;
+      float2 vx = make_float2(0.f, 0.f), vz = make_float2(0.f, 0.f);
+      if (r < r_end) {
+        if (col < a) vx = X[(long long)col * ldx + buf_row(xbuf, p, r, xshift)];
+        if (col < b) vz = Z[(long long)col * ldz + buf_row(zbuf, p, r, zshift)];
+      }
+      Xs[col * GRAM_ROWS + rr] = vx;
+      Zs[col * GRAM_ROWS + rr] = vz;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+      int tile = threadIdx.x + t * blockDim.x;
+      if (tile >= ntile) break;
+      int ta = tile / nb, tb = tile % nb;
+      for (int rr = 0; rr < GRAM_ROWS; ++rr) {
+        float2 xa[4], zb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xa[i] = Xs[(4 * ta + i) * GRAM_ROWS + rr];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) zb[j] = Zs[(4 * tb + j) * GRAM_ROWS + rr];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[t][i][j].x += xa[i].x * zb[j].x + xa[i].y * zb[j].y;
+            acc[t][i][j].y += xa[i].x * zb[j].y - xa[i].y * zb[j].x;
+          }
+      }
+    }
+  }
+  double2* out = (double2*)(D.small + p.soff + out_off);
+#pragma unroll
+  for (int t = 0; t < TPT; ++t) {
+    int tile = threadIdx.x + t * blockDim.x;
+    if (tile >= ntile) break;
+    int ta = tile / nb, tb = tile % nb;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int ia = 4 * ta + i, jb = 4 * tb + j;
+        if (ia < a && jb < b) {
+          atomicAdd(&out[ia * out_ld + jb].x, (double)acc[t][i][j].x);
+          atomicAdd(&out[ia * out_ld + jb].y, (double)acc[t][i][j].y);
+        }
+      }
+  }
+}
+
+// ----------------------------------------------------------------------------- X M products
+constexpr int APPLY_ROWS = 32;
+
+__global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw, long long m_off, int m_double,
+                                               int zbuf, int outbuf, int norm_only) {
+  extern __shared__ float2 smem[];
+  __shared__ double shr[32];
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  ProbState& s = D.st[pi];
+  if (s.done) return;
+  const int a = width_of(s, p, xw), b = width_of(s, p, outw);
+  const int r0 = blockIdx.x * APPLY_ROWS;
+  if (r0 >= p.N || b <= 0) return;
+  float2* Ms = smem;                              // [a][b]  (ld b)
+  float2* Xs = smem + PRONY_RMAX * PRONY_RMAX;    // [a][APPLY_ROWS]
+  for (int idx = threadIdx.x; idx < a * b; idx += blockDim.x) {
+    int i = idx / b, j = idx % b;
+    float2 v;
+    if (m_double) {
+      double2 dv = ((const double2*)(D.small + p.soff + m_off))[i * D.L.LDM + j];
+      v = make_float2((float)dv.x, (float)dv.y);
+    } else {
+      v = ((const float2*)(D.small + p.soff + m_off))[i * D.L.LDR + j];
+    }
+    Ms[idx] = v;
+  }
+  int ldx;
+  const float2* X = buf_base(D, xbuf, p, ldx);
+  for (int idx = threadIdx.x; idx < a * APPLY_ROWS; idx += blockDim.x) {
+    int rr = idx % APPLY_ROWS, col = idx / APPLY_ROWS;
+    int r = r0 + rr;
+    Xs[idx] = (r < p.N) ? X[(long long)col * ldx + buf_row(xbuf, p, r, -1)] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int rr = threadIdx.x % APPLY_ROWS, cg = threadIdx.x / APPLY_ROWS;
+  const int r = r0 + rr;
+  int ldz = 0, ldo = 0;
+  const float2* Z = zbuf >= 0 ? buf_base(D, zbuf, p, ldz) : nullptr;
+  float2* O = norm_only ? nullptr : buf_base(D, outbuf, p, ldo);
+  double nrm = 0.0;
+  if (r < p.N) {
+    for (int j = cg; j < b; j += blockDim.x / APPLY_ROWS) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int i = 0; i < a; ++i) {
+        float2 x = Xs[i * APPLY_ROWS + rr], mm = Ms[i * b + j];
+        acc.x += x.x * mm.x - x.y * mm.y;
+        acc.y += x.x * mm.y + x.y * mm.x;
+      }
+      if (Z) {
+        float2 z = Z[(long long)j * ldz + buf_row(zbuf, p, r, -1)];
+        acc.x = z.x - acc.x;
+        acc.y = z.y - acc.y;
+      }
+      if (norm_only) nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
+      else O[(long long)j * ldo + buf_row(outbuf, p, r, -1)] = acc;
+    }
+  }
+  if (norm_only) {
+    double t = block_sum(nrm, shr);
+    if (threadIdx.x == 0) atomicAdd(&s.resid2, t);
+  }
+}
+
+// Largest-modulus row of each of the first m columns (lowest row on ties).
+__global__ void k_argmax(Dev D, int buf) {
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  const ProbState& s = D.st[pi];
+  int ld;
+  const float2* X = buf_base(D, buf, p, ld);
+  unsigned long long* am = (unsigned long long*)(D.small + p.soff + D.L.argmx);
+  const int w = s.wv;
+  for (int j = 0; j < w; ++j) {
+    unsigned long long best = 0ull;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < p.N; r += gridDim.x * blockDim.x) {
+      float2 v = X[(long long)j * ld + r];
+      float a2 = v.x * v.x + v.y * v.y;
+      unsigned long long key = ((unsigned long long)__float_as_uint(a2) << 32) | (0xFFFFFFFFull - (unsigned)r);
+      best = key > best ? key : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long oth = __shfl_xor_sync(0xffffffffu, best, o);
+      best = oth > best ? oth : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&am[j], best);
+  }
+}
+
+// ----------------------------------------------------------------------------- Vandermonde RHS / residual
+// rhs: b_i = sum_{k in I_n} conj(z_i^k) f(k);  resid: ||sum_j c_j z_j^k - f(k)||^2.
+// z_i^k = prod_l E_l[i][k_l] with E_l[i][x] = exp(-+2 pi i t_i(l) x) built by FP64 recurrence.
+constexpr int RHS_ROWS = 256;
+constexpr int RHS_TABLE_MAX = 6144;
+
+__global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
+  extern __shared__ double2 tab[];   // [d][m][n+1]
+  __shared__ double2 accb[PRONY_MMAX];
+  __shared__ double shr[32];
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  ProbState& s = D.st[pi];
+  const int m = s.rank_used;
+  const int n1 = p.n + 1;
+  const double* t = (const double*)(D.small + p.soff + D.L.t);
+  const double2* c = (const double2*)(D.small + p.soff + D.L.c);
+  const double sign = resid ? -1.0 : 1.0;
+  for (int q = threadIdx.x; q < p.d * m; q += blockDim.x) {
+    int l = q / m, i = q % m;
+    double sn, cs;
+    sincospi(2.0 * t[i * PRONY_DMAX + l], &sn, &cs);
+    double2 e1 = make_double2(cs, sign * sn), e = make_double2(1.0, 0.0);
+    double2* row = tab + ((size_t)l * m + i) * n1;
+    for (int x = 0; x < n1; ++x) {
+      row[x] = e;
+      e = cmul(e, e1);
+    }
+  }
+  for (int i = threadIdx.x; i < PRONY_MMAX; i += blockDim.x) accb[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const int r = blockIdx.x * RHS_ROWS + threadIdx.x;
+  int kk[PRONY_DMAX];
+  double2 f = make_double2(0.0, 0.0);
+  bool valid = r < p.N;
+  if (valid) {
+    int rem = r, gi = 0, mul = 1;
+    for (int l = p.d - 1; l >= 0; --l) {
+      kk[l] = rem % n1;
+      rem /= n1;
+      gi += (kk[l] + p.n) * mul;
+      mul *= p.G;
+    }
+    f = D.grid64[p.grid + gi];
+  }
+  if (!resid) {
+    for (int i = 0; i < m; ++i) {
+      double2 term = make_double2(0.0, 0.0);
+      if (valid) {
+        double2 e = tab[(size_t)i * n1 + kk[0]];
+        for (int l = 1; l < p.d; ++l) e = cmul(e, tab[((size_t)l * m + i) * n1 + kk[l]]);
+        term = cmul(e, f);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        term.x += __shfl_xor_sync(0xffffffffu, term.x, o);
+        term.y += __shfl_xor_sync(0xffffffffu, term.y, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&accb[i].x, term.x);
+        atomicAdd(&accb[i].y, term.y);
+      }
+    }
+    __syncthreads();
+    double2* b = (double2*)(D.small + p.soff + D.L.rhs);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      atomicAdd(&b[i].x, accb[i].x);
+      atomicAdd(&b[i].y, accb[i].y);
+    }
+  } else {
+    double r2 = 0.0;
+    if (valid) {
+      double2 v = make_double2(-f.x, -f.y);
+      for (int i = 0; i < m; ++i) {
+        double2 e = tab[(size_t)i * n1 + kk[0]];
+        for (int l = 1; l < p.d; ++l) e = cmul(e, tab[((size_t)l * m + i) * n1 + kk[l]]);
+        v = cadd(v, cmul(c[i], e));
+      }
+      r2 = cabs2(v);
+    }
+    double tot = block_sum(r2, shr);
+    if (threadIdx.x == 0) atomicAdd(&s.ls_num2, tot);
+  }
+}
+
+// Packed outputs: t_out[(ooff + j) d + l], c_out[ooff + j]; entries past rank_used are zero.
+__global__ void k_gather_out(Dev D, double* t_out, double2* c_out) {
+  const int pi = blockIdx.x;
+  const ProbDesc& p = D.P[pi];
+  const ProbState& s = D.st[pi];
+  const double* t = (const double*)(D.small + p.soff + D.L.t);
+  const double2* c = (const double2*)(D.small + p.soff + D.L.c);
+  for (int q = threadIdx.x; q < p.m * p.d; q += blockDim.x) {
+    int j = q / p.d, l = q % p.d;
+    t_out[(p.ooff + j) * p.d + l] = j < s.rank_used ? t[j * PRONY_DMAX + l] : 0.0;
+  }
+  for (int j = threadIdx.x; j < p.m; j += blockDim.x)
+    c_out[p.ooff + j] = j < s.rank_used ? c[j] : make_double2(0.0, 0.0);
+}
+
+__global__ void k_copy_cols(Dev D, int buf, int wsel, double2* out) {
+  const ProbDesc& p = D.P[0];
+  const ProbState& s = D.st[0];
+  int ld;
+  const float2* X = buf_base(D, buf, p, ld);
+  const int w = width_of(s, p, wsel);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)p.N * p.m;
+       q += (long long)gridDim.x * blockDim.x) {
+    int col = (int)(q / p.N), r = (int)(q % p.N);
+    float2 v = col < w ? X[(long long)col * ld + r] : make_float2(0.f, 0.f);
+    out[q] = make_double2(v.x, v.y);
+  }
+}
+
+// ----------------------------------------------------------------------------- exponential sum (Eq. 1)
+struct Box { int lo[PRONY_DMAX]; int len[PRONY_DMAX]; };
+
+__device__ inline void box_point(const Box& B, int d, long long q, int* k) {
+  for (int l = d - 1; l >= 0; --l) {
+    k[l] = B.lo[l] + (int)(q % B.len[l]);
+    q /= B.len[l];
+  }
+}
+
+// Phase <t_j, k> mod 1 from 64-bit binary fractions (exact), centred to [-1/2, 1/2).
+__device__ inline float centred_phase(const uint64_t* T, const int* k, int d) {
+  uint64_t acc = 0;
+  for (int l = 0; l < d; ++l) acc += T[l] * (uint64_t)(long long)k[l];
+  return (float)(int)(acc >> 32) * 2.3283064365386963e-10f;
+}
+
+__global__ void __launch_bounds__(256) k_expsum_fwd(const double* t, const float2* c, int m, int d, Box B,
+                                                    long long K, float2* f) {
+  __shared__ uint64_t T[PRONY_MMAX * PRONY_DMAX];
+  __shared__ float2 cs[PRONY_MMAX];
+  for (int q = threadIdx.x; q < m * d; q += blockDim.x) T[q] = frac64(t[q]);
+  for (int q = threadIdx.x; q < m; q += blockDim.x) cs[q] = c[q];
+  __syncthreads();
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < K; q += (long long)gridDim.x * blockDim.x) {
+    int k[PRONY_DMAX];
+    box_point(B, d, q, k);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = 0; j < m; ++j) {
+      float u = centred_phase(T + j * d, k, d), sn, cn;
+      sincospif(2.0f * u, &sn, &cn);                  // e = cn - i sn
+      float2 cj = cs[j];
+      acc.x += cj.x * cn + cj.y * sn;
+      acc.y += cj.y * cn - cj.x * sn;
+    }
+    f[q] = acc;
+  }
+}
+
+// acc[j][0..1] += sum_k g_k conj(e_jk);  acc[j][2+l] += sum_k k_l Im(conj(g_k) c_j e_jk)
+__global__ void __launch_bounds__(256) k_expsum_bwd(const double* t, const float2* c, int m, int d, Box B,
+                                                    long long K, const float2* g, double* acc) {
+  __shared__ uint64_t T[PRONY_MMAX * PRONY_DMAX];
+  __shared__ float2 cs[PRONY_MMAX];
+  __shared__ float blk[PRONY_MMAX * (2 + PRONY_DMAX)];
+  const int W = 2 + d;
+  for (int q = threadIdx.x; q < m * d; q += blockDim.x) T[q] = frac64(t[q]);
+  for (int q = threadIdx.x; q < m; q += blockDim.x) cs[q] = c[q];
+  for (int q = threadIdx.x; q < m * W; q += blockDim.x) blk[q] = 0.f;
+  __syncthreads();
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < K; base += (long long)gridDim.x * blockDim.x) {
+    long long q = base + threadIdx.x;
+    int k[PRONY_DMAX] = {0, 0, 0, 0};
+    float2 gk = make_float2(0.f, 0.f);
+    if (q < K) {
+      box_point(B, d, q, k);
+      gk = g[q];
+    }
+    for (int j = 0; j < m; ++j) {
+      float u = centred_phase(T + j * d, k, d), sn, cn;
+      sincospif(2.0f * u, &sn, &cn);
+      float2 e = make_float2(cn, -sn);
+      float gcx = gk.x * e.x + gk.y * e.y;            // g conj(e)
+      float gcy = gk.y * e.x - gk.x * e.y;
+      float2 ce = make_float2(cs[j].x * e.x - cs[j].y * e.y, cs[j].x * e.y + cs[j].y * e.x);
+      float im = gk.x * ce.y - gk.y * ce.x;           // Im(conj(g) c e)
+      float v[2 + PRONY_DMAX] = {gcx, gcy, im * k[0], im * k[1], im * k[2], im * k[3]};
+#pragma unroll
+      for (int w = 0; w < 2 + PRONY_DMAX; ++w) {
+        if (w >= W) break;
+        float x = v[w];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&blk[j * W + w], x);
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < m * W; q += blockDim.x) atomicAdd(&acc[q], (double)blk[q]);
+}
+
+__global__ void k_expsum_bwd_finish(const double* acc, int m, int d, double* gt, float2* gc) {
+  const int W = 2 + d;
+  const double two_pi = 6.283185307179586;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    gc[j] = make_float2((float)acc[j * W], (float)acc[j * W + 1]);
+    for (int l = 0; l < d; ++l) gt[j * d + l] = two_pi * acc[j * W + 2 + l];
+  }
+}
+
+__global__ void k_eval_points(const double* t, const double2* c, int m, int d, const int* k, int K, double2* f) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < K; q += gridDim.x * blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < m; ++j) {
+      uint64_t a = 0;
+      for (int l = 0; l < d; ++l) a += frac64(t[j * d + l]) * (uint64_t)(long long)k[(long long)q * d + l];
+      double u = (double)(long long)a * 5.421010862427522e-20;   // 2^-64
+      double sn, cn;
+      sincospi(2.0 * u, &sn, &cn);
+      acc = cadd(acc, cmul(c[j], make_double2(cn, -sn)));
+    }
+    f[q] = acc;
+  }
+}
+
+inline int blocks_for(long long n, int per) { return (int)std::min<long long>((n + per - 1) / per, 1 << 16); }
+
+}  // namespace
+
+#include <algorithm>
+
+void launch_prep(const Dev& D, cudaStream_t s) {
+  k_state_init<<<(D.nprob + 127) / 128, 128, 0, s>>>(D);
+  dim3 g(std::max(1, std::min((D.maxGd + 255) / 256, 64)), D.nprob);
+  k_prep<<<g, 256, 0, s>>>(D);
+}
+
+void launch_init_v0(const Dev& D, unsigned long long seed, cudaStream_t s) {
+  dim3 g(std::max(1, std::min((D.maxN * D.maxR0 + 255) / 256, 256)), D.nprob);
+  k_init_v0<<<g, 256, 0, s>>>(D, seed);
+}
+
+void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_t s) {
+  dim3 g(std::max<int>(1, std::min<int>((int)((bytes / 4 + 255) / 256), 32)), D.nprob);
+  k_zero_small<<<g, 256, 0, s>>>(D, off, bytes);
+}
+
+void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
+                 int out_ld, cudaStream_t s) {
+  static bool attr = false;
+  size_t sm = sizeof(float2) * 2 * PRONY_RMAX * GRAM_ROWS;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  dim3 g((D.maxN + GRAM_CHUNK - 1) / GRAM_CHUNK, D.nprob);
+  k_gram<<<g, 256, sm, s>>>(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld);
+}
+
+void launch_apply(const Dev& D, int xbuf, int xw, int outw, long long m_off, int m_double, int zbuf, int outbuf,
+                  int norm_only, cudaStream_t s) {
+  static bool attr = false;
+  size_t sm = sizeof(float2) * (PRONY_RMAX * PRONY_RMAX + PRONY_RMAX * APPLY_ROWS);
+  if (!attr) {
+    cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  dim3 g((D.maxN + APPLY_ROWS - 1) / APPLY_ROWS, D.nprob);
+  k_apply<<<g, 256, sm, s>>>(D, xbuf, xw, outw, m_off, m_double, zbuf, outbuf, norm_only);
+}
+
+void launch_argmax(const Dev& D, int buf, cudaStream_t s) {
+  dim3 g(std::max(1, std::min((D.maxN + 255) / 256, 64)), D.nprob);
+  k_argmax<<<g, 256, 0, s>>>(D, buf);
+}
+
+void launch_rhs(const Dev& D, int resid, cudaStream_t s) {
+  static bool attr = false;
+  size_t sm = sizeof(double2) * RHS_TABLE_MAX;
+  if (!attr) {
+    cudaFuncSetAttribute(k_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  dim3 g((D.maxN + RHS_ROWS - 1) / RHS_ROWS, D.nprob);
+  k_rhs<<<g, RHS_ROWS, sm, s>>>(D, resid);
+}
+
+void launch_gather_out(const Dev& D, double* t_out, double2* c_out, cudaStream_t s) {
+  k_gather_out<<<D.nprob, 128, 0, s>>>(D, t_out, c_out);
+}
+
+void launch_copy_cols(const Dev& D, int buf, int w_sel, double2* out, cudaStream_t s) {
+  k_copy_cols<<<64, 256, 0, s>>>(D, buf, w_sel, out);
+}
+
+static Box make_box(int d, const int* lo, const int* len) {
+  Box B = {};
+  for (int l = 0; l < d; ++l) { B.lo[l] = lo[l]; B.len[l] = len[l]; }
+  return B;
+}
+
+void launch_expsum_fwd(const double* t, const float2* c, int m, int d, const int* lo, const int* len, long long K,
+                       float2* f, cudaStream_t s) {
+  k_expsum_fwd<<<blocks_for(K, 256), 256, 0, s>>>(t, c, m, d, make_box(d, lo, len), K, f);
+}
+
+void launch_expsum_bwd(const double* t, const float2* c, int m, int d, const int* lo, const int* len, long long K,
+                       const float2* g, double* acc, cudaStream_t s) {
+  int nb = std::min(blocks_for(K, 256), 4 * 152);
+  k_expsum_bwd<<<nb, 256, 0, s>>>(t, c, m, d, make_box(d, lo, len), K, g, acc);
+}
+
+void launch_expsum_bwd_finish(const double* acc, int m, int d, double* gt, float2* gc, cudaStream_t s) {
+  k_expsum_bwd_finish<<<1, 64, 0, s>>>(acc, m, d, gt, gc);
+}
+
+void launch_eval_points(const double* t, const double2* c, int m, int d, const int* k, int K, double2* f,
+                        cudaStream_t s) {
+  k_eval_points<<<blocks_for(K, 128), 128, 0, s>>>(t, c, m, d, k, K, f);
+}

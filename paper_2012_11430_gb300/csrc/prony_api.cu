@@ -1,0 +1,624 @@
+// Host driver and C ABI of the Prony library (declarations in include/prony.h).
+//
+// One call runs Algorithm 1 for a batch of independent problems on one stream:
+//   prep (grid copies, ||T||_F closed form) -> V_0 (Philox) -> CholeskyQR2(V_0)
+//   -> Y = T V  [Toeplitz product over the box {0..n+1}^d]
+//   -> loop (Algorithm 3):  U = qr(Y|I_n) ; Vbar = T^* U ; V = qr(Vbar) (column pivoting and
+//      rank on the first pass) ; Y = T V ; Q = U^* Y|I_n ; ||Y|I_n - U Q||_F ; stop test
+//   -> SVD(Q), S_l = U_Q^* (U^* Y_l) V_Q Sigma^{-1}  (Y_l = rows k + e_l of the last Y)
+//   -> C_mu, eig, z, t -> conj(A) f, Gram, c -> ||A^T c - f||.
+// Every kernel loops over the problems of the batch; problems that stopped skip work.
+// The host waits once per power iteration to read the "all stopped" flag.
+#include "common.cuh"
+#include "../../include/prony.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_err;
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PRONY_ENOMEM : PRONY_ECUDA;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+int ensure(DBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (b.cap >= bytes) return PRONY_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = bytes + bytes / 4;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  b.cap = want;
+  return PRONY_OK;
+}
+
+}  // namespace
+
+struct prony_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  DBuf grid64, gF, gH, V, U, B1, B2, Y, small, P, st, jobs, flag, tout, cout, misc, misc2, misc3;
+  int* h_flag = nullptr;            // pinned
+  std::vector<ProbState> h_st;
+};
+
+namespace {
+
+struct HostProb {
+  int d, n, m;
+  long long sample_off, out_off;
+};
+
+double default_tol_power(int prec) {
+  (void)prec;
+  return 1e-6;
+}
+
+int validate(const HostProb& h) {
+  if (h.d < 1 || h.d > PRONY_DMAX || h.n < 1 || h.m < 1 || h.m > PRONY_MMAX) return PRONY_EINVAL;
+  double N = std::pow((double)(h.n + 1), h.d);
+  if (N > 2.0e8 || h.m > N) return PRONY_EINVAL;
+  if ((long long)h.d * h.m * (h.n + 1) > 6144) return PRONY_EINVAL;   // phase tables of the RHS kernel
+  return PRONY_OK;
+}
+
+long long ipow(long long b, int e) {
+  long long r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+struct Batch {
+  std::vector<ProbDesc> P;
+  Dev D{};
+  int njobs_ext = 0, njobs_in = 0, nks = 1;
+  ToeplitzJob* jobs_ext = nullptr;
+  ToeplitzJob* jobs_in = nullptr;
+  int maxw = 0;
+};
+
+// Lay out a batch in the context workspace.  Grid samples are copied from `src`
+// (host or device, per problem sample_off) into the packed grid64 buffer.
+int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opts& o, Batch& B) {
+  const int np = (int)hp.size();
+  B.P.resize(np);
+  long long goff = 0, xoff = 0, yoff = 0;
+  int maxN = 0, maxNext = 0, maxGd = 0, maxR0 = 0, maxM = 0, maxD = 0;
+  long long tiles_ext = 0, tiles_in = 0;
+  for (int i = 0; i < np; ++i) {
+    const HostProb& h = hp[i];
+    ProbDesc& p = B.P[i];
+    p.d = h.d;
+    p.n = h.n;
+    p.m = h.m;
+    p.N = (int)ipow(h.n + 1, h.d);
+    p.Next = (int)ipow(h.n + 2, h.d);
+    p.G = 2 * h.n + 2;
+    p.Gd = (int)ipow(p.G, h.d);
+    int pp = o.oversample_p < 0 ? h.m : o.oversample_p;
+    p.r0 = std::min(std::min(h.m + pp, p.N), PRONY_RMAX);
+    p.r0 = std::max(p.r0, h.m);
+    p.grid = goff;
+    p.xoff = xoff;
+    p.yoff = yoff;
+    p.ooff = h.out_off;
+    goff += p.Gd;
+    xoff += (long long)p.N * p.r0;
+    yoff += (long long)p.Next * p.r0;
+    maxN = std::max(maxN, p.N);
+    maxNext = std::max(maxNext, p.Next);
+    maxGd = std::max(maxGd, p.Gd);
+    maxR0 = std::max(maxR0, p.r0);
+    maxM = std::max(maxM, p.m);
+    maxD = std::max(maxD, p.d);
+    tiles_ext += (p.Next + 63) / 64;
+    tiles_in += (p.N + 63) / 64;
+  }
+  SmallLay L = make_small_lay((maxR0 + 1) / 2 * 2, maxM, maxD);
+  for (int i = 0; i < np; ++i) B.P[i].soff = (long long)i * L.bytes;
+  // split K so that the smallest product still fills the GPU
+  int nks = (int)std::max<long long>(1, std::min<long long>(304 / std::max<long long>(1, tiles_in), 16));
+  nks = std::min(nks, std::max(1, maxN / 64));
+  B.nks = nks;
+  std::vector<ToeplitzJob> jobs;
+  for (int i = 0; i < np; ++i)
+    for (int mt = 0; mt < (B.P[i].Next + 63) / 64; ++mt)
+      for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
+  B.njobs_ext = (int)jobs.size();
+  for (int i = 0; i < np; ++i)
+    for (int mt = 0; mt < (B.P[i].N + 63) / 64; ++mt)
+      for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
+  B.njobs_in = (int)jobs.size() - B.njobs_ext;
+  B.maxw = maxR0;
+
+  int rc;
+  if ((rc = ensure(ctx->grid64, sizeof(double2) * goff))) return rc;
+  if ((rc = ensure(ctx->gF, sizeof(float2) * goff))) return rc;
+  if ((rc = ensure(ctx->gH, sizeof(float2) * goff))) return rc;
+  if ((rc = ensure(ctx->V, sizeof(float2) * xoff))) return rc;
+  if ((rc = ensure(ctx->U, sizeof(float2) * xoff))) return rc;
+  if ((rc = ensure(ctx->B1, sizeof(float2) * xoff))) return rc;
+  if ((rc = ensure(ctx->B2, sizeof(float2) * xoff))) return rc;
+  if ((rc = ensure(ctx->Y, sizeof(float2) * yoff))) return rc;
+  if ((rc = ensure(ctx->small, (size_t)L.bytes * np))) return rc;
+  if ((rc = ensure(ctx->P, sizeof(ProbDesc) * np))) return rc;
+  if ((rc = ensure(ctx->st, sizeof(ProbState) * np))) return rc;
+  if ((rc = ensure(ctx->jobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
+  if ((rc = ensure(ctx->flag, 256))) return rc;
+  CK(cudaMemcpyAsync(ctx->P.p, B.P.data(), sizeof(ProbDesc) * np, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->jobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->small.p, 0, (size_t)L.bytes * np, ctx->stream));
+  Dev& D = B.D;
+  D.P = (const ProbDesc*)ctx->P.p;
+  D.st = (ProbState*)ctx->st.p;
+  D.nprob = np;
+  D.maxN = maxN;
+  D.maxNext = maxNext;
+  D.maxGd = maxGd;
+  D.maxR0 = maxR0;
+  D.maxM = maxM;
+  D.maxD = maxD;
+  D.grid64 = (const double2*)ctx->grid64.p;
+  D.gF = (float2*)ctx->gF.p;
+  D.gH = (float2*)ctx->gH.p;
+  D.V = (float2*)ctx->V.p;
+  D.U = (float2*)ctx->U.p;
+  D.B1 = (float2*)ctx->B1.p;
+  D.B2 = (float2*)ctx->B2.p;
+  D.Y = (float2*)ctx->Y.p;
+  D.small = (char*)ctx->small.p;
+  D.L = L;
+  B.jobs_ext = (ToeplitzJob*)ctx->jobs.p;
+  B.jobs_in = B.jobs_ext + B.njobs_ext;
+  return PRONY_OK;
+}
+
+// CholeskyQR2 of the tall block in `xbuf` (width selector xw) into `outbuf`, through B1.
+// mode: QR_PLAIN / QR_DROP / QR_RANK for the first pass; the second pass is plain.
+void tall_qr(const Batch& B, int xbuf, int xw, int target, int mode, double tol, int rank_mode, int outbuf,
+             cudaStream_t s) {
+  const Dev& D = B.D;
+  launch_zero_small(D, D.L.gram, 16LL * D.L.LDR * D.L.LDR, s);
+  launch_gram(D, xbuf, -1, xw, xbuf, -1, xw, D.L.gram, D.L.LDR, s);
+  launch_chol(D, xw, target, mode, tol, rank_mode, s);
+  launch_apply(D, xbuf, W_IN, W_OUT, D.L.mapm, 0, -1, BUF_B1, 0, s);
+  launch_zero_small(D, D.L.gram, 16LL * D.L.LDR * D.L.LDR, s);
+  launch_gram(D, BUF_B1, -1, target, BUF_B1, -1, target, D.L.gram, D.L.LDR, s);
+  launch_chol(D, target, target, QR_PLAIN, 0.0, 0, s);
+  launch_apply(D, BUF_B1, W_IN, W_OUT, D.L.mapm, 0, -1, outbuf, 0, s);
+}
+
+struct RunOut {
+  int want_S = 0;
+};
+
+int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
+  cudaStream_t s = ctx->stream;
+  const Dev& D = B.D;
+  const int prec = o.precision;
+  const double tol_rank = o.tol_rank > 0 ? o.tol_rank : 1e-3;
+  const double tol_power = o.tol_power > 0 ? o.tol_power : default_tol_power(prec);
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 30;
+  const double tol_drop = 1e-3;
+
+  launch_prep(D, s);
+  launch_init_v0(D, o.seed, s);
+  tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+  launch_toeplitz(D, B.jobs_ext, B.njobs_ext, B.nks, 0, BUF_V, W_V, BUF_Y, 1, B.maxw, prec, s);
+  int* dflag = (int*)ctx->flag.p;
+  for (int it = 1; it <= max_iter; ++it) {
+    // U = qr(T V_{k-1})  (rows I_n of Y)
+    tall_qr(B, BUF_Y, W_V, W_U, QR_DROP, tol_drop, 0, BUF_U, s);
+    // Vbar = T^* U
+    launch_toeplitz(D, B.jobs_in, B.njobs_in, B.nks, 1, BUF_U, W_U, BUF_B2, 0, B.maxw, prec, s);
+    // V = qr(Vbar), column pivoting and rank on the first iteration
+    if (it == 1) tall_qr(B, BUF_B2, W_U, W_V, QR_RANK, tol_rank, o.rank_mode, BUF_V, s);
+    else tall_qr(B, BUF_B2, W_U, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+    // Y = T V over the box {0..n+1}^d
+    launch_toeplitz(D, B.jobs_ext, B.njobs_ext, B.nks, 0, BUF_V, W_V, BUF_Y, 1, B.maxw, prec, s);
+    // Q = U^* (T V), ||T V - U Q||_F
+    launch_zero_small(D, D.L.q, 16LL * D.L.LDR * D.L.LDM, s);
+    launch_gram(D, BUF_U, -1, W_U, BUF_Y, -1, W_V, D.L.q, D.L.LDM, s);
+    launch_apply(D, BUF_U, W_U, W_V, D.L.q, 1, BUF_Y, -1, 1, s);
+    CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
+    launch_check(D, tol_power, max_iter, dflag, s);
+    CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*ctx->h_flag != 0) break;
+  }
+  // finishing steps run for every problem that has not failed
+  launch_reset_done(D, s);
+  // M_l = U^* Y_l  with Y_l the rows k + e_l of the last product Y = T V
+  launch_zero_small(D, D.L.mproj, 16LL * D.maxD * D.L.LDR * D.L.LDM, s);
+  for (int l = 0; l < D.maxD; ++l)
+    launch_gram(D, BUF_U, -1, W_U, BUF_Y, l, W_V, D.L.mproj + 16LL * l * D.L.LDR * D.L.LDM, D.L.LDM, s);
+  launch_svd_S(D, s);
+  if (ro.want_S) {
+    // phase-canonical basis: argmax over V V_Q, then rotate U_Q, V_Q, S_l
+    launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);
+    launch_zero_small(D, D.L.argmx, 8LL * D.L.LDM, s);
+    launch_argmax(D, BUF_B1, s);
+    launch_canon(D, s);
+    launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);   // V_final
+    launch_apply(D, BUF_U, W_U, W_V, D.L.uq, 1, -1, BUF_B2, 0, s);   // U_final
+  }
+  launch_eig_t(D, o.seed, s);
+  launch_zero_small(D, D.L.rhs, 16LL * D.L.LDM, s);
+  launch_rhs(D, 0, s);
+  launch_solve_c(D, s);
+  launch_rhs(D, 1, s);
+  CK(cudaGetLastError());
+  return PRONY_OK;
+}
+
+int read_states(prony_ctx* ctx, const Batch& B, prony_info* infos, int* worst) {
+  const int np = B.D.nprob;
+  ctx->h_st.resize(np);
+  CK(cudaMemcpyAsync(ctx->h_st.data(), B.D.st, sizeof(ProbState) * np, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int w = PRONY_OK;
+  for (int i = 0; i < np; ++i) {
+    const ProbState& s = ctx->h_st[i];
+    if (infos) {
+      prony_info& I = infos[i];
+      I.status = s.status;
+      I.rank_detected = s.rank_det;
+      I.rank_used = s.rank_used;
+      I.power_iters = s.iter;
+      I.normT = std::sqrt(std::max(0.0, s.normT2));
+      I.power_resid = s.normT2 > 0 ? std::sqrt(std::max(0.0, s.resid2) / s.normT2) : 0.0;
+      I.ls_resid = s.normf2 > 0 ? std::sqrt(std::max(0.0, s.ls_num2) / s.normf2) : 0.0;
+      I.sigma_ratio = s.sigma_ratio;
+    }
+    if (s.status != PRONY_OK && (w == PRONY_OK || s.status < w)) w = s.status;
+  }
+  *worst = w;
+  return PRONY_OK;
+}
+
+prony_opts resolve_opts(const prony_opts* o) {
+  prony_opts r;
+  prony_default_opts(&r);
+  if (o) r = *o;
+  return r;
+}
+
+int check_precision(int prec) {
+  return prec == PRONY_FP32 ? PRONY_OK : PRONY_EINVAL;
+}
+
+// Copy problem grids to the packed device buffer (host or device source).
+int load_grids(prony_ctx* ctx, const Batch& B, const std::vector<HostProb>& hp, const prony_c128* src, bool device) {
+  for (size_t i = 0; i < hp.size(); ++i) {
+    const ProbDesc& p = B.P[i];
+    CK(cudaMemcpyAsync((double2*)ctx->grid64.p + p.grid, src + hp[i].sample_off, sizeof(double2) * p.Gd,
+                       device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  }
+  return PRONY_OK;
+}
+
+}  // namespace
+
+// ============================================================================= C ABI
+extern "C" {
+
+void prony_default_opts(prony_opts* o) {
+  if (!o) return;
+  o->precision = PRONY_FP32;
+  o->oversample_p = -1;
+  o->tol_rank = 0.0;
+  o->tol_power = 0.0;
+  o->max_iter = 0;
+  o->seed = 2012114300ull;
+  o->rank_mode = 0;
+}
+
+const char* prony_status_string(int s) {
+  switch (s) {
+    case PRONY_OK: return "ok";
+    case PRONY_EINVAL: return "invalid argument";
+    case PRONY_ERANK: return "numerical rank below m";
+    case PRONY_ENOCONV: return "iteration cap reached";
+    case PRONY_ENAN: return "non-finite data";
+    case PRONY_ECUDA: return "CUDA error";
+    case PRONY_ENOMEM: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+const char* prony_last_error(void) { return g_err.c_str(); }
+
+int prony_ctx_create(prony_ctx** out, int device) {
+  if (!out) return PRONY_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return PRONY_EINVAL;
+  CK(cudaSetDevice(device));
+  prony_ctx* c = new prony_ctx();
+  c->device = device;
+  e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreate"); }
+  e = cudaMallocHost(&c->h_flag, 256);
+  if (e != cudaSuccess) { cudaStreamDestroy(c->stream); delete c; return cuda_fail(e, "cudaMallocHost"); }
+  *out = c;
+  return PRONY_OK;
+}
+
+int prony_ctx_destroy(prony_ctx* c) {
+  if (!c) return PRONY_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  DBuf* bufs[] = {&c->grid64, &c->gF, &c->gH, &c->V, &c->U, &c->B1, &c->B2, &c->Y, &c->small, &c->P,
+                  &c->st, &c->jobs, &c->flag, &c->tout, &c->cout, &c->misc, &c->misc2, &c->misc3};
+  for (DBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (c->h_flag) cudaFreeHost(c->h_flag);
+  cudaStreamDestroy(c->stream);
+  delete c;
+  return PRONY_OK;
+}
+
+static int solve_batched_impl(prony_ctx* ctx, int P, const int* d, const int* n, const int* m,
+                              const long long* sample_off, const prony_c128* samples, bool dev_samples,
+                              const long long* out_off, double* t_out, prony_c128* c_out, bool dev_out,
+                              prony_info* infos, const prony_opts* opts, cudaStream_t user_stream) {
+  if (!ctx || P <= 0 || !d || !n || !m || !sample_off || !samples || !out_off || !t_out || !c_out)
+    return PRONY_EINVAL;
+  prony_opts o = resolve_opts(opts);
+  if (check_precision(o.precision)) return PRONY_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<HostProb> hp(P);
+  long long total_terms = 0;
+  for (int i = 0; i < P; ++i) {
+    hp[i] = {d[i], n[i], m[i], sample_off[i], out_off[i]};
+    if (validate(hp[i])) return PRONY_EINVAL;
+    total_terms = std::max(total_terms, out_off[i] + m[i]);
+  }
+  if (user_stream) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, user_stream));
+    CK(cudaStreamWaitEvent(ctx->stream, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  Batch B;
+  int rc = setup_batch(ctx, hp, o, B);
+  if (rc) return rc;
+  if ((rc = load_grids(ctx, B, hp, samples, dev_samples))) return rc;
+  RunOut ro;
+  if ((rc = run_batch(ctx, B, o, ro))) return rc;
+  int maxd = B.D.maxD;
+  double* tdev = t_out;
+  double2* cdev = (double2*)c_out;
+  if (!dev_out) {
+    if ((rc = ensure(ctx->tout, sizeof(double) * total_terms * maxd))) return rc;
+    if ((rc = ensure(ctx->cout, sizeof(double2) * total_terms))) return rc;
+    tdev = (double*)ctx->tout.p;
+    cdev = (double2*)ctx->cout.p;
+  }
+  launch_gather_out(B.D, tdev, cdev, ctx->stream);
+  CK(cudaGetLastError());
+  int worst = PRONY_OK;
+  if ((rc = read_states(ctx, B, infos, &worst))) return rc;
+  if (!dev_out) {
+    // per-problem d may differ: copy each problem's block
+    std::vector<double> th(total_terms * maxd);
+    std::vector<double2> ch(total_terms);
+    CK(cudaMemcpy(th.data(), tdev, sizeof(double) * total_terms * maxd, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(ch.data(), cdev, sizeof(double2) * total_terms, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < P; ++i) {
+      std::memcpy(t_out + out_off[i] * d[i], th.data() + out_off[i] * d[i], sizeof(double) * m[i] * d[i]);
+      std::memcpy(c_out + out_off[i], ch.data() + out_off[i], sizeof(double2) * m[i]);
+    }
+  } else if (user_stream) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, ctx->stream));
+    CK(cudaStreamWaitEvent(user_stream, ev, 0));
+    cudaEventDestroy(ev);
+    CK(cudaStreamSynchronize(user_stream));
+  }
+  return worst;
+}
+
+int prony_solve_batched(prony_ctx* ctx, int P, const int* d, const int* n, const int* m,
+                        const long long* sample_off, const prony_c128* samples, const long long* out_off,
+                        double* t_out, prony_c128* c_out, prony_info* infos, const prony_opts* opts) {
+  return solve_batched_impl(ctx, P, d, n, m, sample_off, samples, false, out_off, t_out, c_out, false, infos, opts,
+                            nullptr);
+}
+
+int prony_solve_batched_dev(prony_ctx* ctx, int P, const int* d, const int* n, const int* m,
+                            const long long* sample_off, const prony_c128* samples_dev, const long long* out_off,
+                            double* t_out_dev, prony_c128* c_out_dev, prony_info* infos, const prony_opts* opts,
+                            void* stream) {
+  return solve_batched_impl(ctx, P, d, n, m, sample_off, samples_dev, true, out_off, t_out_dev, c_out_dev, true,
+                            infos, opts, (cudaStream_t)stream);
+}
+
+int prony_solve(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m, const prony_opts* opts,
+                double* t_out, prony_c128* c_out, prony_info* info) {
+  long long zero = 0;
+  return solve_batched_impl(ctx, 1, &d, &n, &m, &zero, samples, false, &zero, t_out, c_out, false, info, opts,
+                            nullptr);
+}
+
+int prony_build_S(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m, const prony_opts* opts,
+                  prony_c128* S_out, double* sigma_out, prony_c128* U_out, prony_c128* V_out, prony_info* info) {
+  if (!ctx || !samples || !S_out || !sigma_out) return PRONY_EINVAL;
+  prony_opts o = resolve_opts(opts);
+  if (check_precision(o.precision)) return PRONY_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<HostProb> hp = {{d, n, m, 0, 0}};
+  if (validate(hp[0])) return PRONY_EINVAL;
+  Batch B;
+  int rc = setup_batch(ctx, hp, o, B);
+  if (rc) return rc;
+  if ((rc = load_grids(ctx, B, hp, samples, false))) return rc;
+  RunOut ro;
+  ro.want_S = 1;
+  if ((rc = run_batch(ctx, B, o, ro))) return rc;
+  const SmallLay& L = B.D.L;
+  std::vector<char> small(L.bytes);
+  CK(cudaMemcpyAsync(small.data(), ctx->small.p, L.bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  const long long N = B.P[0].N;
+  std::vector<double2> Uh, Vh;
+  if (U_out || V_out) {
+    if ((rc = ensure(ctx->misc, sizeof(double2) * N * m))) return rc;
+    if (U_out) {
+      launch_copy_cols(B.D, BUF_B2, W_V, (double2*)ctx->misc.p, ctx->stream);
+      CK(cudaMemcpyAsync(U_out, ctx->misc.p, sizeof(double2) * N * m, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (V_out) {
+      launch_copy_cols(B.D, BUF_B1, W_V, (double2*)ctx->misc.p, ctx->stream);
+      CK(cudaMemcpyAsync(V_out, ctx->misc.p, sizeof(double2) * N * m, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+  }
+  int worst = PRONY_OK;
+  if ((rc = read_states(ctx, B, info, &worst))) return rc;
+  const int w = ctx->h_st[0].wv;
+  const double2* S = (const double2*)(small.data() + L.S);
+  const double* sg = (const double*)(small.data() + L.sigma);
+  for (int l = 0; l < d; ++l)
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        double2 v = (i < w && j < w) ? S[(size_t)l * L.LDM * L.LDM + i * L.LDM + j] : make_double2(0.0, 0.0);
+        S_out[((size_t)l * m + i) * m + j] = {v.x, v.y};
+      }
+  for (int i = 0; i < m; ++i) sigma_out[i] = i < w ? sg[i] : 0.0;
+  return worst;
+}
+
+int prony_eval(prony_ctx* ctx, const double* t, const prony_c128* c, int m, int d, const int* k, int K,
+               prony_c128* f_out) {
+  if (!ctx || !t || !c || !k || !f_out || m < 1 || m > PRONY_MMAX || d < 1 || d > PRONY_DMAX || K < 0)
+    return PRONY_EINVAL;
+  if (K == 0) return PRONY_OK;
+  CK(cudaSetDevice(ctx->device));
+  int rc;
+  if ((rc = ensure(ctx->misc, sizeof(double) * m * d + sizeof(double2) * m))) return rc;
+  if ((rc = ensure(ctx->misc2, sizeof(int) * (size_t)K * d))) return rc;
+  if ((rc = ensure(ctx->misc3, sizeof(double2) * (size_t)K))) return rc;
+  double* td = (double*)ctx->misc.p;
+  double2* cd = (double2*)((char*)ctx->misc.p + ((sizeof(double) * m * d + 15) / 16 * 16));
+  CK(cudaMemcpyAsync(td, t, sizeof(double) * m * d, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(cd, c, sizeof(double2) * m, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->misc2.p, k, sizeof(int) * (size_t)K * d, cudaMemcpyHostToDevice, ctx->stream));
+  launch_eval_points(td, cd, m, d, (const int*)ctx->misc2.p, K, (double2*)ctx->misc3.p, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(f_out, ctx->misc3.p, sizeof(double2) * (size_t)K, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PRONY_OK;
+}
+
+static long long box_count(int d, const int* len) {
+  long long K = 1;
+  for (int l = 0; l < d; ++l) {
+    if (len[l] < 0) return -1;
+    K *= len[l];
+  }
+  return K;
+}
+
+int prony_expsum_fwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev, int m, int d, const int* lo,
+                         const int* len, void* f_dev, void* stream) {
+  if (!ctx || !t_dev || !c_dev || !f_dev || !lo || !len || m < 1 || m > PRONY_MMAX || d < 1 || d > PRONY_DMAX)
+    return PRONY_EINVAL;
+  long long K = box_count(d, len);
+  if (K < 0) return PRONY_EINVAL;
+  if (K == 0) return PRONY_OK;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  launch_expsum_fwd(t_dev, (const float2*)c_dev, m, d, lo, len, K, (float2*)f_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return PRONY_OK;
+}
+
+int prony_expsum_bwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev, int m, int d, const int* lo,
+                         const int* len, const void* g_dev, double* grad_t_dev, void* grad_c_dev, void* stream) {
+  if (!ctx || !t_dev || !c_dev || !g_dev || !grad_t_dev || !grad_c_dev || !lo || !len || m < 1 ||
+      m > PRONY_MMAX || d < 1 || d > PRONY_DMAX)
+    return PRONY_EINVAL;
+  long long K = box_count(d, len);
+  if (K < 0) return PRONY_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  int rc;
+  if ((rc = ensure(ctx->misc3, sizeof(double) * m * (2 + d)))) return rc;
+  CK(cudaMemsetAsync(ctx->misc3.p, 0, sizeof(double) * m * (2 + d), s));
+  if (K > 0) launch_expsum_bwd(t_dev, (const float2*)c_dev, m, d, lo, len, K, (const float2*)g_dev,
+                               (double*)ctx->misc3.p, s);
+  launch_expsum_bwd_finish((const double*)ctx->misc3.p, m, d, grad_t_dev, (float2*)grad_c_dev, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return PRONY_OK;
+}
+
+int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int n, const void* X_dev, int r, int L,
+                          int adjoint, int precision, void* Y_dev, void* stream) {
+  if (!ctx || !grid_dev || !X_dev || !Y_dev || d < 1 || d > PRONY_DMAX || n < 1 || r < 1 || r > PRONY_RMAX)
+    return PRONY_EINVAL;
+  if (L != n + 1 && L != n + 2) return PRONY_EINVAL;
+  if (adjoint && L != n + 1) return PRONY_EINVAL;
+  if (check_precision(precision)) return PRONY_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  std::vector<HostProb> hp = {{d, n, 1, 0, 0}};
+  if (std::pow((double)(n + 1), d) > 2.0e8) return PRONY_EINVAL;
+  prony_opts o;
+  prony_default_opts(&o);
+  o.oversample_p = r - 1;
+  Batch B;
+  // ensure the stream order: ctx work after the caller's stream
+  if (stream) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, s));
+    CK(cudaStreamWaitEvent(ctx->stream, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  int rc = setup_batch(ctx, hp, o, B);
+  if (rc) return rc;
+  B.P[0].r0 = r;
+  CK(cudaMemcpyAsync(ctx->P.p, B.P.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->grid64.p, grid_dev, sizeof(double2) * B.P[0].Gd, cudaMemcpyDeviceToDevice, ctx->stream));
+  launch_prep(B.D, ctx->stream);
+  // operate directly on the caller's buffers: X as V (ld N), Y as Y (ld L^d)
+  Dev D = B.D;
+  D.V = (float2*)X_dev;
+  D.Y = (float2*)Y_dev;
+  D.B2 = (float2*)Y_dev;
+  const int y_ext = (L == n + 2);
+  launch_toeplitz(D, y_ext ? B.jobs_ext : B.jobs_in, y_ext ? B.njobs_ext : B.njobs_in, B.nks, adjoint, BUF_V, W_R0,
+                  y_ext ? BUF_Y : BUF_B2, y_ext, r, precision, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PRONY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 Toeplitz products, FP64 small steps):
+  * Toeplitz product, elementwise: |Y_gpu - Y| <= (2N + 16) u32 (|F| |X|)  -- the classic
+    floating-point dot-product bound gamma_N |a||b| plus the rounding of the FP64 samples to FP32.
+  * Prony results, noise-free: torus distance of t <= 1e-6, relative 2-norm error of c <= 1e-5,
+    relative Frobenius error of the S_l (phase-aligned) <= 1e-5.
+  * Noisy data: the forward error of the GPU result is at most 1.5x the oracle's, plus 1e-6 absolute.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import prony_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_11430_gb300 import Context
+    from paper_2012_11430_gb300.build import build
+    build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _random_grid(d, n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (2 * n + 2,) * d
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _toeplitz_rows(grid, n, d, L, adjoint):
+    """Explicit matrix of the product: rows k in {0..L-1}^d, columns h in I_n."""
+    K = O.box_set([L] * d, d)
+    H = O.index_set(n, d)
+    if adjoint:
+        return O.build_T(grid, n, d).conj().T
+    return O.sample(grid, n, K[:, None, :] - H[None, :, :])
+
+
+@pytest.mark.parametrize("d,n,r,L_ext,adjoint", [
+    (1, 7, 3, 0, 0), (1, 7, 3, 1, 0), (1, 12, 5, 0, 1),
+    (2, 15, 10, 1, 0), (2, 15, 10, 0, 1), (2, 9, 5, 1, 0), (2, 9, 17, 0, 1),
+    (3, 4, 7, 1, 0), (3, 4, 7, 0, 1), (2, 31, 40, 1, 0), (2, 5, 1, 1, 0),
+])
+def test_toeplitz_product(ctx, d, n, r, L_ext, adjoint):
+    import torch
+    grid = _random_grid(d, n, 100 + d * 10 + n)
+    N = (n + 1) ** d
+    L = n + 2 if L_ext else n + 1
+    rng = np.random.Generator(np.random.PCG64(7 + r))
+    X = (rng.standard_normal((r, N)) + 1j * rng.standard_normal((r, N))).astype(np.complex64)
+    g_dev = torch.from_numpy(grid.reshape(-1).astype(np.complex128)).cuda()
+    X_dev = torch.from_numpy(X).cuda()
+    Y_dev = torch.zeros((r, L ** d), dtype=torch.complex64, device="cuda")
+    ctx.toeplitz_mm_dev(g_dev, d, n, X_dev, L, adjoint, "fp32", Y_dev)
+    Y = Y_dev.cpu().numpy().astype(np.complex128).T
+    T = _toeplitz_rows(grid, n, d, L, adjoint)
+    Xd = X.astype(np.complex128).T
+    ref = T @ Xd
+    bound = (2 * N + 16) * U32 * (np.abs(T) @ np.abs(Xd))
+    assert np.all(np.abs(Y - ref) <= bound + 1e-30), float(np.max(np.abs(Y - ref) / (bound + 1e-30)))
+
+
+def test_eval_matches_expsum(ctx):
+    P = W.make_problem("ev", 3, 5, 6, 11)
+    rng = np.random.Generator(np.random.PCG64(3))
+    k = rng.integers(-70, 70, size=(257, 3)).astype(np.int32)
+    f = ctx.eval(P.t, P.c, k)
+    ref = O.expsum(P.t, P.c, k.astype(np.int64))
+    assert np.max(np.abs(f - ref)) <= 1e-12 * np.sum(np.abs(P.c))
+
+
+def _check_solution(res, t_ref, c_ref, t_tol=1e-6, c_tol=1e-5):
+    t_err = float(np.max(W.torus_dist(res.t, t_ref))) if len(t_ref) else 0.0
+    c_err = float(np.linalg.norm(res.c - c_ref) / np.linalg.norm(c_ref))
+    assert t_err <= t_tol and c_err <= c_tol, (t_err, c_err, res.info)
+
+
+@pytest.mark.parametrize("name,d,n,m,seed", [
+    ("C1", 2, 15, 5, None), ("d1", 1, 12, 3, 5), ("d1m1", 1, 4, 1, 6), ("d2rag", 2, 9, 7, 7),
+    ("d3", 3, 5, 4, 8), ("d2small", 2, 3, 2, 9), ("d2m12", 2, 23, 12, 10),
+])
+def test_solve_noise_free_matches_oracle(ctx, name, d, n, m, seed):
+    P = W.config_problem("C1") if seed is None else W.make_problem(name, d, n, m, seed)
+    res = ctx.solve(P.grid, P.d, P.n, P.m)
+    t_o, c_o, info_o = O.prony(P.grid, P.d, P.n, P.m)
+    assert res.info["status"] == 0, res.info
+    _check_solution(res, t_o, c_o)
+    _check_solution(res, P.t[np.lexsort(P.t.T[::-1])], P.c[np.lexsort(P.t.T[::-1])])
+    assert res.info["rank_detected"] == m
+    assert res.info["ls_resid"] < 1e-5
+
+
+def _phase_invariants(S):
+    """|S_ab| and S_ab S_ba are unchanged by S -> D^* S D (D diagonal unitary)."""
+    return np.abs(S), S * np.swapaxes(S, -1, -2)
+
+
+def test_build_S_matches_oracle(ctx):
+    P = W.config_problem("C1")
+    S, sig, U, V, info = ctx.build_S(P.grid, P.d, P.n, P.m, want_uv=True)
+    S_o, s_o, U_o, V_o = O.prony_S(P.grid, P.d, P.n, P.m)
+    assert np.max(np.abs(sig - s_o) / s_o) <= 1e-5
+    for l in range(P.d):
+        a, b = _phase_invariants(S[l])
+        ao, bo = _phase_invariants(S_o[l])
+        assert np.linalg.norm(a - ao) / np.linalg.norm(ao) <= 1e-5
+        assert np.linalg.norm(b - bo) / np.linalg.norm(bo) <= 1e-5
+        # phase-aligned comparison: D = diag(phase(v_o^H v_gpu))
+        ph = np.sum(V_o.conj() * V, axis=0)
+        ph = ph / np.abs(ph)
+        S_al = np.diag(ph) @ S[l] @ np.diag(ph.conj())
+        assert np.linalg.norm(S_al - S_o[l]) / np.linalg.norm(S_o[l]) <= 1e-5
+    # the canonical basis itself: columns of V and U orthonormal, U S_l Sigma V^H = U U^H T_l V V^H
+    assert np.allclose(V.conj().T @ V, np.eye(P.m), atol=1e-5)
+    assert np.allclose(U.conj().T @ U, np.eye(P.m), atol=1e-5)
+
+
+def test_solve_noisy_C2_forward_error_within_oracle(ctx):
+    P = W.config_problem("C2")
+    res = ctx.solve(P.grid, P.d, P.n, P.m)
+    t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
+    te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
+    te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
+    assert te_g <= 1.5 * te_o + 1e-6, (te_g, te_o, res.info)
+    assert ce_g <= 1.5 * ce_o + 1e-6, (ce_g, ce_o, res.info)
+
+
+def test_nonfinite_input_reports_enan(ctx):
+    from paper_2012_11430_gb300 import PRONY_ENAN
+    P = W.config_problem("C1")
+    g = P.grid.copy()
+    g.reshape(-1)[17] = np.nan
+    res = ctx.solve(g, P.d, P.n, P.m, allow=(PRONY_ENAN,))
+    assert res.info["status"] == PRONY_ENAN
+
+
+def test_invalid_arguments(ctx):
+    from paper_2012_11430_gb300 import PronyError
+    P = W.config_problem("C1")
+    with pytest.raises(PronyError):
+        ctx.solve(P.grid, 2, 15, 0)
+    with pytest.raises(PronyError):
+        ctx.solve(P.grid, 2, 15, 65)
+    with pytest.raises(ValueError):
+        ctx.solve(P.grid, 2, 14, 5)
+
+
+def test_batched_matches_single_and_oracle(ctx):
+    probs = W.batch_problems(count=12, n_lo=5, n_hi=12, snr_db=None)
+    outs, rc = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
+                                 [p.m for p in probs])
+    for p, r in zip(probs, outs):
+        t_o, c_o, _ = O.prony(p.grid, p.d, p.n, p.m)
+        _check_solution(r, t_o, c_o)
+        single = ctx.solve(p.grid, p.d, p.n, p.m)
+        assert np.max(W.torus_dist(single.t, r.t)) <= 1e-9

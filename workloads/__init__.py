@@ -58,23 +58,46 @@ def torus_dist(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def draw_nodes(rng: np.random.Generator, m: int, d: int, sep: float,
                restarts: int = 200, tries_per_node: int = 2000) -> np.ndarray:
-    """m nodes uniform on [0,1)^d, pairwise torus inf-distance >= sep.
+    """m nodes on [0,1)^d, pairwise torus inf-distance >= sep.
 
-    Sequential rejection sampling; a set that gets stuck is discarded and redrawn."""
+    Sequential rejection sampling (uniform nodes); a set that gets stuck is redrawn.  When
+    that keeps failing (dense packings), a jittered grid is used: g = floor(1/sep) cells per
+    axis, m distinct cells drawn at random, one node per cell at the cell centre plus a
+    uniform jitter of half-width (1/g - sep)/2, which keeps neighbours >= sep apart.
+    A separation no packing of m nodes can reach is lowered to 1/ceil(m^(1/d))."""
+    g_need = math.ceil(m ** (1.0 / d) - 1e-12)
+    sep = min(sep, 1.0 / g_need)
+    g = max(1, int(math.floor(1.0 / sep + 1e-12)))
+    if g ** d >= m and (g ** d) < 3 * m:
+        restarts = min(restarts, 3)           # dense packing: go to the jittered grid quickly
     for _ in range(restarts):
         out = np.empty((m, d))
         k = 0
-        tries = 0
-        while k < m and tries < tries_per_node * m:
-            tries += 1
-            cand = rng.random(d)
-            if k and np.min(np.max(torus_dist(out[:k], cand[None, :]), axis=1)) < sep:
-                continue
-            out[k] = cand
+        draws = 0
+        while k < m and draws < tries_per_node * m:
+            cand = rng.random((64, d))          # candidates tried in order, first valid one kept
+            draws += 64
+            if k:
+                ok = np.min(np.max(torus_dist(out[None, :k, :], cand[:, None, :]), axis=2), axis=1) >= sep
+                idx = np.flatnonzero(ok)
+                if idx.size == 0:
+                    continue
+                cand = cand[idx]
+            out[k] = cand[0]
             k += 1
         if k == m:
             return out
-    raise RuntimeError(f"cannot place {m} nodes at separation {sep} in d={d}")
+    if g ** d < m:
+        raise RuntimeError(f"cannot place {m} nodes at separation {sep} in d={d}")
+    cells = rng.choice(g ** d, size=m, replace=False)
+    half = max(0.0, (1.0 / g - sep) / 2.0)
+    out = np.empty((m, d))
+    for j, cidx in enumerate(cells):
+        rem = int(cidx)
+        for l in range(d - 1, -1, -1):
+            out[j, l] = ((rem % g) + 0.5) / g + rng.uniform(-half, half)
+            rem //= g
+    return np.mod(out, 1.0)
 
 
 def draw_coeffs(rng: np.random.Generator, m: int) -> np.ndarray:
