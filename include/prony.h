@@ -153,6 +153,24 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
                           const void* X_dev, int r, int L, int adjoint, int precision,
                           void* Y_dev, void* stream);
 
+/* Measurement support (not part of the method).  With profiling on, every Toeplitz
+ * block product launched by the solver is bracketed by CUDA events on the context
+ * stream; its algorithmic work is accumulated: flops = 8 * rows * N * width per live
+ * problem (one complex multiply-add = 8 real flops), bytes = samples read
+ * (8 (2n+2)^d) + X read (8 N width) + Y written (8 rows width) at complex64.
+ * launches counts every kernel the library launched (all kernels, all contexts)
+ * since the last reset. */
+typedef struct {
+  long long launches;        /* all library kernel launches since reset */
+  long long toeplitz_launches;
+  double toeplitz_ms;        /* summed CUDA-event durations of the Toeplitz launches */
+  double toeplitz_flops;     /* summed algorithmic flops of those launches */
+  double toeplitz_bytes;     /* summed algorithmic bytes of those launches */
+} prony_stats;
+
+int prony_set_profiling(prony_ctx* ctx, int enable);   /* also resets the statistics */
+int prony_get_stats(prony_ctx* ctx, prony_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,13 +56,53 @@ def complex_normal(seed: int, stream: int, index: int) -> complex:
     return complex(np.sqrt(-np.log(u0)) * np.exp(2j * np.pi * u1))
 
 
-def complex_normal_block(seed: int, stream: int, rows: int, cols: int) -> np.ndarray:
-    """rows x cols matrix, entry (i, j) drawn with counter index i*cols + j."""
+def complex_normal_block_scalar(seed: int, stream: int, rows: int, cols: int) -> np.ndarray:
+    """rows x cols matrix, entry (i, j) drawn with counter index i*cols + j (Python integers)."""
     out = np.empty((rows, cols), dtype=np.complex128)
     for i in range(rows):
         for j in range(cols):
             out[i, j] = complex_normal(seed, stream, i * cols + j)
     return out
+
+
+def _mulhilo64(a: np.ndarray, b: int):
+    """Full 64x64 -> 128-bit product of uint64 arrays by a constant, from 32-bit halves."""
+    m32 = np.uint64(0xFFFFFFFF)
+    s32 = np.uint64(32)
+    a0, a1 = a & m32, a >> s32
+    b0, b1 = np.uint64(b & 0xFFFFFFFF), np.uint64(b >> 32)
+    p00, p01, p10, p11 = a0 * b0, a0 * b1, a1 * b0, a1 * b1
+    mid = (p00 >> s32) + (p01 & m32) + (p10 & m32)
+    hi = p11 + (p01 >> s32) + (p10 >> s32) + (mid >> s32)
+    lo = (mid << s32) | (p00 & m32)
+    return hi, lo
+
+
+def philox4x64_10_vec(counter0: np.ndarray, key) -> tuple:
+    """Philox4x64-10 of counters (counter0, 0, 0, 0) for an array of counter0, numpy uint64."""
+    with np.errstate(over="ignore"):
+        c0 = counter0.astype(np.uint64)
+        c1 = np.zeros_like(c0)
+        c2 = np.zeros_like(c0)
+        c3 = np.zeros_like(c0)
+        k0, k1 = int(key[0]) & _MASK, int(key[1]) & _MASK
+        for _ in range(10):
+            hi0, lo0 = _mulhilo64(c0, _M0)
+            hi1, lo1 = _mulhilo64(c2, _M1)
+            c0, c1, c2, c3 = hi1 ^ c1 ^ np.uint64(k0), lo1, hi0 ^ c3 ^ np.uint64(k1), lo0
+            k0 = (k0 + _W0) & _MASK
+            k1 = (k1 + _W1) & _MASK
+    return c0, c1, c2, c3
+
+
+def complex_normal_block(seed: int, stream: int, rows: int, cols: int) -> np.ndarray:
+    """rows x cols matrix, entry (i, j) drawn with counter index i*cols + j."""
+    idx = np.arange(rows * cols, dtype=np.uint64)
+    w0, w1, _, _ = philox4x64_10_vec(idx, (seed, stream))
+    u0 = ((w0 >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+    u1 = ((w1 >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+    z = np.sqrt(-np.log(u0)) * np.exp(2j * np.pi * u1)
+    return z.reshape(rows, cols)
 
 
 def draw_mu(seed: int, d: int) -> np.ndarray:

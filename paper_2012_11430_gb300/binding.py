@@ -22,8 +22,18 @@ PRECISIONS = {"fp32": PRONY_FP32, "bf16x3": PRONY_BF16X3, "tf32x3": PRONY_TF32X3
 EXPORTS = [
     "prony_default_opts", "prony_status_string", "prony_last_error", "prony_ctx_create", "prony_ctx_destroy",
     "prony_solve", "prony_build_S", "prony_eval", "prony_solve_batched", "prony_solve_batched_dev",
-    "prony_expsum_fwd_dev", "prony_expsum_bwd_dev", "prony_toeplitz_mm_dev",
+    "prony_expsum_fwd_dev", "prony_expsum_bwd_dev", "prony_toeplitz_mm_dev", "prony_set_profiling",
+    "prony_get_stats",
 ]
+
+
+class PronyStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("toeplitz_launches", ctypes.c_longlong),
+                ("toeplitz_ms", ctypes.c_double), ("toeplitz_flops", ctypes.c_double),
+                ("toeplitz_bytes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PronyOpts(ctypes.Structure):
@@ -75,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.prony_expsum_fwd_dev.argtypes = [P, P, P, I, I, P, P, P, P]
     lib.prony_expsum_bwd_dev.argtypes = [P, P, P, I, I, P, P, P, P, P, P]
     lib.prony_toeplitz_mm_dev.argtypes = [P, P, I, I, P, I, I, I, I, P, P]
+    lib.prony_set_profiling.argtypes = [P, I]
+    lib.prony_get_stats.argtypes = [P, ctypes.POINTER(PronyStats)]
     for name in EXPORTS:
         if name not in ("prony_default_opts", "prony_status_string", "prony_last_error"):
             getattr(lib, name).restype = I
@@ -148,6 +160,14 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_profiling(self, enable: bool = True):
+        _check(self._lib.prony_set_profiling(self._h, int(enable)), "prony_set_profiling")
+
+    def stats(self) -> dict:
+        s = PronyStats()
+        _check(self._lib.prony_get_stats(self._h, ctypes.byref(s)), "prony_get_stats")
+        return s.as_dict()
 
     # ---------------------------------------------------------------- host-pointer calls
     def solve(self, grid, d: int, n: int, m: int, opts: PronyOpts | None = None,

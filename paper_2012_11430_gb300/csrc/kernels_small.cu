@@ -808,7 +808,7 @@ __global__ void k_reset_done(Dev D) {
 
 }  // namespace
 
-void launch_reset_done(const Dev& D, cudaStream_t s) { k_reset_done<<<(D.nprob + 127) / 128, 128, 0, s>>>(D); }
+void launch_reset_done(const Dev& D, cudaStream_t s) { note_launch(); k_reset_done<<<(D.nprob + 127) / 128, 128, 0, s>>>(D); }
 
 void launch_chol(const Dev& D, int wsel, int target, int mode, double tol, int rank_mode, cudaStream_t s) {
   static bool attr = false;
@@ -817,6 +817,7 @@ void launch_chol(const Dev& D, int wsel, int target, int mode, double tol, int r
     attr = true;
   }
   size_t sm = sizeof(float2) * D.L.LDR * D.L.LDR;
+  note_launch();
   k_chol<<<D.nprob, 256, sm, s>>>(D, wsel, target, mode, tol, rank_mode);
 }
 
@@ -828,10 +829,11 @@ void launch_svd_S(const Dev& D, cudaStream_t s) {
     attr = true;
   }
   size_t sm = sizeof(double2) * ((size_t)D.L.LDM * D.L.LDR + (size_t)D.L.LDM * D.L.LDM);
+  note_launch();
   k_svd_S<<<D.nprob, 256, sm, s>>>(D);
 }
 
-void launch_canon(const Dev& D, cudaStream_t s) { k_canon<<<D.nprob, 256, 0, s>>>(D); }
+void launch_canon(const Dev& D, cudaStream_t s) { note_launch(); k_canon<<<D.nprob, 256, 0, s>>>(D); }
 
 void launch_eig_t(const Dev& D, unsigned long long seed, cudaStream_t s) {
   static bool attr = false;
@@ -840,6 +842,7 @@ void launch_eig_t(const Dev& D, unsigned long long seed, cudaStream_t s) {
     attr = true;
   }
   size_t sm = sizeof(double2) * 3 * D.L.LDM * D.L.LDM;
+  note_launch();
   k_eig_t<<<D.nprob, 256, sm, s>>>(D, seed);
 }
 
@@ -850,9 +853,11 @@ void launch_solve_c(const Dev& D, cudaStream_t s) {
     cudaFuncSetAttribute(k_solve_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
+  note_launch();
   k_solve_c<<<D.nprob, 256, sm, s>>>(D);
 }
 
 void launch_check(const Dev& D, double tol_power, int max_iter, int* all_done, cudaStream_t s) {
+  note_launch();
   k_check<<<(D.nprob + 127) / 128, 128, 0, s>>>(D, tol_power, max_iter, all_done);
 }

@@ -526,18 +526,22 @@ inline int blocks_for(long long n, int per) { return (int)std::min<long long>((n
 #include <algorithm>
 
 void launch_prep(const Dev& D, cudaStream_t s) {
+  note_launch();
   k_state_init<<<(D.nprob + 127) / 128, 128, 0, s>>>(D);
   dim3 g(std::max(1, std::min((D.maxGd + 255) / 256, 64)), D.nprob);
+  note_launch();
   k_prep<<<g, 256, 0, s>>>(D);
 }
 
 void launch_init_v0(const Dev& D, unsigned long long seed, cudaStream_t s) {
   dim3 g(std::max(1, std::min((D.maxN * D.maxR0 + 255) / 256, 256)), D.nprob);
+  note_launch();
   k_init_v0<<<g, 256, 0, s>>>(D, seed);
 }
 
 void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_t s) {
   dim3 g(std::max<int>(1, std::min<int>((int)((bytes / 4 + 255) / 256), 32)), D.nprob);
+  note_launch();
   k_zero_small<<<g, 256, 0, s>>>(D, off, bytes);
 }
 
@@ -550,6 +554,7 @@ void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshif
     attr = true;
   }
   dim3 g((D.maxN + GRAM_CHUNK - 1) / GRAM_CHUNK, D.nprob);
+  note_launch();
   k_gram<<<g, 256, sm, s>>>(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld);
 }
 
@@ -562,11 +567,13 @@ void launch_apply(const Dev& D, int xbuf, int xw, int outw, long long m_off, int
     attr = true;
   }
   dim3 g((D.maxN + APPLY_ROWS - 1) / APPLY_ROWS, D.nprob);
+  note_launch();
   k_apply<<<g, 256, sm, s>>>(D, xbuf, xw, outw, m_off, m_double, zbuf, outbuf, norm_only);
 }
 
 void launch_argmax(const Dev& D, int buf, cudaStream_t s) {
   dim3 g(std::max(1, std::min((D.maxN + 255) / 256, 64)), D.nprob);
+  note_launch();
   k_argmax<<<g, 256, 0, s>>>(D, buf);
 }
 
@@ -578,14 +585,17 @@ void launch_rhs(const Dev& D, int resid, cudaStream_t s) {
     attr = true;
   }
   dim3 g((D.maxN + RHS_ROWS - 1) / RHS_ROWS, D.nprob);
+  note_launch();
   k_rhs<<<g, RHS_ROWS, sm, s>>>(D, resid);
 }
 
 void launch_gather_out(const Dev& D, double* t_out, double2* c_out, cudaStream_t s) {
+  note_launch();
   k_gather_out<<<D.nprob, 128, 0, s>>>(D, t_out, c_out);
 }
 
 void launch_copy_cols(const Dev& D, int buf, int w_sel, double2* out, cudaStream_t s) {
+  note_launch();
   k_copy_cols<<<64, 256, 0, s>>>(D, buf, w_sel, out);
 }
 
@@ -597,20 +607,24 @@ static Box make_box(int d, const int* lo, const int* len) {
 
 void launch_expsum_fwd(const double* t, const float2* c, int m, int d, const int* lo, const int* len, long long K,
                        float2* f, cudaStream_t s) {
+  note_launch();
   k_expsum_fwd<<<blocks_for(K, 256), 256, 0, s>>>(t, c, m, d, make_box(d, lo, len), K, f);
 }
 
 void launch_expsum_bwd(const double* t, const float2* c, int m, int d, const int* lo, const int* len, long long K,
                        const float2* g, double* acc, cudaStream_t s) {
   int nb = std::min(blocks_for(K, 256), 4 * 152);
+  note_launch();
   k_expsum_bwd<<<nb, 256, 0, s>>>(t, c, m, d, make_box(d, lo, len), K, g, acc);
 }
 
 void launch_expsum_bwd_finish(const double* acc, int m, int d, double* gt, float2* gc, cudaStream_t s) {
+  note_launch();
   k_expsum_bwd_finish<<<1, 64, 0, s>>>(acc, m, d, gt, gc);
 }
 
 void launch_eval_points(const double* t, const double2* c, int m, int d, const int* k, int K, double2* f,
                         cudaStream_t s) {
+  note_launch();
   k_eval_points<<<blocks_for(K, 128), 128, 0, s>>>(t, c, m, d, k, K, f);
 }

@@ -168,6 +168,7 @@ template <int TN>
 void run_simt(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int xbuf, int wsel, int ybuf, int y_ext,
               cudaStream_t s) {
   constexpr int KB = TN > 5 ? 16 : 32;   // keep the static tiles under 48 KB
+  note_launch();
   k_toeplitz_simt<TN, KB><<<njobs, 256, 0, s>>>(D, jobs, adjoint, xbuf, wsel, ybuf, y_ext);
 }
 
@@ -175,6 +176,7 @@ void run_simt(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int
 
 void launch_zero_buf(const Dev& D, int buf, int wsel, int y_ext, cudaStream_t s) {
   dim3 g(64, D.nprob);
+  note_launch();
   k_zero_buf<<<g, 256, 0, s>>>(D, buf, wsel, y_ext);
 }
 

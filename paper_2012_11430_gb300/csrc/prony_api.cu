@@ -18,6 +18,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <atomic>
 
 namespace {
 
@@ -54,12 +55,23 @@ int ensure(DBuf& b, size_t bytes) {
 
 }  // namespace
 
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 struct prony_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   DBuf grid64, gF, gH, V, U, B1, B2, Y, small, P, st, jobs, flag, tout, cout, misc, misc2, misc3;
   int* h_flag = nullptr;            // pinned
   std::vector<ProbState> h_st;
+  // profiling of the Toeplitz launches
+  bool prof = false;
+  struct TRec { int ev; int iter; int ext; int wsel; };
+  std::vector<TRec> trecs;
+  std::vector<cudaEvent_t> events;  // pool, two per record
+  std::vector<std::vector<ProbState>> snaps;
+  prony_stats stats{};
+  long long launch_base = 0;
 };
 
 namespace {
@@ -222,21 +234,48 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   const int max_iter = o.max_iter > 0 ? o.max_iter : 30;
   const double tol_drop = 1e-3;
 
+  // Toeplitz launch, bracketed by events when profiling
+  auto toeplitz = [&](int iter, int ext) -> int {
+    int ev = -1;
+    if (ctx->prof) {
+      ev = (int)ctx->trecs.size() * 2;
+      while ((int)ctx->events.size() < ev + 2) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->events.push_back(e);
+      }
+      ctx->trecs.push_back({ev, iter, ext, ext ? W_V : W_U});
+      CK(cudaEventRecord(ctx->events[ev], s));
+    }
+    if (ext) launch_toeplitz(D, B.jobs_ext, B.njobs_ext, B.nks, 0, BUF_V, W_V, BUF_Y, 1, B.maxw, prec, s);
+    else launch_toeplitz(D, B.jobs_in, B.njobs_in, B.nks, 1, BUF_U, W_U, BUF_B2, 0, B.maxw, prec, s);
+    if (ctx->prof) CK(cudaEventRecord(ctx->events[ev + 1], s));
+    return PRONY_OK;
+  };
+  int rc;
+  if (ctx->prof) {
+    ctx->trecs.clear();
+    ctx->snaps.clear();
+  }
   launch_prep(D, s);
   launch_init_v0(D, o.seed, s);
   tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
-  launch_toeplitz(D, B.jobs_ext, B.njobs_ext, B.nks, 0, BUF_V, W_V, BUF_Y, 1, B.maxw, prec, s);
+  if ((rc = toeplitz(0, 1))) return rc;
+  if (ctx->prof) {
+    ctx->snaps.emplace_back(D.nprob);
+    CK(cudaMemcpyAsync(ctx->snaps.back().data(), D.st, sizeof(ProbState) * D.nprob, cudaMemcpyDeviceToHost, s));
+  }
   int* dflag = (int*)ctx->flag.p;
   for (int it = 1; it <= max_iter; ++it) {
     // U = qr(T V_{k-1})  (rows I_n of Y)
     tall_qr(B, BUF_Y, W_V, W_U, QR_DROP, tol_drop, 0, BUF_U, s);
     // Vbar = T^* U
-    launch_toeplitz(D, B.jobs_in, B.njobs_in, B.nks, 1, BUF_U, W_U, BUF_B2, 0, B.maxw, prec, s);
+    if ((rc = toeplitz(it, 0))) return rc;
     // V = qr(Vbar), column pivoting and rank on the first iteration
     if (it == 1) tall_qr(B, BUF_B2, W_U, W_V, QR_RANK, tol_rank, o.rank_mode, BUF_V, s);
     else tall_qr(B, BUF_B2, W_U, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
     // Y = T V over the box {0..n+1}^d
-    launch_toeplitz(D, B.jobs_ext, B.njobs_ext, B.nks, 0, BUF_V, W_V, BUF_Y, 1, B.maxw, prec, s);
+    if ((rc = toeplitz(it, 1))) return rc;
     // Q = U^* (T V), ||T V - U Q||_F
     launch_zero_small(D, D.L.q, 16LL * D.L.LDR * D.L.LDM, s);
     launch_gram(D, BUF_U, -1, W_U, BUF_Y, -1, W_V, D.L.q, D.L.LDM, s);
@@ -244,8 +283,35 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
     launch_check(D, tol_power, max_iter, dflag, s);
     CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (ctx->prof) {
+      ctx->snaps.emplace_back(D.nprob);
+      CK(cudaMemcpyAsync(ctx->snaps.back().data(), D.st, sizeof(ProbState) * D.nprob, cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaStreamSynchronize(s));
     if (*ctx->h_flag != 0) break;
+  }
+  if (ctx->prof) {
+    // accumulate durations and algorithmic work of the Toeplitz launches of this solve
+    CK(cudaStreamSynchronize(s));
+    for (const auto& r : ctx->trecs) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->events[r.ev], ctx->events[r.ev + 1]));
+      const auto& before = ctx->snaps[r.iter > 0 ? r.iter - 1 : 0];
+      const auto& after = ctx->snaps[r.iter];
+      double fl = 0.0, by = 0.0;
+      for (int p = 0; p < D.nprob; ++p) {
+        if (r.iter > 0 && before[p].done) continue;
+        const ProbDesc& q = B.P[p];
+        int w = r.iter == 0 ? q.r0 : (r.ext ? after[p].wv : after[p].wu);
+        double rows = r.ext ? q.Next : q.N;
+        fl += 8.0 * rows * q.N * w;
+        by += 8.0 * q.Gd + 8.0 * q.N * w + 8.0 * rows * w;
+      }
+      ctx->stats.toeplitz_launches += 1;
+      ctx->stats.toeplitz_ms += ms;
+      ctx->stats.toeplitz_flops += fl;
+      ctx->stats.toeplitz_bytes += by;
+    }
   }
   // finishing steps run for every problem that has not failed
   launch_reset_done(D, s);
@@ -376,8 +442,24 @@ int prony_ctx_destroy(prony_ctx* c) {
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->h_flag) cudaFreeHost(c->h_flag);
+  for (cudaEvent_t e : c->events) cudaEventDestroy(e);
   cudaStreamDestroy(c->stream);
   delete c;
+  return PRONY_OK;
+}
+
+int prony_set_profiling(prony_ctx* c, int enable) {
+  if (!c) return PRONY_EINVAL;
+  c->prof = enable != 0;
+  c->stats = prony_stats{};
+  c->launch_base = g_launches.load();
+  return PRONY_OK;
+}
+
+int prony_get_stats(prony_ctx* c, prony_stats* out) {
+  if (!c || !out) return PRONY_EINVAL;
+  *out = c->stats;
+  out->launches = g_launches.load() - c->launch_base;
   return PRONY_OK;
 }
 

@@ -163,4 +163,5 @@ def test_batched_matches_single_and_oracle(ctx):
         t_o, c_o, _ = O.prony(p.grid, p.d, p.n, p.m)
         _check_solution(r, t_o, c_o)
         single = ctx.solve(p.grid, p.d, p.n, p.m)
-        assert np.max(W.torus_dist(single.t, r.t)) <= 1e-9
+        # a batch splits the K dimension differently than a single problem: FP32 rounding differs
+        assert np.max(W.torus_dist(single.t, r.t)) <= 1e-6

@@ -324,3 +324,13 @@ def test_pins_catch_planted_mistakes(monkeypatch, mistake):
     t, c, _ = O.prony(P.grid, 2, 9, 4)
     t_err, c_err = W.match_to_truth(t, c, P.t, P.c)
     assert t_err > 1e-6 or c_err > 1e-6
+
+
+def test_vectorised_philox_matches_scalar():
+    a = philox.complex_normal_block(99, philox.STREAM_V0, 7, 5)
+    b = philox.complex_normal_block_scalar(99, philox.STREAM_V0, 7, 5)
+    assert np.array_equal(a, b)
+    big = np.array([2 ** 63 + 12345, 2 ** 64 - 1], dtype=np.uint64)
+    got = philox.philox4x64_10_vec(big, (3, 4))
+    for i, c in enumerate([2 ** 63 + 12345, 2 ** 64 - 1]):
+        assert tuple(int(w[i]) for w in got) == philox.philox4x64_10((c, 0, 0, 0), (3, 4))
