@@ -153,6 +153,26 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
                           const void* X_dev, int r, int L, int adjoint, int precision,
                           void* Y_dev, void* stream);
 
+/* Allocation-free variant of prony_toeplitz_mm_dev (FP32 path).  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library allocate
+ * device memory -- programs whose device memory is fixed up front by their own
+ * allocator or budget, and latency-critical loops where cudaMalloc/cudaFree may
+ * synchronise the device.  It takes no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine: its scratch (problem descriptor, job list, complex64
+ * copies of the grid) lives in one fixed file-scope device array of
+ * PRONY_STATIC_SCRATCH_BYTES that every GPU loading the library holds until exit.
+ * Arguments as prony_toeplitz_mm_dev; it runs on the current device, is asynchronous
+ * on `stream` (results are ready when the stream reaches that point) and returns
+ * PRONY_EINVAL (message: prony_last_error) when (2n+2)^d > PRONY_STATIC_MAX_GRID.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
+ * share the array and each rewrites what it reads; calls that overlap on the GPU
+ * (e.g. on two streams at once) race on it. */
+#define PRONY_STATIC_MAX_GRID (1 << 20)
+#define PRONY_STATIC_SCRATCH_BYTES (512 + 65536 * 16 + 16 * PRONY_STATIC_MAX_GRID)   /* 17 MiB */
+int prony_toeplitz_mm_static(const prony_c128* grid_dev, int d, int n, const void* X_dev, int r, int L,
+                             int adjoint, void* Y_dev, void* stream);
+
 /* Measurement support (not part of the method).  With profiling on, every Toeplitz
  * block product launched by the solver is bracketed by CUDA events on the context
  * stream; its algorithmic work is accumulated: flops = 8 * rows * N * width per live

@@ -23,7 +23,7 @@ EXPORTS = [
     "prony_default_opts", "prony_status_string", "prony_last_error", "prony_ctx_create", "prony_ctx_destroy",
     "prony_solve", "prony_build_S", "prony_eval", "prony_solve_batched", "prony_solve_batched_dev",
     "prony_expsum_fwd_dev", "prony_expsum_bwd_dev", "prony_toeplitz_mm_dev", "prony_set_profiling",
-    "prony_get_stats",
+    "prony_get_stats", "prony_toeplitz_mm_static",
 ]
 
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
     lib.prony_expsum_fwd_dev.argtypes = [P, P, P, I, I, P, P, P, P]
     lib.prony_expsum_bwd_dev.argtypes = [P, P, P, I, I, P, P, P, P, P, P]
     lib.prony_toeplitz_mm_dev.argtypes = [P, P, I, I, P, I, I, I, I, P, P]
+    lib.prony_toeplitz_mm_static.argtypes = [P, I, I, P, I, I, I, P, P]
     lib.prony_set_profiling.argtypes = [P, I]
     lib.prony_get_stats.argtypes = [P, ctypes.POINTER(PronyStats)]
     for name in EXPORTS:
@@ -104,6 +105,18 @@ def last_error() -> str:
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def toeplitz_mm_static(grid_dev, d: int, n: int, X_dev, L: int, adjoint: int, Y_dev, stream: int = 0) -> int:
+    """Allocation-free Toeplitz product on the current device (asynchronous on `stream`).
+
+    For callers that cannot let the library allocate device memory; it needs no Context.
+    Scratch lives in a fixed device array shared by all calls (overlapping calls race)."""
+    r = X_dev.shape[0] if X_dev.dim() == 2 else 1
+    rc = load().prony_toeplitz_mm_static(ctypes.c_void_p(grid_dev.data_ptr()), d, n,
+                                         ctypes.c_void_p(X_dev.data_ptr()), r, L, adjoint,
+                                         ctypes.c_void_p(Y_dev.data_ptr()), ctypes.c_void_p(stream))
+    return _check(rc, "prony_toeplitz_mm_static")
 
 
 def default_opts(**kw) -> PronyOpts:

@@ -188,6 +188,8 @@ __device__ inline uint64_t frac64(double t) {
 // Every kernel launch of the library goes through a launcher that calls note_launch()
 // (a process-wide counter, read with prony_get_stats).
 void note_launch();
+// Message returned by prony_last_error() on this host thread.
+void set_last_error(const char* msg);
 
 enum WidthSel { W_R0 = 0, W_U = 1, W_V = 2, W_M = 3, W_IN = 4, W_OUT = 5 };
 enum BufSel { BUF_V = 0, BUF_U = 1, BUF_B1 = 2, BUF_B2 = 3, BUF_Y = 4 };

@@ -57,6 +57,7 @@ int ensure(DBuf& b, size_t bytes) {
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
 struct prony_ctx {
   int device = 0;
