@@ -11,6 +11,7 @@
 //           (rows k + e_l) of Eq. generateSl at once
 //   small   per-problem FP64 / FP32 workspace for the r0 x r0 and m x m steps
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -223,6 +224,14 @@ struct ToeplitzJob { int prob, mt, ks, nks; };
 void launch_zero_buf(const Dev& D, int buf, int wsel, int y_ext, cudaStream_t s);
 void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int xbuf, int wsel,
                      int ybuf, int y_ext, int maxw, int precision, cudaStream_t s);
+
+// kernels_tc.cu (tensor-core Toeplitz products, split BF16 planes)
+int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows, int ntbox);
+size_t tc_smem_bytes(int npl, int ntbox, int stages, int win_cap);
+void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int npl, int ntbox, int kpitch, cudaStream_t s);
+void launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel, int ybuf,
+                        int y_ext, int npl, int ntbox, int kpitch, int win_cap, int stages, const CUtensorMap& map,
+                        int* err, cudaStream_t s);
 
 // kernels_small.cu
 enum QrMode { QR_PLAIN = 0, QR_DROP = 1, QR_RANK = 2 };

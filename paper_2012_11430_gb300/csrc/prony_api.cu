@@ -63,6 +63,7 @@ struct prony_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   DBuf grid64, gF, gH, V, U, B1, B2, Y, small, P, st, jobs, flag, tout, cout, misc, misc2, misc3;
+  DBuf xb, tcjobs, tcerr;           // tensor-core path: B' planes, 128-row job list, error flag
   int* h_flag = nullptr;            // pinned
   std::vector<ProbState> h_st;
   // profiling of the Toeplitz launches
@@ -101,6 +102,17 @@ long long ipow(long long b, int e) {
   return r;
 }
 
+// Tensor-core configuration of a batch (split BF16 planes).
+struct TcConf {
+  bool on = false;
+  int npl = 3, ntbox = 16, kpitch = 64, stages = 2, win_cap = 0, nks = 1;
+  int njobs_ext = 0, njobs_in = 0;
+  ToeplitzJob* jobs_ext = nullptr;
+  ToeplitzJob* jobs_in = nullptr;
+  CUtensorMap map;
+  int* err = nullptr;
+};
+
 struct Batch {
   std::vector<ProbDesc> P;
   Dev D{};
@@ -108,7 +120,121 @@ struct Batch {
   ToeplitzJob* jobs_ext = nullptr;
   ToeplitzJob* jobs_in = nullptr;
   int maxw = 0;
+  TcConf tc;
 };
+
+bool is_tc(int prec) { return prec == PRONY_BF16X3 || prec == PRONY_BF16X2; }
+
+// host copies of the device index maps (window sizing)
+int h_grid_of_row(int row, int L, const ProbDesc& p) {
+  int g = 0, mul = 1, rem = row;
+  for (int l = p.d - 1; l >= 0; --l) {
+    g += (rem % L + p.n) * mul;
+    rem /= L;
+    mul *= p.G;
+  }
+  return g;
+}
+int h_grid_of_h(int h, const ProbDesc& p) {
+  int g = 0, mul = 1, rem = h;
+  for (int l = p.d - 1; l >= 0; --l) {
+    g += (rem % (p.n + 1)) * mul;
+    rem /= (p.n + 1);
+    mul *= p.G;
+  }
+  return g;
+}
+// largest window (float2 entries) over the CTAs of a problem for a K split into nks ranges
+int max_window(const ProbDesc& p, int L, int nks) {
+  const int rows = ipow(L, p.d) > 0 ? (int)ipow(L, p.d) : 0;
+  const int nc = (p.N + 31) / 32, cper = (nc + nks - 1) / nks;
+  int mx = 0;
+  for (int r0 = 0; r0 < rows; r0 += 128) {
+    int last = std::min(rows, r0 + 128) - 1;
+    for (int ks = 0; ks < nks; ++ks) {
+      int cb = ks * cper, ce = std::min(nc, cb + cper);
+      if (cb >= ce) continue;
+      int hf = 32 * cb, hl = std::min(p.N, 32 * ce) - 1;
+      int lo = (h_grid_of_row(r0, L, p) - h_grid_of_h(hl, p)) & ~1;
+      int hi = h_grid_of_row(last, L, p) - h_grid_of_h(hf, p);
+      mx = std::max(mx, ((hi - lo + 1) + 1) & ~1);
+    }
+  }
+  return mx;
+}
+
+int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
+  TcConf& T = B.tc;
+  T.on = true;
+  T.npl = prec == PRONY_BF16X3 ? 3 : 2;
+  T.ntbox = ((2 * maxw + 15) / 16) * 16;
+  int maxnc = 0, tiles_ext = 0, tiles_in = 0;
+  for (const auto& p : B.P) {
+    maxnc = std::max(maxnc, (p.N + 31) / 32);
+    tiles_ext += (p.Next + 127) / 128;
+    tiles_in += (p.N + 127) / 128;
+  }
+  T.kpitch = 64 * maxnc;
+  const size_t stage = (size_t)T.npl * T.ntbox * 128;
+  const size_t avail = 227 * 1024 - 2048;
+  T.stages = T.npl == 3 ? 2 : 3;
+  while (T.stages > 1 && 1024 + T.stages * stage + 8 * 2048 > avail) --T.stages;
+  T.win_cap = (int)((avail - 1024 - T.stages * stage) / 8) & ~1;
+  if (T.win_cap < 256) return PRONY_EINVAL;
+  // split K: enough CTAs to fill the GPU, and every window within the shared-memory capacity
+  int nks = std::max(1, std::min(16, (2 * 152 + tiles_in - 1) / std::max(1, tiles_in)));
+  for (;; ++nks) {
+    bool fits = true;
+    for (const auto& p : B.P) {
+      nks = std::min(nks, std::max(1, (p.N + 31) / 32));
+      if (max_window(p, p.n + 2, nks) > T.win_cap || max_window(p, p.n + 1, nks) > T.win_cap) fits = false;
+    }
+    if (fits || nks >= maxnc) break;
+  }
+  T.nks = nks;
+  std::vector<ToeplitzJob> jobs;
+  for (int i = 0; i < (int)B.P.size(); ++i)
+    for (int mt = 0; mt < (B.P[i].Next + 127) / 128; ++mt)
+      for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
+  T.njobs_ext = (int)jobs.size();
+  for (int i = 0; i < (int)B.P.size(); ++i)
+    for (int mt = 0; mt < (B.P[i].N + 127) / 128; ++mt)
+      for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
+  T.njobs_in = (int)jobs.size() - T.njobs_ext;
+  int rc;
+  if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
+  const long long rows = (long long)B.P.size() * T.npl * T.ntbox;
+  if ((rc = ensure(ctx->xb, (size_t)rows * T.kpitch * 2))) return rc;
+  if ((rc = ensure(ctx->tcerr, 256))) return rc;
+  CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->tcerr.p, 0, sizeof(int), ctx->stream));
+  T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
+  T.jobs_in = T.jobs_ext + T.njobs_ext;
+  T.err = (int*)ctx->tcerr.p;
+  if (encode_xb_map(&T.map, ctx->xb.p, T.kpitch, rows, T.ntbox)) {
+    g_err = "cuTensorMapEncodeTiled failed for the B' planes";
+    return PRONY_ECUDA;
+  }
+  return PRONY_OK;
+}
+
+// One Toeplitz block product for every live problem of the batch.
+int check_tc_error(prony_ctx* ctx, const Batch& B);
+
+void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int xbuf, int wsel, int ybuf, int prec,
+                      cudaStream_t s, int adjoint = -1) {
+  if (adjoint < 0) adjoint = ext ? 0 : 1;
+  if (B.tc.on) {
+    const TcConf& T = B.tc;
+    launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.npl, T.ntbox, T.kpitch, s);
+    launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, T.nks, adjoint, wsel, ybuf,
+                       ext, T.npl, T.ntbox, T.kpitch, T.win_cap, T.stages, T.map, T.err, s);
+  } else {
+    launch_toeplitz(D, ext ? B.jobs_ext : B.jobs_in, ext ? B.njobs_ext : B.njobs_in, B.nks, adjoint, xbuf, wsel, ybuf,
+                    ext, B.maxw, prec, s);
+  }
+}
 
 // Lay out a batch in the context workspace.  Grid samples are copied from `src`
 // (host or device, per problem sample_off) into the packed grid64 buffer.
@@ -166,8 +292,8 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
 
   int rc;
   if ((rc = ensure(ctx->grid64, sizeof(double2) * goff))) return rc;
-  if ((rc = ensure(ctx->gF, sizeof(float2) * goff))) return rc;
-  if ((rc = ensure(ctx->gH, sizeof(float2) * goff))) return rc;
+  if ((rc = ensure(ctx->gF, sizeof(float2) * (goff + 64)))) return rc;   // window copies may read past the end
+  if ((rc = ensure(ctx->gH, sizeof(float2) * (goff + 64)))) return rc;
   if ((rc = ensure(ctx->V, sizeof(float2) * xoff))) return rc;
   if ((rc = ensure(ctx->U, sizeof(float2) * xoff))) return rc;
   if ((rc = ensure(ctx->B1, sizeof(float2) * xoff))) return rc;
@@ -204,6 +330,7 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
   D.L = L;
   B.jobs_ext = (ToeplitzJob*)ctx->jobs.p;
   B.jobs_in = B.jobs_ext + B.njobs_ext;
+  if (is_tc(o.precision)) return setup_tc(ctx, B, o.precision, maxR0);
   return PRONY_OK;
 }
 
@@ -248,8 +375,8 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
       ctx->trecs.push_back({ev, iter, ext, ext ? W_V : W_U});
       CK(cudaEventRecord(ctx->events[ev], s));
     }
-    if (ext) launch_toeplitz(D, B.jobs_ext, B.njobs_ext, B.nks, 0, BUF_V, W_V, BUF_Y, 1, B.maxw, prec, s);
-    else launch_toeplitz(D, B.jobs_in, B.njobs_in, B.nks, 1, BUF_U, W_U, BUF_B2, 0, B.maxw, prec, s);
+    if (ext) toeplitz_product(ctx, B, D, 1, BUF_V, W_V, BUF_Y, prec, s);
+    else toeplitz_product(ctx, B, D, 0, BUF_U, W_U, BUF_B2, prec, s);
     if (ctx->prof) CK(cudaEventRecord(ctx->events[ev + 1], s));
     return PRONY_OK;
   };
@@ -336,7 +463,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   launch_solve_c(D, s);
   launch_rhs(D, 1, s);
   CK(cudaGetLastError());
-  return PRONY_OK;
+  return check_tc_error(ctx, B);
 }
 
 int read_states(prony_ctx* ctx, const Batch& B, prony_info* infos, int* worst) {
@@ -372,7 +499,20 @@ prony_opts resolve_opts(const prony_opts* o) {
 }
 
 int check_precision(int prec) {
-  return prec == PRONY_FP32 ? PRONY_OK : PRONY_EINVAL;
+  return (prec == PRONY_FP32 || is_tc(prec)) ? PRONY_OK : PRONY_EINVAL;
+}
+
+// Error flag of the tensor-core kernels (bounded waits that gave up, window overflow).
+int check_tc_error(prony_ctx* ctx, const Batch& B) {
+  if (!B.tc.on) return PRONY_OK;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, B.tc.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    g_err = "tensor-core Toeplitz kernel reported error " + std::to_string(h);
+    return PRONY_ECUDA;
+  }
+  return PRONY_OK;
 }
 
 // Copy problem grids to the packed device buffer (host or device source).
@@ -672,10 +812,11 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
   std::vector<HostProb> hp = {{d, n, 1, 0, 0}};
-  if (std::pow((double)(n + 1), d) > 2.0e8) return PRONY_EINVAL;
+  if (std::pow((double)(n + 1), d) > 2.0e8 || r > (long long)ipow(n + 1, d)) return PRONY_EINVAL;
   prony_opts o;
   prony_default_opts(&o);
   o.oversample_p = r - 1;
+  o.precision = precision;
   Batch B;
   // ensure the stream order: ctx work after the caller's stream
   if (stream) {
@@ -697,11 +838,10 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
   D.Y = (float2*)Y_dev;
   D.B2 = (float2*)Y_dev;
   const int y_ext = (L == n + 2);
-  launch_toeplitz(D, y_ext ? B.jobs_ext : B.jobs_in, y_ext ? B.njobs_ext : B.njobs_in, B.nks, adjoint, BUF_V, W_R0,
-                  y_ext ? BUF_Y : BUF_B2, y_ext, r, precision, ctx->stream);
+  toeplitz_product(ctx, B, D, y_ext, BUF_V, W_R0, y_ext ? BUF_Y : BUF_B2, precision, ctx->stream, adjoint);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
-  return PRONY_OK;
+  return check_tc_error(ctx, B);
 }
 
 }  // extern "C"

@@ -165,3 +165,74 @@ def test_batched_matches_single_and_oracle(ctx):
         single = ctx.solve(p.grid, p.d, p.n, p.m)
         # a batch splits the K dimension differently than a single problem: FP32 rounding differs
         assert np.max(W.torus_dist(single.t, r.t)) <= 1e-6
+
+
+# ----------------------------------------------------------------------------- tensor-core path
+# Split-BF16 products: three planes represent an FP32 value exactly; the three dropped products
+# (relative 2^-24, 2^-24, 2^-32) add ~3 u32 per term; two planes round each operand to 16 bits
+# (x = x0 + x1 with |error| <= 2^-17 |x|) and drop x1 y1, ~3 * 2^-16 per term.
+TC_REL = {"bf16x3": lambda N: (2 * N + 32) * U32, "bf16x2": lambda N: (2 * N + 16) * U32 + 3 * 2.0 ** -16}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("d,n,r,L_ext,adjoint", [
+    (1, 7, 3, 1, 0), (1, 40, 5, 0, 1), (2, 15, 10, 1, 0), (2, 15, 10, 0, 1), (2, 9, 5, 1, 0),
+    (2, 9, 17, 0, 1), (3, 4, 7, 1, 0), (3, 4, 7, 0, 1), (2, 31, 40, 1, 0), (2, 63, 20, 1, 0),
+    (2, 63, 40, 0, 1), (3, 19, 80, 1, 0), (2, 5, 1, 1, 0),
+])
+def test_toeplitz_product_tensor_core(ctx, prec, d, n, r, L_ext, adjoint):
+    import torch
+    grid = _random_grid(d, n, 200 + d * 10 + n)
+    N = (n + 1) ** d
+    L = n + 2 if L_ext else n + 1
+    rng = np.random.Generator(np.random.PCG64(17 + r))
+    X = (rng.standard_normal((r, N)) + 1j * rng.standard_normal((r, N))).astype(np.complex64)
+    g_dev = torch.from_numpy(grid.reshape(-1).astype(np.complex128)).cuda()
+    X_dev = torch.from_numpy(X).cuda()
+    Y_dev = torch.full((r, L ** d), float("nan"), dtype=torch.complex64, device="cuda")
+    ctx.toeplitz_mm_dev(g_dev, d, n, X_dev, L, adjoint, prec, Y_dev)
+    Y = Y_dev.cpu().numpy().astype(np.complex128).T
+    T = _toeplitz_rows(grid, n, d, L, adjoint)
+    Xd = X.astype(np.complex128).T
+    ref = T @ Xd
+    bound = TC_REL[prec](N) * (np.abs(T) @ np.abs(Xd))
+    assert np.all(np.isfinite(Y))
+    assert np.all(np.abs(Y - ref) <= bound + 1e-30), float(np.max(np.abs(Y - ref) / (bound + 1e-30)))
+
+
+@pytest.mark.parametrize("name,d,n,m,seed", [
+    ("C1", 2, 15, 5, None), ("d1", 1, 40, 3, 5), ("d2rag", 2, 9, 7, 7), ("d3", 3, 5, 4, 8),
+    ("d2m12", 2, 23, 12, 10),
+])
+def test_solve_tensor_core_bf16x3_matches_oracle(ctx, name, d, n, m, seed):
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C1") if seed is None else W.make_problem(name, d, n, m, seed)
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision="bf16x3"))
+    t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m)
+    assert res.info["status"] == 0, res.info
+    _check_solution(res, t_o, c_o)
+
+
+def test_build_S_tensor_core_matches_oracle(ctx):
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C1")
+    S, sig, U, V, info = ctx.build_S(P.grid, P.d, P.n, P.m, default_opts(precision="bf16x3"), want_uv=True)
+    S_o, s_o, U_o, V_o = O.prony_S(P.grid, P.d, P.n, P.m)
+    assert np.max(np.abs(sig - s_o) / s_o) <= 1e-5
+    ph = np.sum(V_o.conj() * V, axis=0)
+    ph = ph / np.abs(ph)
+    for l in range(P.d):
+        S_al = np.diag(ph) @ S[l] @ np.diag(ph.conj())
+        assert np.linalg.norm(S_al - S_o[l]) / np.linalg.norm(S_o[l]) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+def test_solve_noisy_C2_tensor_core(ctx, prec):
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C2")
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision=prec))
+    t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
+    te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
+    te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
+    assert te_g <= 1.5 * te_o + 1e-6, (te_g, te_o, res.info)
+    assert ce_g <= 1.5 * ce_o + 1e-6, (ce_g, ce_o, res.info)
