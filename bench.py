@@ -2,20 +2,24 @@
 """Benchmark of the GPU Prony solver on the C2 workload (d=2, n=63, N=4096, m=20, 40 dB).
 
 One step = one pass of the whole hot path (Algorithm 1 with the block power SVD) over a
-batch of `--batch` independent synthetic C2 problems.  Printed as one JSON line:
+batch of `--batch` independent synthetic C2 problems (default 152, one per SM).  Printed as one
+JSON line:
 
   value     solves/s that pass the accuracy gate, inputs resident in HBM, CUDA events on
             the launching stream, L2 flushed (256 MB write) between steps outside the events
   e2e       the same metric through the host-pointer C-ABI call (pinned host buffers,
             host->device copy of the samples and device->host copy of t, c inside the timing)
-  roofline  the Toeplitz block products (dominant kernel): algorithmic flops / CUDA-event
-            duration of every launch in the timed steps, against the FP32 FFMA peak
+  roofline  the Toeplitz block products (dominant kernel, k_toeplitz_tc): useful flops /
+            CUDA-event duration of every launch in the timed steps, against the measured BF16
+            tensor peak divided by the split products per useful product (6 for BF16x3)
   cpu_baseline  the FP64 oracle (Algorithm 3, explicit T, LAPACK) on a bounded sample
 
 Gate: under noise a solve counts if its torus error of t and relative error of c are within
 1.5x the oracle's (+1e-6); the oracle runs on a sample of the batch and the largest sampled
 error sets the threshold of unsampled problems.
 
+`--config C4` runs the 4096-problem batch workload, `--config C5` the refinement workload
+(its own JSON line: ms per refinement step and errors before / after).
 `--impl reference` times the oracle itself (the reference arm) on the host cores.
 Multi-GPU (torchrun): every rank solves its own batch (weak scaling, no collective on the
 data path); rank 0 prints the aggregate.
@@ -41,7 +45,10 @@ import workloads as W  # noqa: E402
 METRIC = "Prony solves/sec at t-error≤1e-6; Toeplitz-GEMM TFLOP/s as % of peak"
 WORKLOAD = {"C2": "C2 plain large: d=2, n=63 (N=4096), m=20, additive complex Gaussian noise SNR 40 dB",
             "C1": "C1 plain small: d=2, n=15 (N=256), m=5, noise-free",
-            "C3": "C3 precision: d=3, n=19 (N=8000), m=40, SNR 50 dB"}
+            "C3": "C3 precision: d=3, n=19 (N=8000), m=40, SNR 50 dB",
+            "C4": "C4 batch: independent d=2 problems, n~U{7..31}, m~U{2..min(12,floor(n/2)^2)}, SNR 30 dB",
+            "C5": "C5 refine: d=2, n=63 (N=4096), m=20, SNR 20 dB; Prony estimate, then 50 "
+                  "Levenberg-Marquardt / 50 Adam steps on ||f_obs - f(t,c)||^2 over k in {-63..64}^2"}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 
@@ -70,7 +77,7 @@ def roofline(prec, achieved, traffic, launches, stats, total_ms) -> dict:
     if prec in SPLIT_PRODUCTS:
         pk = measured_peaks()
         peak = pk["bf16"] / SPLIT_PRODUCTS[prec]
-        return {"bound": "tensor", "kernel": f"k_toeplitz_tc<{SPLIT_PRODUCTS[prec] // 2 + 1}> (tcgen05, A in TMEM)",
+        return {"bound": "tensor", "kernel": f"k_toeplitz_tc<{3 if prec == 'bf16x3' else 2}> (tcgen05, A in TMEM)",
                 "peak": peak, "frac": achieved / peak,
                 "peak_source": f"BF16 dense {pk['bf16']:.0f} TFLOP/s {pk['src']} / {SPLIT_PRODUCTS[prec]} split products",
                 "tensor_pipe_frac": achieved * SPLIT_PRODUCTS[prec] / pk["bf16"], **common}
@@ -85,9 +92,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3"])
-    ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3", "C4", "C5"])
+    ap.add_argument("--batch", type=int, default=None, help="problems per GPU (default 152; C4: 4096)")
+    ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--oracle-sample", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -166,6 +173,13 @@ class Clocks:
                 "reasons": reasons, "samples": len(use), "in_window": bool(inwin)}
 
 
+def make_problems(config: str, count: int, rank: int = 0):
+    """The synthetic problems of one GPU (rank) for a configuration."""
+    if config == "C4":
+        return W.batch_problems(count, seed_offset=rank)
+    return [W.config_problem(config, seed_offset=rank * count + i) for i in range(count)]
+
+
 def oracle_solve(P):
     from oracle import prony_oracle as O
     t, c, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
@@ -193,11 +207,32 @@ def blas_threads() -> int:
     return os.cpu_count() or 1
 
 
+def share_gate(gmax, device):
+    """Rank 0's gate thresholds (largest sampled oracle errors x 1.5) to every rank."""
+    import torch
+    import torch.distributed as dist
+    g = torch.tensor(list(gmax) if gmax else [-1.0, -1.0], dtype=torch.float64, device=device)
+    dist.broadcast(g, 0)
+    return None if float(g[0]) < 0 else (float(g[0]), float(g[1]))
+
+
+def reduce_over_ranks(total_ms: float, passed: int, device):
+    """Whole-job figures of a multi-rank run: the slowest rank's time and the solves of all ranks."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([total_ms, float(passed)], dtype=torch.float64, device=device)
+    tmax = tt.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = tt.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    problems = [W.config_problem(args.config, seed_offset=i) for i in range(args.warmup + args.steps)]
+    problems = make_problems(args.config, args.warmup + args.steps)
     for P in problems[:args.warmup]:
         oracle_solve(P)
     times = []
@@ -220,10 +255,68 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def refine_bench(args):
+    """C5: the Prony estimate of each problem, then 50 on-device Levenberg-Marquardt steps (one
+    CUDA graph) and, separately, 50 Adam steps through the exp-sum autograd kernels.  Prints one
+    JSON line: ms per refinement step and the parameter errors before and after."""
+    import torch
+    from paper_2012_11430_gb300 import Context, default_opts
+    from paper_2012_11430_gb300.build import build
+    from paper_2012_11430_gb300.refine import refine_adam, refine_lm
+    build()
+    B = args.batch or 8
+    problems = make_problems("C5", B)
+    ctx = Context(0)
+    ds, ns, ms = [P.d for P in problems], [P.n for P in problems], [P.m for P in problems]
+    outs, _ = ctx.solve_batched([P.grid for P in problems], ds, ns, ms, default_opts(precision=args.precision))
+    n, d = problems[0].n, problems[0].d
+    lo, length = [-n] * d, [2 * n + 2] * d
+    steps = 50
+    res = {"lm": [], "adam": []}
+    err = {"prony": [], "lm": [], "adam": [], "oracle_fit": []}
+    stream = torch.cuda.current_stream()
+    for i, P in enumerate(problems):
+        t0, c0 = outs[i].t, outs[i].c
+        y = torch.as_tensor(P.grid.reshape(-1), dtype=torch.complex64, device="cuda")
+        td = torch.as_tensor(t0, dtype=torch.float64, device="cuda")
+        cd = torch.as_tensor(c0, dtype=torch.complex128, device="cuda")
+        err["prony"].append(W.match_to_truth(t0, c0, P.t, P.c))
+        for kind in ("lm", "adam"):
+            for rep in range(2):                  # the first run captures the graph / warms up
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if kind == "lm":
+                    t, c, L = refine_lm(td, cd, y, ctx, lo, length, steps=steps)
+                else:
+                    t, c, L = refine_adam(td, cd.to(torch.complex64), y, ctx, lo, length, steps=steps,
+                                          lr_t=2e-5, lr_c=5e-3)
+                e1.record(stream)
+                e1.synchronize()
+            res[kind].append(e0.elapsed_time(e1) / steps)
+            err[kind].append(W.match_to_truth(t.cpu().numpy(), c.cpu().numpy().astype(np.complex128), P.t, P.c))
+    from oracle import prony_oracle as O
+    k = O.box_set(length, d) + np.array(lo)
+    P = problems[0]
+    to, co, _ = O.refine_least_squares(outs[0].t, outs[0].c, k, P.grid.reshape(-1))
+    err["oracle_fit"].append(W.match_to_truth(to, co, P.t, P.c))
+    worst = {key: {"t_max": max(e[0] for e in v), "c_max": max(e[1] for e in v)} for key, v in err.items() if v}
+    line = {"metric": "C5 refinement: ms per Levenberg-Marquardt step", "value": statistics.median(res["lm"]),
+            "unit": "ms/step", "higher_is_better": False, "n_gpus": 1, "steps": steps,
+            "adam_ms_per_step": statistics.median(res["adam"]), "dtype": "f32 exp-sum, f64 parameters",
+            "data": "synthetic", "config": {"workload": WORKLOAD["C5"], "problems": B},
+            "errors_vs_truth": worst,
+            "note": "oracle_fit = FP64 scipy Levenberg-Marquardt from the same Prony estimate (problem 0)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.config == "C5":
+        refine_bench(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -237,8 +330,8 @@ def main():
         build()
     if ws > 1:
         torch.distributed.barrier()
-    B = args.batch
-    problems = [W.config_problem(args.config, seed_offset=rank * B + i) for i in range(B)]
+    B = args.batch or (4096 if args.config == "C4" else 152)
+    problems = make_problems(args.config, B, rank)
     ds = [P.d for P in problems]
     ns = [P.n for P in problems]
     ms = [P.m for P in problems]
@@ -282,14 +375,9 @@ def main():
                "sample": f"{len(sample)} of the {args.config} problems of the batch, FP64 oracle with explicit T "
                          f"and Algorithm 3 (LAPACK), one after another"}
         gate = [(1.5 * te + 1e-6, 1.5 * ce + 1e-6) for te, ce in oerr]
+    gmax = (max(x[0] for x in gate), max(x[1] for x in gate)) if gate else None
     if ws > 1:
-        import torch.distributed as dist
-        g = torch.tensor([max(x[0] for x in gate), max(x[1] for x in gate)] if gate else [0.0, 0.0],
-                         dtype=torch.float64, device="cuda")
-        dist.broadcast(g, 0)
-        gmax = (float(g[0]), float(g[1]))
-    else:
-        gmax = (max(x[0] for x in gate), max(x[1] for x in gate)) if gate else None
+        gmax = share_gate(gmax, torch.device("cuda", local))
     passed = 0
     for i, (te, ce) in enumerate(errs):
         if not noisy:
@@ -327,13 +415,7 @@ def main():
     ctx.set_profiling(False)
     total_ms = sum(ms_steps)
     if ws > 1:
-        tt = torch.tensor([total_ms, float(passed)], dtype=torch.float64, device="cuda")
-        import torch.distributed as dist
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = tt.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, passed_all = float(tmax[0]), float(tsum[1])
+        total_ms, passed_all = reduce_over_ranks(total_ms, passed, torch.device("cuda", local))
     else:
         passed_all = float(passed)
     value = passed_all * args.steps / (total_ms / 1e3)

@@ -79,7 +79,7 @@ typedef struct {
   double normT;             /* ||T||_F (closed form from the grid) */
 } prony_info;
 
-/* Fill *opts with defaults (PRONY_BF16X3 if the tensor-core path is built, p = m). */
+/* Fill *opts with defaults: PRONY_BF16X3, p = m, tolerances and cap as documented above. */
 void prony_default_opts(prony_opts* opts);
 const char* prony_status_string(int status);
 /* Message of the last PRONY_ECUDA / PRONY_ENOMEM on this host thread. */
@@ -135,12 +135,32 @@ int prony_expsum_fwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev,
                          const int* lo, const int* len, void* f_dev, void* stream);
 
 /* Vector-Jacobian product of the exponential sum over the same box: given
- * g = dL/d(conj f) as complex64 (L real; for L = sum |f - y|^2, g = f - y),
- * writes grad_t[m*d] (float64) = dL/dt and grad_c[m] (complex64) =
- * dL/dRe c + i dL/dIm c.  The exponentials are recomputed, not stored. */
+ * g = dL/dRe f + i dL/dIm f as complex64 (L real; for L = sum |f - y|^2,
+ * g = 2 (f - y)), writes grad_t[m*d] (float64) = dL/dt and grad_c[m]
+ * (complex64) = dL/dRe c + i dL/dIm c, i.e. grad_c = sum_k g_k conj(e_jk) and
+ * grad_t = 2 pi sum_k k Im(conj(g_k) c_j e_jk) with e_jk = exp(-2 pi i <t_j, k>).
+ * The exponentials are recomputed, not stored. */
 int prony_expsum_bwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev, int m, int d,
                          const int* lo, const int* len, const void* g_dev,
                          double* grad_t_dev, void* grad_c_dev, void* stream);
+
+/* Least-squares refinement of an exponential sum on device data by damped Gauss-Newton
+ * (Levenberg-Marquardt) steps, starting from (t, c) -- typically the Prony estimate:
+ *   minimise L(t, c) = sum_k |sum_j c_j exp(-2 pi i <t_j, k>) - y_k|^2
+ * over the integer points k of the box {lo_l .. lo_l + len_l - 1} (row-major).  The model is
+ * Eq. (1) of Section 1; the paper fits only c by least squares (Eq. ls_probl), this also moves t.
+ * t_dev: m*d float64 (in/out, kept in [0,1)), c_dev: m complex128 (in/out),
+ * y_dev: prod(len) complex64 samples, loss_dev: iters+1 float64 or NULL (the loss before each
+ * step and after the last).  Each step: one pass over the points for J^* J and J^* r (FP32 per
+ * block, FP64 accumulators), one FP32 Cholesky solve of the Jacobi-scaled damped system
+ * (Marquardt damping lambda, initial value lambda0 > 0), one trial pass; the step is taken if
+ * the loss decreased (lambda / 3), else refused (lambda * 4).  All steps run as one CUDA graph,
+ * captured on the first call with a given argument set and reused while the set repeats.
+ * m * (d + 2) <= 160, else PRONY_EINVAL.  Runs on `stream` (NULL: the context stream) and
+ * returns when the refined (t, c) are written. */
+int prony_refine_lm_dev(prony_ctx* ctx, double* t_dev, prony_c128* c_dev, int m, int d,
+                        const int* lo, const int* len, const void* y_dev, int iters,
+                        double lambda0, double* loss_dev, void* stream);
 
 /* The Toeplitz block product used by the power iterations, exposed for testing:
  * Y[k, j] = sum_{h in I_n} F(k - h) X[h, j] for k in the box {0..L-1}^d

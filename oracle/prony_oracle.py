@@ -362,3 +362,38 @@ def expsum_grad(t, c, k, r):
     for l in range(t.shape[1]):
         gt[:, l] = 2.0 * np.real((E * (-2j * np.pi * k[:, l:l + 1])).T @ r.conj() * c)
     return gt, gc
+
+
+def refine_least_squares(t0, c0, k, y, max_nfev: int = 200):
+    """argmin over (t, c) of L = sum_k |f(k; t, c) - y_k|^2 (Eq. 1 model), from (t0, c0).
+
+    The paper fits c alone by least squares for fixed t (Eq. ls_probl); the refinement moves
+    t as well.  Plain definition: scipy's Levenberg-Marquardt on the real residual vector
+    [Re r; Im r] with the parameters (t_j(1..d), Re c_j, Im c_j) and its analytic Jacobian."""
+    from scipy.optimize import least_squares
+    m, d = t0.shape
+    kf = k.astype(np.float64)
+
+    def unpack(x):
+        return x[:m * d].reshape(m, d), x[m * d:m * d + m] + 1j * x[m * d + m:]
+
+    def resid(x):
+        t, c = unpack(x)
+        r = np.exp(-2j * np.pi * (kf @ t.T)) @ c - y
+        return np.concatenate([r.real, r.imag])
+
+    def jac(x):
+        t, c = unpack(x)
+        E = np.exp(-2j * np.pi * (kf @ t.T))                       # (K, m)
+        cols = []
+        Jt = (-2j * np.pi) * E[:, :, None] * kf[:, None, :] * c[None, :, None]   # (K, m, d)
+        cols.append(Jt.reshape(len(kf), m * d))
+        cols.append(E)
+        cols.append(1j * E)
+        J = np.concatenate(cols, axis=1)
+        return np.concatenate([J.real, J.imag], axis=0)
+
+    x0 = np.concatenate([t0.reshape(-1), c0.real, c0.imag])
+    sol = least_squares(resid, x0, jac=jac, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=max_nfev)
+    t, c = unpack(sol.x)
+    return np.mod(t, 1.0), c, float(np.sum(sol.fun ** 2))

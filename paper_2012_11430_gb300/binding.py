@@ -23,7 +23,7 @@ EXPORTS = [
     "prony_default_opts", "prony_status_string", "prony_last_error", "prony_ctx_create", "prony_ctx_destroy",
     "prony_solve", "prony_build_S", "prony_eval", "prony_solve_batched", "prony_solve_batched_dev",
     "prony_expsum_fwd_dev", "prony_expsum_bwd_dev", "prony_toeplitz_mm_dev", "prony_set_profiling",
-    "prony_get_stats", "prony_toeplitz_mm_static",
+    "prony_get_stats", "prony_toeplitz_mm_static", "prony_refine_lm_dev",
 ]
 
 
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
     lib.prony_solve_batched_dev.argtypes = [P, I, P, P, P, P, P, P, P, P, P, P, P]
     lib.prony_expsum_fwd_dev.argtypes = [P, P, P, I, I, P, P, P, P]
     lib.prony_expsum_bwd_dev.argtypes = [P, P, P, I, I, P, P, P, P, P, P]
+    lib.prony_refine_lm_dev.argtypes = [P, P, P, I, I, P, P, P, I, ctypes.c_double, P, P]
     lib.prony_toeplitz_mm_dev.argtypes = [P, P, I, I, P, I, I, I, I, P, P]
     lib.prony_toeplitz_mm_static.argtypes = [P, I, I, P, I, I, I, P, P]
     lib.prony_set_profiling.argtypes = [P, I]
@@ -283,6 +284,20 @@ class Context:
                                               ctypes.c_void_p(g_dev.data_ptr()), ctypes.c_void_p(gt_dev.data_ptr()),
                                               ctypes.c_void_p(gc_dev.data_ptr()), ctypes.c_void_p(stream)),
                "prony_expsum_bwd_dev")
+
+    def refine_lm_dev(self, t_dev, c_dev, lo, length, y_dev, iters: int, lambda0: float = 1e-3, loss_dev=None,
+                      stream: int = 0):
+        """Levenberg-Marquardt refinement in place: t_dev (m, d) float64, c_dev (m,) complex128,
+        y_dev complex64 samples on the box; loss_dev (iters + 1,) float64 or None."""
+        m, d = t_dev.shape
+        lo = np.ascontiguousarray(lo, dtype=np.int32)
+        ln = np.ascontiguousarray(length, dtype=np.int32)
+        _check(self._lib.prony_refine_lm_dev(self._h, ctypes.c_void_p(t_dev.data_ptr()),
+                                             ctypes.c_void_p(c_dev.data_ptr()), m, d, _ptr(lo), _ptr(ln),
+                                             ctypes.c_void_p(y_dev.data_ptr()), int(iters), float(lambda0),
+                                             ctypes.c_void_p(loss_dev.data_ptr() if loss_dev is not None else 0),
+                                             ctypes.c_void_p(stream)),
+               "prony_refine_lm_dev")
 
     def toeplitz_mm_dev(self, grid_dev, d: int, n: int, X_dev, L: int, adjoint: int, precision, Y_dev,
                         stream: int = 0):

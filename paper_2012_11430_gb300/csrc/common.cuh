@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #define PRONY_RMAX 128        // max columns r0 = m + p
+#define PRONY_LM_PMAX 160     // max real parameters m (d + 2) of the refinement
 #define PRONY_MMAX 64         // max terms m
 #define PRONY_DMAX 4          // max dimension d
 
@@ -27,6 +28,8 @@ struct ProbDesc {
   long long yoff;             // offset (elements) of its Next x r0 block in Y
   long long soff;             // offset (bytes) of its small workspace
   long long ooff;             // offset (terms) of its results in the packed t / c outputs
+  long long toff;             // offset (words) of its split-plane tables in tabF / tabH
+  int Gd4;                    // Gd rounded up to a multiple of 4 (length of one table)
 };
 
 // Per-problem iteration state, device resident.
@@ -64,6 +67,7 @@ struct SmallLay {
   long long c;       // LDM double2
   long long phase;   // LDM double2
   long long argmx;   // LDM u64
+  long long work1, work2, work3, work4;   // LDR x LDM double2 scratch of the FP64 steps
   long long bytes;
 };
 
@@ -86,6 +90,10 @@ inline SmallLay make_small_lay(int LDR, int LDM, int dmax) {
   L.c = take(16LL * LDM);
   L.phase = take(16LL * LDM);
   L.argmx = take(8LL * LDM);
+  L.work1 = take(16LL * LDR * LDM);
+  L.work2 = take(16LL * LDR * LDM);
+  L.work3 = take(16LL * LDR * LDM);
+  L.work4 = take(16LL * LDR * LDM);
   L.bytes = (o + 255) / 256 * 256;
   return L;
 }
@@ -99,6 +107,11 @@ struct Dev {
   const double2* grid64;
   float2* gF;
   float2* gH;
+  // Split BF16 planes of the samples for the tensor-core path (Section 1 samples, split once):
+  // table a = part * 3 + plane (part 0: Re, 1: Im) of problem p at toff + a * Gd4; word x holds
+  // plane(F[x]) in its low half and plane(F[x - 1]) in its high half (F = gF for tabF, gH for tabH).
+  uint32_t* tabF;
+  uint32_t* tabH;
   float2* V;
   float2* U;
   float2* B1;
@@ -185,6 +198,29 @@ __device__ inline uint64_t frac64(double t) {
   return (hi << 32) + lo;
 }
 
+// Integer box {lo_l .. lo_l + len_l - 1} enumerated row-major (last coordinate fastest).
+struct Box { int lo[PRONY_DMAX]; int len[PRONY_DMAX]; };
+
+inline Box make_box(int d, const int* lo, const int* len) {
+  Box B = {};
+  for (int l = 0; l < d; ++l) { B.lo[l] = lo[l]; B.len[l] = len[l]; }
+  return B;
+}
+
+__device__ inline void box_point(const Box& B, int d, long long q, int* k) {
+  for (int l = d - 1; l >= 0; --l) {
+    k[l] = B.lo[l] + (int)(q % B.len[l]);
+    q /= B.len[l];
+  }
+}
+
+// Phase <t_j, k> mod 1 from 64-bit binary fractions (exact), centred to [-1/2, 1/2).
+__device__ inline float centred_phase(const uint64_t* T, const int* k, int d) {
+  uint64_t acc = 0;
+  for (int l = 0; l < d; ++l) acc += T[l] * (uint64_t)(long long)k[l];
+  return (float)(int)(acc >> 32) * 2.3283064365386963e-10f;
+}
+
 // ----------------------------------------------------------------------------- launchers
 // Every kernel launch of the library goes through a launcher that calls note_launch()
 // (a process-wide counter, read with prony_get_stats).
@@ -226,12 +262,22 @@ void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, 
                      int ybuf, int y_ext, int maxw, int precision, cudaStream_t s);
 
 // kernels_tc.cu (tensor-core Toeplitz products, split BF16 planes)
-int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows, int ntbox);
+int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows);
 size_t tc_smem_bytes(int npl, int ntbox, int stages, int win_cap);
+void launch_split_tables(const Dev& D, cudaStream_t s);
+int tc_max_cluster(int npl, int want, size_t smem);
 void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int npl, int ntbox, int kpitch, cudaStream_t s);
-void launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel, int ybuf,
-                        int y_ext, int npl, int ntbox, int kpitch, int win_cap, int stages, const CUtensorMap& map,
-                        int* err, cudaStream_t s);
+cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel,
+                               int ybuf, int y_ext, int npl, int ntbox, int win_cap, int stages, int cs,
+                               const CUtensorMap& map, int* err, cudaStream_t s);
+
+// kernels_refine.cu (Levenberg-Marquardt refinement of (t, c))
+long long lm_workspace_bytes(int m, int d);
+size_t lm_solve_smem(int m, int d);
+cudaError_t lm_set_attributes(int m, int d);
+void launch_refine_lm(double* t, double2* c, int m, int d, const int* lo, const int* len, long long K,
+                      const float2* y, int iters, double lambda0, double* hist, void* ws, cudaStream_t s);
+constexpr int LM_LAUNCHES_PER_STEP = 4;
 
 // kernels_small.cu
 enum QrMode { QR_PLAIN = 0, QR_DROP = 1, QR_RANK = 2 };

@@ -1,0 +1,655 @@
+// FP64-accurate small steps of Algorithm 1, designed for GB300's FP64 unit (high latency per
+// dependent operation, low throughput): iterations run in FP32, and the quantities that fix the
+// results are then computed or refined in FP64 with matrix products only (latency-tolerant).
+//
+//  k_svd_S  SVD of Q = U^* T V (Algorithm 3, final step): FP32 one-sided Jacobi gives V_Q; FP64
+//           refinement of V_Q as eigenvectors of Q^*Q (Ogita & Aishima 2018, iterative refinement
+//           for the symmetric eigenvalue problem based on matrix multiplication, Hermitian form);
+//           sigma = sqrt(eigenvalues), U_Q = Q V_Q Sigma^{-1} and S_l = U_Q^* (U^* T_l V) V_Q
+//           Sigma^{-1} (Eq. generateSl) in FP64.
+//  k_eig_t  C_mu = sum_l mu_l S_l (FP64); W from an FP32 Hessenberg reduction, shifted complex QR
+//           and triangular eigenvectors; W^{-1} from an FP32 Gauss-Jordan inverse refined by one
+//           FP64 Newton-Schulz step X <- X (2I - W X); z_j(l) = (W^{-1} S_l W)_jj in FP64
+//           (Eq. diagonalizeSl).  The diagonal of W^{-1} S_l W is stationary in W: an error E in
+//           W (W = W_0 (I + E)) changes it only at second order, so z carries FP64 accuracy even
+//           though W comes from FP32 iterations.  t_j(l) = -arg z_j(l) / 2pi mod 1.
+//  k_canon  phase-canonical singular basis for the S_l output.
+#include "common.cuh"
+
+#include <algorithm>
+
+#define ST_OK 0
+#define ST_ENOCONV (-3)
+#define ST_ENAN (-4)
+
+namespace {
+
+__device__ inline void set_status_e(ProbState& s, int st) {
+  if (s.status == ST_OK) s.status = st;
+}
+
+// ----------------------------------------------------------------------------- FP32 complex
+__device__ inline float2 fc(float x, float y) { return make_float2(x, y); }
+__device__ inline float2 fmul(float2 a, float2 b) { return fc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ inline float2 fmulc(float2 a, float2 b) { return fc(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+__device__ inline float2 fadd(float2 a, float2 b) { return fc(a.x + b.x, a.y + b.y); }
+__device__ inline float2 fsub(float2 a, float2 b) { return fc(a.x - b.x, a.y - b.y); }
+__device__ inline float2 fconj(float2 a) { return fc(a.x, -a.y); }
+__device__ inline float2 fscale(float2 a, float s) { return fc(a.x * s, a.y * s); }
+__device__ inline float fabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ inline float fabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__device__ inline float2 fdiv(float2 a, float2 b) {
+  if (fabsf(b.x) >= fabsf(b.y)) {
+    float r = b.y / b.x, den = b.x + b.y * r;
+    return fc((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  }
+  float r = b.x / b.y, den = b.x * r + b.y;
+  return fc((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+}
+__device__ inline float2 fsqrtc(float2 a) {
+  float r = hypotf(a.x, a.y);
+  if (r == 0.f) return fc(0.f, 0.f);
+  float sx = sqrtf(0.5f * (r + fabsf(a.x)));
+  if (a.x >= 0.f) return fc(sx, a.y / (2.f * sx));
+  return fc(fabsf(a.y) / (2.f * sx), a.y >= 0.f ? sx : -sx);
+}
+
+// ----------------------------------------------------------------------------- FP64 small products
+// C (M x N, ld ldc) = opA(A) (M x K) * opB(B) (K x N); opX = conjugate transpose when XH.
+// Four independent accumulators per entry keep several FP64 multiply-adds in flight.
+template <bool AH, bool BH>
+__device__ void zgemm(double2* C, int ldc, const double2* A, int lda, const double2* B, int ldb, int M, int N, int K) {
+  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx % N;
+    double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        double2 a = AH ? cconj(A[(k + u) * lda + i]) : A[i * lda + k + u];
+        double2 b = BH ? cconj(B[j * ldb + k + u]) : B[(k + u) * ldb + j];
+        acc[u] = cadd(acc[u], cmul(a, b));
+      }
+    }
+    for (; k < K; ++k) {
+      double2 a = AH ? cconj(A[k * lda + i]) : A[i * lda + k];
+      double2 b = BH ? cconj(B[j * ldb + k]) : B[k * ldb + j];
+      acc[0] = cadd(acc[0], cmul(a, b));
+    }
+    C[i * ldc + j] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+  }
+}
+
+// block-wide sum of a double (tree; result in every thread)
+__device__ double block_sum_d(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+  __syncthreads();
+  return r;
+}
+
+__device__ inline void rr_pair(int step, int k, int nb, int& pa, int& pb) {
+  // round-robin (circle) ordering: position 0 fixed, positions 1..nb-1 rotate
+  auto who = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + step) % (nb - 1)) + 1; };
+  pa = who(k);
+  pb = who(nb - 1 - k);
+}
+
+// ----------------------------------------------------------------------------- SVD of Q and S_l
+__global__ void __launch_bounds__(256) k_svd_S(Dev D) {
+  extern __shared__ float2 fsm[];
+  __shared__ int s_rot;
+  __shared__ double s_red[32];
+  __shared__ double s_lam[PRONY_MMAX];
+  __shared__ int s_rank[PRONY_MMAX];
+  const ProbDesc& p = D.P[blockIdx.x];
+  ProbState& st = D.st[blockIdx.x];
+  if (st.status == ST_ENAN) return;
+  const int a = st.wu, b = st.wv;
+  if (b <= 0 || a <= 0) return;
+  const int LM = D.L.LDM, LR = D.L.LDR;
+  char* sb = D.small + p.soff;
+  const double2* Q = (const double2*)(sb + D.L.q);            // a x b, ld LM
+  double2* UQ = (double2*)(sb + D.L.uq);                        // a x b, ld LM
+  double2* VQ = (double2*)(sb + D.L.vq);                        // b x b, ld LM
+  double* sig = (double*)(sb + D.L.sigma);
+  double2* Hm = (double2*)(sb + D.L.work1);                     // b x b
+  double2* Vm = (double2*)(sb + D.L.work2);                     // b x b
+  double2* T1 = (double2*)(sb + D.L.work3);                     // up to a x b
+  double2* T2 = (double2*)(sb + D.L.work4);                     // up to a x b
+  float2* Qc = fsm;                                             // [b][a] columns (FP32)
+  float2* Vc = fsm + (size_t)LM * LR;                           // [b][b] columns (FP32)
+
+  // ---- FP32 one-sided Jacobi on the columns of Q
+  for (int idx = threadIdx.x; idx < a * b; idx += blockDim.x) {
+    int i = idx % a, j = idx / a;
+    double2 q = Q[i * LM + j];
+    Qc[j * a + i] = fc((float)q.x, (float)q.y);
+  }
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+    int i = idx % b, j = idx / b;
+    Vc[j * b + i] = fc(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  const int nb = b + (b & 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const float jtol = 4.f * a * 5.9604645e-8f;
+  int sweep = 0;
+  for (; sweep < 30 && b > 1; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int step = 0; step < nb - 1; ++step) {
+      for (int k = warp; k < nb / 2; k += nwarp) {
+        int pa, pb;
+        rr_pair(step, k, nb, pa, pb);
+        if (pa >= b || pb >= b) continue;
+        if (pa > pb) { int t = pa; pa = pb; pb = t; }
+        float al = 0.f, be = 0.f;
+        float2 ga = fc(0.f, 0.f);
+        for (int i = lane; i < a; i += 32) {
+          float2 x = Qc[pa * a + i], y = Qc[pb * a + i];
+          al += fabs2(x);
+          be += fabs2(y);
+          ga = fadd(ga, fmulc(x, y));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+          ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+        }
+        float ag = sqrtf(fabs2(ga));
+        if (ag <= jtol * sqrtf(al * be) || ag == 0.f) continue;
+        float zeta = (be - al) / (2.f * ag);
+        float tt = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        float c = rsqrtf(1.f + tt * tt), s = c * tt;
+        float2 ph = fc(ga.x / ag, -ga.y / ag);   // e^{-i arg gamma}
+        for (int i = lane; i < a; i += 32) {
+          float2 x = Qc[pa * a + i], y = fmul(Qc[pb * a + i], ph);
+          Qc[pa * a + i] = fsub(fscale(x, c), fscale(y, s));
+          Qc[pb * a + i] = fadd(fscale(x, s), fscale(y, c));
+        }
+        for (int i = lane; i < b; i += 32) {
+          float2 x = Vc[pa * b + i], y = fmul(Vc[pb * b + i], ph);
+          Vc[pa * b + i] = fsub(fscale(x, c), fscale(y, s));
+          Vc[pb * b + i] = fadd(fscale(x, s), fscale(y, c));
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    if (!s_rot) break;
+    __syncthreads();
+  }
+  // ---- FP64: H = Q^* Q, then refine V (eigenvectors of H) by two matrix-product steps
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+    int i = idx / b, j = idx % b;
+    float2 v = Vc[j * b + i];
+    Vm[i * LM + j] = make_double2(v.x, v.y);
+  }
+  zgemm<true, false>(Hm, LM, Q, LM, Q, LM, b, b, a);
+  __syncthreads();
+  for (int iter = 0; iter < 2; ++iter) {
+    zgemm<true, false>(T1, LM, Vm, LM, Vm, LM, b, b, b);        // V^* V
+    zgemm<false, false>(T2, LM, Hm, LM, Vm, LM, b, b, b);       // H V
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {   // R = I - V^* V  (into T1)
+      int i = idx / b, j = idx % b;
+      double2 r = T1[i * LM + j];
+      T1[i * LM + j] = make_double2((i == j ? 1.0 : 0.0) - r.x, -r.y);
+    }
+    __syncthreads();
+    // S = V^* (H V)  -> Hv scratch: reuse UQ rows as b x b scratch (overwritten later)
+    zgemm<true, false>(UQ, LM, Vm, LM, T2, LM, b, b, b);
+    __syncthreads();
+    for (int i = threadIdx.x; i < b; i += blockDim.x) s_lam[i] = UQ[i * LM + i].x / (1.0 - T1[i * LM + i].x);
+    __syncthreads();
+    // delta = 2 (||S - diag(lambda)||_F + ||H||_F ||R||_F)
+    double e1 = 0.0, e2 = 0.0, e3 = 0.0;
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+      int i = idx / b, j = idx % b;
+      double2 sv = UQ[i * LM + j];
+      if (i == j) sv.x -= s_lam[i];
+      e1 += cabs2(sv);
+      e2 += cabs2(Hm[i * LM + j]);
+      e3 += cabs2(T1[i * LM + j]);
+    }
+    e1 = block_sum_d(e1, s_red);
+    e2 = block_sum_d(e2, s_red);
+    e3 = block_sum_d(e3, s_red);
+    const double delta = 2.0 * (sqrt(e1) + sqrt(e2) * sqrt(e3));
+    // E (into T2): e_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i), or r_ij / 2 inside a cluster
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+      int i = idx / b, j = idx % b;
+      double2 r = T1[i * LM + j];
+      double2 e;
+      if (i != j && fabs(s_lam[i] - s_lam[j]) > delta) {
+        double2 sv = UQ[i * LM + j];
+        e = cscale(cadd(sv, cscale(r, s_lam[j])), 1.0 / (s_lam[j] - s_lam[i]));
+      } else {
+        e = cscale(r, 0.5);
+      }
+      T2[i * LM + j] = e;
+    }
+    __syncthreads();
+    zgemm<false, false>(T1, LM, Vm, LM, T2, LM, b, b, b);        // V E
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+      int i = idx / b, j = idx % b;
+      Vm[i * LM + j] = cadd(Vm[i * LM + j], T1[i * LM + j]);
+    }
+    __syncthreads();
+  }
+  // ---- order by eigenvalue of H = sigma^2 (descending)
+  for (int j = threadIdx.x; j < b; j += blockDim.x) {
+    int r = 0;
+    for (int i = 0; i < b; ++i)
+      if (s_lam[i] > s_lam[j] || (s_lam[i] == s_lam[j] && i < j)) ++r;
+    s_rank[j] = r;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {   // VQ (sorted columns)
+    int i = idx / b, j = idx % b;
+    VQ[i * LM + s_rank[j]] = Vm[i * LM + j];
+  }
+  for (int j = threadIdx.x; j < b; j += blockDim.x) sig[s_rank[j]] = sqrt(fmax(s_lam[j], 0.0));
+  __syncthreads();
+  // U_Q = Q V_Q Sigma^{-1}
+  zgemm<false, false>(UQ, LM, Q, LM, VQ, LM, a, b, b);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < a * b; idx += blockDim.x) {
+    int i = idx / b, j = idx % b;
+    double sj = sig[j];
+    UQ[i * LM + j] = sj > 0.0 ? cscale(UQ[i * LM + j], 1.0 / sj) : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  // S_l = U_Q^* (M_l V_Q) Sigma^{-1}
+  for (int l = 0; l < p.d; ++l) {
+    const double2* Ml = (const double2*)(sb + D.L.mproj) + (size_t)l * LR * LM;
+    double2* S = (double2*)(sb + D.L.S) + (size_t)l * LM * LM;
+    zgemm<false, false>(T1, LM, Ml, LM, VQ, LM, a, b, b);
+    __syncthreads();
+    zgemm<true, false>(S, LM, UQ, LM, T1, LM, b, b, a);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+      int i = idx / b, j = idx % b;
+      double sj = sig[j];
+      S[i * LM + j] = sj > 0.0 ? cscale(S[i * LM + j], 1.0 / sj) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st.sigma_ratio = sig[0] > 0.0 ? sig[b - 1] / sig[0] : 0.0;
+    if (sweep >= 30) set_status_e(st, ST_ENOCONV);
+  }
+}
+
+// Canonical phases: ph_j = v_j[argmax] / |.| of V_final = V V_Q (in B1); S_l <- D^* S_l D with
+// D = diag(conj ph); U_Q, V_Q columns times conj(ph).
+__global__ void k_canon(Dev D) {
+  const ProbDesc& p = D.P[blockIdx.x];
+  ProbState& st = D.st[blockIdx.x];
+  const int b = st.wv, a = st.wu;
+  const int LM = D.L.LDM;
+  __shared__ double2 ph[PRONY_MMAX];
+  const unsigned long long* am = (const unsigned long long*)(D.small + p.soff + D.L.argmx);
+  for (int j = threadIdx.x; j < b; j += blockDim.x) {
+    unsigned row = am[j] == 0ull ? 0u : 0xFFFFFFFFu - (unsigned)(am[j] & 0xFFFFFFFFull);
+    if (row >= (unsigned)p.N) row = 0u;
+    float2 v = D.B1[p.xoff + (long long)j * p.N + row];
+    double r = hypot((double)v.x, (double)v.y);
+    ph[j] = r > 0.0 ? make_double2(v.x / r, v.y / r) : make_double2(1.0, 0.0);
+    ((double2*)(D.small + p.soff + D.L.phase))[j] = ph[j];
+  }
+  __syncthreads();
+  for (int l = 0; l < p.d; ++l) {
+    double2* S = (double2*)(D.small + p.soff + D.L.S) + (size_t)l * LM * LM;
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+      int i = idx / b, j = idx % b;
+      S[i * LM + j] = cmul(cmul(ph[i], S[i * LM + j]), cconj(ph[j]));
+    }
+  }
+  double2* UQ = (double2*)(D.small + p.soff + D.L.uq);
+  double2* VQ = (double2*)(D.small + p.soff + D.L.vq);
+  for (int idx = threadIdx.x; idx < a * b; idx += blockDim.x) {
+    int i = idx / b, j = idx % b;
+    UQ[i * LM + j] = cmul(UQ[i * LM + j], cconj(ph[j]));
+  }
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+    int i = idx / b, j = idx % b;
+    VQ[i * LM + j] = cmul(VQ[i * LM + j], cconj(ph[j]));
+  }
+}
+
+// ----------------------------------------------------------------------------- eigen step
+__global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
+  extern __shared__ float2 esm[];
+  __shared__ double2 mu[PRONY_DMAX];
+  __shared__ float2 hv[PRONY_MMAX];
+  __shared__ float2 sv[PRONY_MMAX];
+  __shared__ float s_norm;
+  __shared__ int s_fail, s_pr;
+  const ProbDesc& p = D.P[blockIdx.x];
+  ProbState& st = D.st[blockIdx.x];
+  if (st.status == ST_ENAN) return;
+  const int m = st.wv;
+  if (m <= 0) return;
+  const int LM = D.L.LDM;
+  const int LD = m;                             // smem leading dimension
+  float2* H = esm;                              // m x m  (C_mu, then Schur form, then W^{-1} work)
+  float2* Z = esm + LD * LD;                    // m x m  (Schur vectors, then W)
+  float2* Y = Z + LD * LD;                      // m x m  (triangular eigenvectors, then W^{-1})
+  char* sb = D.small + p.soff;
+  const double2* S = (const double2*)(sb + D.L.S);
+  double2* Cd = (double2*)(sb + D.L.work1);     // C_mu (FP64), then S_l W
+  double2* Wd = (double2*)(sb + D.L.work2);     // W (FP64)
+  double2* Xd = (double2*)(sb + D.L.work3);     // W^{-1} (FP64)
+  double2* Rd = (double2*)(sb + D.L.work4);     // scratch
+  if (threadIdx.x == 0) {
+    double nrm = 0.0;
+    for (int l = 0; l < p.d; ++l) {
+      uint64_t c[4] = {(uint64_t)l, 0, 0, 0};
+      philox4x64(c, seed, PRONY_STREAM_MU);
+      double u0 = philox_u01(c[0]), u1 = philox_u01(c[1]);
+      double r = sqrt(-log(u0)), sn, cs;
+      sincospi(2.0 * u1, &sn, &cs);
+      mu[l] = make_double2(r * cs, r * sn);
+      nrm += cabs2(mu[l]);
+    }
+    nrm = sqrt(nrm);
+    for (int l = 0; l < p.d; ++l) mu[l] = cscale(mu[l], 1.0 / nrm);
+    s_fail = 0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    int i = idx / m, j = idx % m;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < p.d; ++l) acc = cadd(acc, cmul(mu[l], S[(size_t)l * LM * LM + i * LM + j]));
+    Cd[i * LM + j] = acc;
+    H[i * LD + j] = fc((float)acc.x, (float)acc.y);
+    Z[i * LD + j] = fc(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  // ---- FP32 Householder reduction to Hessenberg form
+  for (int k = 0; k + 2 < m; ++k) {
+    if (threadIdx.x == 0) {
+      float nx = 0.f;
+      for (int i = k + 1; i < m; ++i) nx += fabs2(H[i * LD + k]);
+      nx = sqrtf(nx);
+      float2 x0 = H[(k + 1) * LD + k];
+      float ax0 = sqrtf(fabs2(x0));
+      float2 ph = ax0 > 0.f ? fscale(x0, 1.f / ax0) : fc(1.f, 0.f);
+      float2 alpha = fscale(ph, -nx);
+      for (int i = 0; i < m; ++i) hv[i] = fc(0.f, 0.f);
+      for (int i = k + 1; i < m; ++i) hv[i] = H[i * LD + k];
+      hv[k + 1] = fsub(hv[k + 1], alpha);
+      float nv = 0.f;
+      for (int i = k + 1; i < m; ++i) nv += fabs2(hv[i]);
+      s_norm = nv;
+      if (nv > 0.f) {
+        float inv = rsqrtf(nv);
+        for (int i = k + 1; i < m; ++i) hv[i] = fscale(hv[i], inv);
+      }
+    }
+    __syncthreads();
+    if (s_norm > 0.f) {
+      for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        float2 s = fc(0.f, 0.f);
+        for (int i = k + 1; i < m; ++i) s = fadd(s, fmulc(hv[i], H[i * LD + j]));
+        sv[j] = s;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < (m - k - 1) * m; idx += blockDim.x) {
+        int i = k + 1 + idx / m, j = idx % m;
+        H[i * LD + j] = fsub(H[i * LD + j], fscale(fmul(hv[i], sv[j]), 2.f));
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
+        float2* R = i < m ? H : Z;
+        int ii = i < m ? i : i - m;
+        float2 s = fc(0.f, 0.f);
+        for (int j = k + 1; j < m; ++j) s = fadd(s, fmul(R[ii * LD + j], hv[j]));
+        for (int j = k + 1; j < m; ++j) R[ii * LD + j] = fsub(R[ii * LD + j], fscale(fmul(s, fconj(hv[j])), 2.f));
+      }
+      __syncthreads();
+      for (int i = k + 2 + threadIdx.x; i < m; i += blockDim.x) H[i * LD + k] = fc(0.f, 0.f);
+      __syncthreads();
+    }
+  }
+  // ---- FP32 shifted complex QR iteration (one warp), full Schur form
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const float eps = 5.9604645e-8f;
+    int hi = m - 1, its = 0, total = 0;
+    const int cap = 30 * m + 30;
+    while (hi > 0) {
+      if (total > cap) break;
+      int l = hi;
+      for (; l > 0; --l) {
+        float s = fabs1(H[(l - 1) * LD + l - 1]) + fabs1(H[l * LD + l]);
+        if (s == 0.f) s = 1.f;
+        if (fabs1(H[l * LD + l - 1]) <= eps * s) break;
+      }
+      if (l > 0 && lane == 0) H[l * LD + l - 1] = fc(0.f, 0.f);
+      __syncwarp();
+      if (l == hi) {
+        --hi;
+        its = 0;
+        continue;
+      }
+      float2 sh;
+      if (its == 10 || its == 20) {
+        sh = fadd(H[hi * LD + hi], fc(0.75f * fabs1(H[hi * LD + hi - 1]), 0.f));
+      } else {
+        float2 a = H[(hi - 1) * LD + hi - 1], bb = H[(hi - 1) * LD + hi], c = H[hi * LD + hi - 1], dd = H[hi * LD + hi];
+        float2 hd = fscale(fsub(a, dd), 0.5f);
+        float2 disc = fsqrtc(fadd(fmul(hd, hd), fmul(bb, c)));
+        float2 mid = fscale(fadd(a, dd), 0.5f);
+        float2 l1 = fadd(mid, disc), l2 = fsub(mid, disc);
+        sh = fabs2(fsub(l1, dd)) <= fabs2(fsub(l2, dd)) ? l1 : l2;
+      }
+      float2 x = fsub(H[l * LD + l], sh), y = H[(l + 1) * LD + l];
+      for (int k = l; k < hi; ++k) {
+        if (k > l) {
+          x = H[k * LD + k - 1];
+          y = H[(k + 1) * LD + k - 1];
+        }
+        float ax = sqrtf(fabs2(x)), ay = sqrtf(fabs2(y));
+        float nr = hypotf(ax, ay);
+        float c;
+        float2 s;
+        if (nr == 0.f) {
+          c = 1.f;
+          s = fc(0.f, 0.f);
+        } else if (ax == 0.f) {
+          c = 0.f;
+          s = fscale(fconj(y), 1.f / ay);
+        } else {
+          c = ax / nr;
+          s = fscale(fmul(fscale(x, 1.f / ax), fconj(y)), 1.f / nr);
+        }
+        for (int j = max(l, k - 1) + lane; j < m; j += 32) {
+          float2 rk = H[k * LD + j], rk1 = H[(k + 1) * LD + j];
+          H[k * LD + j] = fadd(fscale(rk, c), fmul(s, rk1));
+          H[(k + 1) * LD + j] = fsub(fscale(rk1, c), fmul(fconj(s), rk));
+        }
+        __syncwarp();
+        int rmax = min(k + 2, hi);
+        for (int i = lane; i <= rmax; i += 32) {
+          float2 ck = H[i * LD + k], ck1 = H[i * LD + k + 1];
+          H[i * LD + k] = fadd(fscale(ck, c), fmul(fconj(s), ck1));
+          H[i * LD + k + 1] = fsub(fscale(ck1, c), fmul(s, ck));
+        }
+        for (int i = lane; i < m; i += 32) {
+          float2 ck = Z[i * LD + k], ck1 = Z[i * LD + k + 1];
+          Z[i * LD + k] = fadd(fscale(ck, c), fmul(fconj(s), ck1));
+          Z[i * LD + k + 1] = fsub(fscale(ck1, c), fmul(s, ck));
+        }
+        __syncwarp();
+      }
+      ++its;
+      ++total;
+    }
+    if (lane == 0 && hi > 0) s_fail = 1;
+  }
+  __syncthreads();
+  if (s_fail && threadIdx.x == 0) set_status_e(st, ST_ENOCONV);
+  // ---- triangular eigenvectors (FP32), W = Z Y with unit columns
+  if (threadIdx.x == 0) {
+    float hn = 0.f;
+    for (int i = 0; i < m; ++i)
+      for (int j = i; j < m; ++j) hn = fmaxf(hn, fabs1(H[i * LD + j]));
+    s_norm = hn;
+  }
+  __syncthreads();
+  const float small = fmaxf(s_norm, 1e-30f) * 5.9604645e-8f;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    float2 lam = H[k * LD + k];
+    for (int i = k + 1; i < m; ++i) Y[i * LD + k] = fc(0.f, 0.f);
+    Y[k * LD + k] = fc(1.f, 0.f);
+    for (int i = k - 1; i >= 0; --i) {
+      float2 s = fc(0.f, 0.f);
+      for (int j = i + 1; j <= k; ++j) s = fadd(s, fmul(H[i * LD + j], Y[j * LD + k]));
+      float2 den = fsub(H[i * LD + i], lam);
+      if (fabs1(den) < small) den = fc(small, 0.f);
+      Y[i * LD + k] = fdiv(fc(-s.x, -s.y), den);
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    int i = idx / m, k = idx % m;
+    float2 acc = fc(0.f, 0.f);
+    for (int j = 0; j <= k; ++j) acc = fadd(acc, fmul(Z[i * LD + j], Y[j * LD + k]));
+    H[i * LD + k] = acc;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    float s = 0.f;
+    for (int i = 0; i < m; ++i) s += fabs2(H[i * LD + k]);
+    sv[k] = fc(s > 0.f ? rsqrtf(s) : 1.f, 0.f);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    int i = idx / m, k = idx % m;
+    float2 w = fscale(H[i * LD + k], sv[k].x);
+    Z[i * LD + k] = w;                                  // W (FP32) for the inverse
+    Wd[i * LM + k] = make_double2(w.x, w.y);            // W (FP64, exactly the same numbers)
+    Y[i * LD + k] = fc(i == k ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  // ---- FP32 Gauss-Jordan inverse of W (partial pivoting): Z -> I, Y -> W^{-1}
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      int pr = k;
+      float best = fabs1(Z[k * LD + k]);
+      for (int i = k + 1; i < m; ++i) {
+        float v = fabs1(Z[i * LD + k]);
+        if (v > best) { best = v; pr = i; }
+      }
+      s_pr = pr;
+      if (best == 0.f) s_fail = 2;
+    }
+    __syncthreads();
+    const int pr = s_pr;
+    if (pr != k) {
+      for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        float2 t = Z[k * LD + j]; Z[k * LD + j] = Z[pr * LD + j]; Z[pr * LD + j] = t;
+        t = Y[k * LD + j]; Y[k * LD + j] = Y[pr * LD + j]; Y[pr * LD + j] = t;
+      }
+      __syncthreads();
+    }
+    float2 piv = Z[k * LD + k];
+    if (fabs1(piv) == 0.f) piv = fc(1e-30f, 0.f);
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      Z[k * LD + j] = fdiv(Z[k * LD + j], piv);
+      Y[k * LD + j] = fdiv(Y[k * LD + j], piv);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) hv[i] = (i == k) ? fc(0.f, 0.f) : Z[i * LD + k];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      int i = idx / m, j = idx % m;
+      if (i == k) continue;
+      float2 f = hv[i];
+      Z[i * LD + j] = fsub(Z[i * LD + j], fmul(f, Z[k * LD + j]));
+      Y[i * LD + j] = fsub(Y[i * LD + j], fmul(f, Y[k * LD + j]));
+    }
+    __syncthreads();
+  }
+  // ---- FP64: X = W^{-1} refined by Newton-Schulz X <- X (2I - W X)
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    int i = idx / m, j = idx % m;
+    float2 x = Y[i * LD + j];
+    Xd[i * LM + j] = make_double2(x.x, x.y);
+  }
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    zgemm<false, false>(Rd, LM, Wd, LM, Xd, LM, m, m, m);            // W X
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      int i = idx / m, j = idx % m;
+      double2 r = Rd[i * LM + j];
+      Rd[i * LM + j] = make_double2((i == j ? 2.0 : 0.0) - r.x, -r.y);
+    }
+    __syncthreads();
+    zgemm<false, false>(Cd, LM, Xd, LM, Rd, LM, m, m, m);            // X (2I - W X)
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      int i = idx / m, j = idx % m;
+      Xd[i * LM + j] = Cd[i * LM + j];
+    }
+    __syncthreads();
+  }
+  // ---- z_j(l) = sum_a X[j][a] (S_l W)[a][j];  t = -arg z / 2 pi  mod 1
+  double* tout = (double*)(sb + D.L.t);
+  for (int l = 0; l < p.d; ++l) {
+    zgemm<false, false>(Cd, LM, S + (size_t)l * LM * LM, LM, Wd, LM, m, m, m);
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+      for (int a = 0; a < m; ++a) acc[a & 3] = cadd(acc[a & 3], cmul(Xd[j * LM + a], Cd[a * LM + j]));
+      double2 z = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+      double tj = -atan2(z.y, z.x) / 6.283185307179586;
+      tj -= floor(tj);
+      if (tj >= 1.0) tj = 0.0;
+      tout[j * PRONY_DMAX + l] = tj;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && s_fail == 2) set_status_e(st, ST_ENOCONV);
+  if (threadIdx.x == 0) st.rank_used = m;
+}
+
+}  // namespace
+
+void launch_svd_S(const Dev& D, cudaStream_t s) {
+  static size_t set = 0;
+  size_t sm = sizeof(float2) * ((size_t)D.L.LDM * D.L.LDR + (size_t)D.L.LDM * D.L.LDM);
+  if (sm > set) {
+    cudaFuncSetAttribute(k_svd_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = sm;
+  }
+  note_launch();
+  k_svd_S<<<D.nprob, 256, sm, s>>>(D);
+}
+
+void launch_canon(const Dev& D, cudaStream_t s) {
+  note_launch();
+  k_canon<<<D.nprob, 256, 0, s>>>(D);
+}
+
+void launch_eig_t(const Dev& D, unsigned long long seed, cudaStream_t s) {
+  static size_t set = 0;
+  size_t sm = sizeof(float2) * 3 * (size_t)D.maxM * D.maxM;
+  if (sm > set) {
+    cudaFuncSetAttribute(k_eig_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1024));
+    set = sm;
+  }
+  note_launch();
+  k_eig_t<<<D.nprob, 256, std::max<size_t>(sm, 16), s>>>(D, seed);
+}

@@ -123,15 +123,21 @@ __global__ void k_init_v0(Dev D, unsigned long long seed) {
   }
 }
 
+// Clears a block of the small workspace of every problem still iterating (a stopped problem keeps
+// the Q and U^* T_l V of its last iteration).
 __global__ void k_zero_small(Dev D, long long off, long long bytes) {
+  if (D.st[blockIdx.y].done) return;
   const ProbDesc& p = D.P[blockIdx.y];
   unsigned int* b = (unsigned int*)(D.small + p.soff + off);
   for (long long i = blockIdx.x * blockDim.x + threadIdx.x; i < bytes / 4; i += gridDim.x * blockDim.x) b[i] = 0u;
 }
 
 // ----------------------------------------------------------------------------- tall-skinny Gram
+// out[a][b] += sum_r conj(X[r, a]) Z[r, b] over a block of GRAM_CHUNK rows.  Each thread owns a
+// 2x2 tile of (a, b) and a residue class of rows; partial sums (FP32) meet in shared memory and
+// each block adds its totals to the FP64 output with one atomic per entry.
 constexpr int GRAM_ROWS = 32;       // rows staged per pass
-constexpr int GRAM_CHUNK = 256;     // rows per block
+constexpr int GRAM_CHUNK = 512;     // rows per block
 
 __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
                                               long long out_off, int out_ld) {
@@ -144,77 +150,79 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
   const int r_begin = blockIdx.x * GRAM_CHUNK;
   if (r_begin >= p.N || a <= 0 || b <= 0) return;
   const int r_end = min(p.N, r_begin + GRAM_CHUNK);
+  const int LR = D.L.LDR;
   float2* Xs = smem;                              // [a][GRAM_ROWS]
-  float2* Zs = smem + PRONY_RMAX * GRAM_ROWS;     // [b][GRAM_ROWS]
+  float2* Zs = smem + LR * GRAM_ROWS;             // [b][GRAM_ROWS]
+  float* acc_s = (float*)(smem + 2 * LR * GRAM_ROWS);   // [a][b] complex as 2 floats
   int ldx, ldz;
   const float2* X = buf_base(D, xbuf, p, ldx);
   const float2* Z = buf_base(D, zbuf, p, ldz);
-  const int na = (a + 3) >> 2, nb = (b + 3) >> 2, ntile = na * nb;
-  constexpr int TPT = 4;  // tiles per thread (up to 32 x 32 tiles)
-  float2 acc[TPT][4][4];
-#pragma unroll
-  for (int t = 0; t < TPT; ++t)
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[t][i][j] = make_float2(0.f, 0.f);
-
+  const int na = (a + 1) >> 1, nb = (b + 1) >> 1, ntile = na * nb;
+  const int RG = max(1, min(GRAM_ROWS, (int)blockDim.x / ntile));
+  const int tile = threadIdx.x % ntile, grp = threadIdx.x / ntile;
+  const bool active = grp < RG && (int)threadIdx.x < ntile * RG;
+  const int ta = tile / nb, tb = tile % nb;
+  for (int e = threadIdx.x; e < 2 * a * b; e += blockDim.x) acc_s[e] = 0.f;
+  float2 acc[2][2] = {{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}};
   for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < PRONY_RMAX * GRAM_ROWS; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < (a + b) * GRAM_ROWS; idx += blockDim.x) {
       int rr = idx % GRAM_ROWS, col = idx / GRAM_ROWS;
       int r = r0 + rr;
-      float2 vx = make_float2(0.f, 0.f), vz = make_float2(0.f, 0.f);
-      if (r < r_end) {
-        if (col < a) vx = X[(long long)col * ldx + buf_row(xbuf, p, r, xshift)];
-        if (col < b) vz = Z[(long long)col * ldz + buf_row(zbuf, p, r, zshift)];
+      if (col < a) {
+        Xs[col * GRAM_ROWS + rr] =
+            r < r_end ? X[(long long)col * ldx + buf_row(xbuf, p, r, xshift)] : make_float2(0.f, 0.f);
+      } else {
+        int cz = col - a;
+        Zs[cz * GRAM_ROWS + rr] =
+            r < r_end ? Z[(long long)cz * ldz + buf_row(zbuf, p, r, zshift)] : make_float2(0.f, 0.f);
       }
-      Xs[col * GRAM_ROWS + rr] = vx;
-      Zs[col * GRAM_ROWS + rr] = vz;
     }
     __syncthreads();
+    if (active) {
+      const int ia0 = 2 * ta, jb0 = 2 * tb;
+      for (int rr = grp; rr < GRAM_ROWS; rr += RG) {
+        float2 xa[2], zb[2];
 #pragma unroll
-    for (int t = 0; t < TPT; ++t) {
-      int tile = threadIdx.x + t * blockDim.x;
-      if (tile >= ntile) break;
-      int ta = tile / nb, tb = tile % nb;
-      for (int rr = 0; rr < GRAM_ROWS; ++rr) {
-        float2 xa[4], zb[4];
+        for (int i = 0; i < 2; ++i) xa[i] = ia0 + i < a ? Xs[(ia0 + i) * GRAM_ROWS + rr] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) xa[i] = Xs[(4 * ta + i) * GRAM_ROWS + rr];
+        for (int j = 0; j < 2; ++j) zb[j] = jb0 + j < b ? Zs[(jb0 + j) * GRAM_ROWS + rr] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) zb[j] = Zs[(4 * tb + j) * GRAM_ROWS + rr];
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            acc[t][i][j].x += xa[i].x * zb[j].x + xa[i].y * zb[j].y;
-            acc[t][i][j].y += xa[i].x * zb[j].y - xa[i].y * zb[j].x;
+          for (int j = 0; j < 2; ++j) {
+            acc[i][j].x += xa[i].x * zb[j].x + xa[i].y * zb[j].y;
+            acc[i][j].y += xa[i].x * zb[j].y - xa[i].y * zb[j].x;
           }
       }
     }
   }
-  double2* out = (double2*)(D.small + p.soff + out_off);
+  __syncthreads();
+  if (active) {
 #pragma unroll
-  for (int t = 0; t < TPT; ++t) {
-    int tile = threadIdx.x + t * blockDim.x;
-    if (tile >= ntile) break;
-    int ta = tile / nb, tb = tile % nb;
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        int ia = 4 * ta + i, jb = 4 * tb + j;
+      for (int j = 0; j < 2; ++j) {
+        int ia = 2 * ta + i, jb = 2 * tb + j;
         if (ia < a && jb < b) {
-          atomicAdd(&out[ia * out_ld + jb].x, (double)acc[t][i][j].x);
-          atomicAdd(&out[ia * out_ld + jb].y, (double)acc[t][i][j].y);
+          atomicAdd(&acc_s[2 * (ia * b + jb)], acc[i][j].x);
+          atomicAdd(&acc_s[2 * (ia * b + jb) + 1], acc[i][j].y);
         }
       }
+  }
+  __syncthreads();
+  double2* out = (double2*)(D.small + p.soff + out_off);
+  for (int e = threadIdx.x; e < a * b; e += blockDim.x) {
+    int ia = e / b, jb = e % b;
+    atomicAdd(&out[ia * out_ld + jb].x, (double)acc_s[2 * e]);
+    atomicAdd(&out[ia * out_ld + jb].y, (double)acc_s[2 * e + 1]);
   }
 }
 
 // ----------------------------------------------------------------------------- X M products
-constexpr int APPLY_ROWS = 32;
+// OUT[r, j] = sum_i X[r, i] M[i][j] (- Z[r, j] with OUT = Z - X M for the residual), 64 rows per
+// block; M is staged once per block, each thread takes one row and every fourth column.
+constexpr int APPLY_ROWS = 64;
 
 __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw, long long m_off, int m_double,
                                                int zbuf, int outbuf, int norm_only) {
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
   const int r0 = blockIdx.x * APPLY_ROWS;
   if (r0 >= p.N || b <= 0) return;
   float2* Ms = smem;                              // [a][b]  (ld b)
-  float2* Xs = smem + PRONY_RMAX * PRONY_RMAX;    // [a][APPLY_ROWS]
+  float2* Xs = smem + D.L.LDR * D.L.LDR;          // [a][APPLY_ROWS]
   for (int idx = threadIdx.x; idx < a * b; idx += blockDim.x) {
     int i = idx / b, j = idx % b;
     float2 v;
@@ -249,13 +257,14 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
   }
   __syncthreads();
   const int rr = threadIdx.x % APPLY_ROWS, cg = threadIdx.x / APPLY_ROWS;
+  const int ngrp = blockDim.x / APPLY_ROWS;
   const int r = r0 + rr;
   int ldz = 0, ldo = 0;
   const float2* Z = zbuf >= 0 ? buf_base(D, zbuf, p, ldz) : nullptr;
   float2* O = norm_only ? nullptr : buf_base(D, outbuf, p, ldo);
   double nrm = 0.0;
   if (r < p.N) {
-    for (int j = cg; j < b; j += blockDim.x / APPLY_ROWS) {
+    for (int j = cg; j < b; j += ngrp) {
       float2 acc = make_float2(0.f, 0.f);
       for (int i = 0; i < a; ++i) {
         float2 x = Xs[i * APPLY_ROWS + rr], mm = Ms[i * b + j];
@@ -416,22 +425,6 @@ __global__ void k_copy_cols(Dev D, int buf, int wsel, double2* out) {
 }
 
 // ----------------------------------------------------------------------------- exponential sum (Eq. 1)
-struct Box { int lo[PRONY_DMAX]; int len[PRONY_DMAX]; };
-
-__device__ inline void box_point(const Box& B, int d, long long q, int* k) {
-  for (int l = d - 1; l >= 0; --l) {
-    k[l] = B.lo[l] + (int)(q % B.len[l]);
-    q /= B.len[l];
-  }
-}
-
-// Phase <t_j, k> mod 1 from 64-bit binary fractions (exact), centred to [-1/2, 1/2).
-__device__ inline float centred_phase(const uint64_t* T, const int* k, int d) {
-  uint64_t acc = 0;
-  for (int l = 0; l < d; ++l) acc += T[l] * (uint64_t)(long long)k[l];
-  return (float)(int)(acc >> 32) * 2.3283064365386963e-10f;
-}
-
 __global__ void __launch_bounds__(256) k_expsum_fwd(const double* t, const float2* c, int m, int d, Box B,
                                                     long long K, float2* f) {
   __shared__ uint64_t T[PRONY_MMAX * PRONY_DMAX];
@@ -547,11 +540,11 @@ void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_
 
 void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
                  int out_ld, cudaStream_t s) {
-  static bool attr = false;
-  size_t sm = sizeof(float2) * 2 * PRONY_RMAX * GRAM_ROWS;
-  if (!attr) {
+  static size_t set = 0;
+  size_t sm = sizeof(float2) * (2 * (size_t)D.L.LDR * GRAM_ROWS + (size_t)D.L.LDR * D.L.LDR);
+  if (sm > set) {
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
+    set = sm;
   }
   dim3 g((D.maxN + GRAM_CHUNK - 1) / GRAM_CHUNK, D.nprob);
   note_launch();
@@ -560,11 +553,11 @@ void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshif
 
 void launch_apply(const Dev& D, int xbuf, int xw, int outw, long long m_off, int m_double, int zbuf, int outbuf,
                   int norm_only, cudaStream_t s) {
-  static bool attr = false;
-  size_t sm = sizeof(float2) * (PRONY_RMAX * PRONY_RMAX + PRONY_RMAX * APPLY_ROWS);
-  if (!attr) {
+  static size_t set = 0;
+  size_t sm = sizeof(float2) * ((size_t)D.L.LDR * D.L.LDR + (size_t)D.L.LDR * APPLY_ROWS);
+  if (sm > set) {
     cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
+    set = sm;
   }
   dim3 g((D.maxN + APPLY_ROWS - 1) / APPLY_ROWS, D.nprob);
   note_launch();
@@ -597,12 +590,6 @@ void launch_gather_out(const Dev& D, double* t_out, double2* c_out, cudaStream_t
 void launch_copy_cols(const Dev& D, int buf, int w_sel, double2* out, cudaStream_t s) {
   note_launch();
   k_copy_cols<<<64, 256, 0, s>>>(D, buf, w_sel, out);
-}
-
-static Box make_box(int d, const int* lo, const int* len) {
-  Box B = {};
-  for (int l = 0; l < d; ++l) { B.lo[l] = lo[l]; B.len[l] = len[l]; }
-  return B;
 }
 
 void launch_expsum_fwd(const double* t, const float2* c, int m, int d, const int* lo, const int* len, long long K,

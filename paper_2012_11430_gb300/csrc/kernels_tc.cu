@@ -8,12 +8,24 @@
 // a + b <= NPL - 1 are accumulated in FP32 in tensor memory (3 products for two planes,
 // 6 for three planes, which represent FP32 inputs exactly).
 //
+// B' depends on the problem and the K chunk only, so one small kernel (k_xb_prep) writes its
+// planes once per product, K-major, and the CTAs read them with 2-D TMA in the 128-byte swizzle
+// layout of the MMA.  The CTAs of a thread-block cluster work on consecutive 128-row tiles of
+// the same problem and K range: each loads a share of every B' stage and multicasts it to all,
+// which divides the L2 -> SM traffic of B' by the cluster size.
+//
 // One CTA = 128 output rows x all 2w columns x a range of K chunks.  Warp roles:
-//   warp 0  TMA: the sample-grid window (one bulk copy) and the B' tiles (2-D tiled, 128B swizzle)
-//   warp 1  MMA issue (one thread), tcgen05.commit to the stage barriers
-//   warps 2-5  generate the Toeplitz A' tile of each chunk from the window in shared memory and
-//           write its BF16 planes straight into tensor memory (tcgen05.st); then the epilogue
+//   warp 0      TMA: the CTA's window of the split-plane sample tables (cp.async.bulk) and its
+//               share of the B' stages (multicast)
+//   warp 1      MMA issue (one thread): tcgen05.mma, A from tensor memory, B from shared memory
+//   warps 2-9   A' producers: each chunk's Toeplitz tile is gathered from the window (its BF16
+//               planes are split once per solve, k_split_tables, two input points per word) and
+//               written straight into tensor memory (tcgen05.st); two warps per TMEM
+//               lane quadrant, each taking half of the chunk's input points; then the epilogue
 // The Toeplitz matrix is never formed in HBM: each A' element is F at grid index gk(k) - gh(h).
+// Stages of A (TMEM) and B (shared memory) form an mbarrier pipeline; every wait is bounded.
+// A CTA whose tile lies past the last row of its problem (a cluster filler) only loads and
+// releases its share of B'.
 #include "common.cuh"
 #include "tc_ptx.cuh"
 
@@ -27,7 +39,11 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr uint32_t TC_SPIN = 1u << 24;      // bounded mbarrier polls (~seconds)
-constexpr int TC_A_COL0 = 256;              // TMEM: D in columns [0, 256), A stages from 256
+constexpr int TC_MAXSTAGE = 8;
+constexpr int TC_APROD = 8;                 // A' warps (two per TMEM lane quadrant)
+constexpr int TC_THREADS = 32 * (2 + TC_APROD);
+constexpr int TC_BOXR = 16;                // rows of one B' TMA box
+constexpr int TC_MAXCH = 512;               // K chunks per CTA (host splits K to stay below)
 
 __device__ inline int tc_width(const ProbState& s, const ProbDesc& p, int sel) {
   switch (sel) {
@@ -85,7 +101,14 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t* w) {
   }
 }
 
-// X (N x w complex64, column-major) -> B' planes: row 2j / 2j+1 of plane p, K index 64c + q.
+// byte offset of BF16 element (row, k) of a K-major tile of 64-element rows, 128-byte swizzle
+__device__ __forceinline__ uint32_t sw128(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 3) ^ (row & 7)) << 4) | ((k & 7) << 1)));
+}
+
+// X (N x w complex64, column-major) -> B' planes, K-major: plane pl of problem pi, row 2j / 2j+1,
+// K index 64c + q (q < 32: Re-F block of input point 32c + q, q >= 32: Im-F block).  Rows of a
+// problem from 2w up to its MMA width NT are zero.
 __global__ void k_xb_prep(Dev D, int xbuf, int wsel, uint16_t* xb, int npl, int ntbox, int kpitch) {
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
@@ -97,20 +120,19 @@ __global__ void k_xb_prep(Dev D, int xbuf, int wsel, uint16_t* xb, int npl, int 
   int ldx;
   const float2* X = tc_buf(D, xbuf, p, ldx);
   uint16_t* out = xb + (size_t)pi * npl * ntbox * kpitch;
-  const long long total = (long long)nt * nc * 32;        // (row, chunk, point-in-chunk)
+  const long long total = (long long)nt * nc * 32;        // (row, chunk, point in chunk)
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
-    int jj = (int)(q % 32);
-    long long t = q / 32;
-    int c = (int)(t % nc);
-    int row = (int)(t / nc);
-    int h = 32 * c + jj;
-    int j = row >> 1;
-    float2 x = (h < p.N && j < w) ? X[(long long)j * ldx + h] : make_float2(0.f, 0.f);
-    float vr, vi;                          // value in the Re-F block (q < 32) and the Im-F block (q >= 32)
+    const int jj = (int)(q % 32);
+    const long long t = q / 32;
+    const int c = (int)(t % nc);
+    const int row = (int)(t / nc);
+    const int h = 32 * c + jj;
+    const int j = row >> 1;
+    const float2 x = (h < p.N && j < w) ? X[(long long)j * ldx + h] : make_float2(0.f, 0.f);
+    float vr, vi;                          // value in the Re-F block and in the Im-F block
     if ((row & 1) == 0) { vr = x.x; vi = -x.y; }
     else { vr = x.y; vi = x.x; }
-    // split both values; planes stored at [plane][row][kpitch]
     uint32_t wr[3];
     if (npl == 3) split_pair<3>(vr, vi, wr);
     else split_pair<2>(vr, vi, wr);
@@ -122,24 +144,55 @@ __global__ void k_xb_prep(Dev D, int xbuf, int wsel, uint16_t* xb, int npl, int 
   }
 }
 
+// Split planes of the sample grid, paired with the preceding entry (the A' operand of two
+// consecutive input points on a grid line is one table word).  One pass per solve.
+__global__ void k_split_tables(Dev D) {
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < p.Gd4; x += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const float2* F = (side ? D.gH : D.gF) + p.grid;
+      uint32_t* tab = (side ? D.tabH : D.tabF) + p.toff;
+      const float2 v = x < p.Gd ? F[x] : make_float2(0.f, 0.f);
+      const float2 v1 = (x >= 1 && x - 1 < p.Gd) ? F[x - 1] : make_float2(0.f, 0.f);
+      uint32_t wr[3], wi[3];
+      split_pair<3>(v.x, v1.x, wr);
+      split_pair<3>(v.y, v1.y, wi);
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl) {
+        tab[(long long)pl * p.Gd4 + x] = wr[pl];
+        tab[(long long)(3 + pl) * p.Gd4 + x] = wi[pl];
+      }
+    }
+  }
+}
+
 struct TcParams {
-  int adjoint, xbuf_unused, wsel, ybuf, y_ext;
-  int ntbox, kpitch, win_cap;     // TMA box rows, K pitch of B', window capacity (float2 entries)
-  int stages;
+  int adjoint, wsel, ybuf, y_ext;
+  int ntbox;                      // B' rows reserved per plane and problem (>= every NT)
+  int win_cap;                    // window capacity (words per table, a multiple of 4)
+  int stages;                     // pipeline depth (A stages in TMEM, B stages in shared memory)
+  int acol0;                      // first TMEM column of the A stages (D uses [0, acol0))
+  int cs;                         // cluster size (CTAs sharing the B' stages)
 };
 
 template <int NPL>
-__global__ void __launch_bounds__(192, 1) k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P,
-                                                        const __grid_constant__ CUtensorMap bmap, int* err) {
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P, const __grid_constant__ CUtensorMap bmap, int* err) {
   constexpr int NPROD = NPL == 3 ? 6 : 3;
   constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
   constexpr int PB[6] = {0, 1, 0, 2, 1, 0};
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t bar_win, bar_d;
-  __shared__ uint64_t bar_bfull[4], bar_afull[4], bar_empty[4];
+  __shared__ uint64_t bar_bfull[TC_MAXSTAGE], bar_afull[TC_MAXSTAGE], bar_aempty[TC_MAXSTAGE],
+      bar_bempty[TC_MAXSTAGE];
   __shared__ uint32_t s_tmem;
   __shared__ int s_err;
+  __shared__ int ghalf[2 * TC_MAXCH];   // grid offset of each half chunk on one grid line, else -1
 
+  // Everything that decides an early return depends on the problem and K range only, which the
+  // CTAs of a cluster share, so a cluster returns as a whole.
   const ToeplitzJob job = jobs[blockIdx.x];
   const ProbDesc& p = D.P[job.prob];
   const ProbState& st = D.st[job.prob];
@@ -149,7 +202,6 @@ __global__ void __launch_bounds__(192, 1) k_toeplitz_tc(Dev D, const ToeplitzJob
   const int L = P.y_ext ? p.n + 2 : p.n + 1;
   const int rows_total = P.y_ext ? p.Next : p.N;
   const int row0 = job.mt * TC_BM;
-  if (row0 >= rows_total) return;
   const int nc = (p.N + 31) / 32;
   const int cper = (nc + job.nks - 1) / job.nks;
   const int c_begin = job.ks * cper, c_end = min(nc, c_begin + cper);
@@ -157,28 +209,42 @@ __global__ void __launch_bounds__(192, 1) k_toeplitz_tc(Dev D, const ToeplitzJob
   const int nchunks = c_end - c_begin;
   const int NT = ((2 * w + 15) / 16) * 16;
   const int S = P.stages;
-
-  // window of grid indices needed by this CTA: [gk(first row) - gh(last h), gk(last row) - gh(first h)]
-  const int last_row = min(rows_total, row0 + TC_BM) - 1;
-  const int h_first = 32 * c_begin, h_last = min(p.N, 32 * c_end) - 1;
-  int wlo = grid_of_row(row0, L, p) - grid_of_h(h_last, p);
-  int whi = grid_of_row(last_row, L, p) - grid_of_h(h_first, p);
-  wlo &= ~1;                                  // 16-byte aligned start (float2 pairs)
-  int wlen = whi - wlo + 1;
-  wlen = (wlen + 1) & ~1;
-  if (wlen > P.win_cap) {                     // host sizing guarantees this does not happen
+  const int CS = P.cs;
+  const uint32_t crank = CS > 1 ? cluster_ctarank() : 0u;
+  const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
+  bool filler = row0 >= rows_total;
+  if (nchunks > TC_MAXCH || NT > P.ntbox) {       // host sizing rules these out (cluster-uniform)
     if (threadIdx.x == 0) atomicExch(err, 3);
     return;
   }
-  const float2* F = (P.adjoint ? D.gH : D.gF) + p.grid;
 
-  // shared memory: B stages (1024-aligned), then the window
+  // window of grid indices needed by this CTA: [gk(first row) - gh(last h), gk(last row) - gh(first h)]
+  int wlo = 0, wlen = 0;
+  if (!filler) {
+    const int last_row = min(rows_total, row0 + TC_BM) - 1;
+    const int h_first = 32 * c_begin, h_last = min(p.N, 32 * c_end) - 1;
+    wlo = grid_of_row(row0, L, p) - grid_of_h(h_last, p);
+    const int whi = grid_of_row(last_row, L, p) - grid_of_h(h_first, p);
+    wlo &= ~3;                                  // 16-byte aligned start (4 words)
+    wlen = ((whi - wlo + 1) + 3) & ~3;
+    if (wlen > P.win_cap) {
+      if (threadIdx.x == 0) atomicExch(err, 3);
+      filler = true;
+    }
+  }
+  const uint32_t* gtab = (P.adjoint ? D.tabH : D.tabF) + p.toff;
+
+  // shared memory: B stages (1024-aligned, the same offsets in every CTA), then the window of
+  // the 2 NPL split-plane tables
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
-  const uint32_t stage_bytes = (uint32_t)NPL * P.ntbox * 128u;
+  const uint32_t plane_bytes = (uint32_t)P.ntbox * 128u;
+  const uint32_t stage_bytes = (uint32_t)NPL * plane_bytes;
   unsigned char* Bs = sm;
-  float2* win = (float2*)(sm + (size_t)S * stage_bytes);
+  uint32_t* wtab = (uint32_t*)(sm + (size_t)S * stage_bytes);   // table a at wtab + a * win_cap
+
+  if (filler && CS == 1) return;                 // no cluster to serve
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -190,39 +256,62 @@ __global__ void __launch_bounds__(192, 1) k_toeplitz_tc(Dev D, const ToeplitzJob
     mbar_init(&bar_d, 1);
     for (int i = 0; i < S; ++i) {
       mbar_init(&bar_bfull[i], 1);
-      mbar_init(&bar_afull[i], 4);
-      mbar_init(&bar_empty[i], 1);
+      mbar_init(&bar_afull[i], TC_APROD);
+      mbar_init(&bar_aempty[i], 1);
+      mbar_init(&bar_bempty[i], CS);            // one release per CTA of the cluster
     }
     s_err = 0;
     fence_barrier_init();
   }
+  // grid offset gh of the first of each 16 input points when all 16 lie on one grid line
+  for (int idx = threadIdx.x; idx < 2 * nchunks; idx += blockDim.x) {
+    const int h0 = 32 * (c_begin + idx / 2) + 16 * (idx & 1);
+    const bool line = h0 + 15 < p.N && (h0 % (p.n + 1)) + 15 <= p.n;
+    ghalf[idx] = line ? grid_of_h(h0, p) : -1;
+  }
   tc_fence_before();
   __syncthreads();
+  if (CS > 1) cluster_sync();                     // every barrier of the cluster is initialised
   tc_fence_after();
   const uint32_t tb = s_tmem;
 
   if (warp == 0) {
-    // ------------------------------------------------------------- TMA producer
+    // ------------------------------------------------------------- TMA: window and B' share
     if (lane == 0) {
-      mbar_arrive_expect_tx(&bar_win, (uint32_t)wlen * 8u);
-      tma_load_1d(win, F + wlo, (uint32_t)wlen * 8u, &bar_win);
+      if (!filler) {
+        mbar_arrive_expect_tx(&bar_win, (uint32_t)(2 * NPL * wlen) * 4u);
+#pragma unroll
+        for (int part = 0; part < 2; ++part)
+#pragma unroll
+          for (int pl = 0; pl < NPL; ++pl)
+            tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap, gtab + (long long)(3 * part + pl) * p.Gd4 + wlo,
+                        (uint32_t)wlen * 4u, &bar_win);
+      }
+      const int ng = NT / TC_BOXR, units = NPL * ng;
+      const int u_lo = (int)crank * units / CS, u_hi = ((int)crank + 1) * units / CS;
       const int yrow0 = job.prob * NPL * P.ntbox;
+      const uint32_t stage_tx = (uint32_t)(NPL * NT * 128);
       int issued = 0;
       for (int it = 0; it < nchunks; ++it) {
         const int s = it % S, u = it / S;
-        if (it >= S && !mbar_wait(&bar_empty[s], (u - 1) & 1, TC_SPIN)) { s_err = 1; break; }
-        mbar_arrive_expect_tx(&bar_bfull[s], stage_bytes);
-        for (int pl = 0; pl < NPL; ++pl)
-          tma_load_2d(Bs + (size_t)s * stage_bytes + (size_t)pl * P.ntbox * 128, &bmap, 64 * (c_begin + it),
-                      yrow0 + pl * P.ntbox, &bar_bfull[s]);
+        // stage s is free once every CTA of the cluster has consumed its previous contents
+        if (it >= S && !mbar_wait(&bar_bempty[s], (u - 1) & 1, TC_SPIN)) { s_err = 1; break; }
+        mbar_arrive_expect_tx(&bar_bfull[s], stage_tx);
+        for (int un = u_lo; un < u_hi; ++un) {
+          const int pl = un / ng, g = un % ng;
+          unsigned char* dst = Bs + (size_t)s * stage_bytes + (size_t)pl * plane_bytes + (size_t)g * TC_BOXR * 128;
+          const int x = 64 * (c_begin + it), y = yrow0 + pl * P.ntbox + g * TC_BOXR;
+          if (CS > 1) tma_load_2d_mc(dst, &bmap, x, y, &bar_bfull[s], cmask);
+          else tma_load_2d(dst, &bmap, x, y, &bar_bfull[s]);
+        }
         ++issued;
       }
-      // in-flight copies end before the CTA exits
-      if (issued > 0) {
-        const int last = issued - 1;
-        mbar_wait(&bar_bfull[last % S], (last / S) & 1, TC_SPIN);
-      }
-      mbar_wait(&bar_win, 0, TC_SPIN);
+      // Tail: the last stages are released by every CTA of the cluster, so every copy into this
+      // CTA and every copy this CTA multicast have landed before it exits.
+      if (!s_err)
+        for (int it = max(0, issued - S); it < issued; ++it)
+          if (!mbar_wait(&bar_bempty[it % S], (it / S) & 1, TC_SPIN)) { s_err = 1; break; }
+      if (!filler && !mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
@@ -230,28 +319,38 @@ __global__ void __launch_bounds__(192, 1) k_toeplitz_tc(Dev D, const ToeplitzJob
       const uint32_t idesc = idesc_bf16_f32(TC_BM, NT);
       for (int it = 0; it < nchunks; ++it) {
         const int s = it % S, u = it / S;
-        if (!mbar_wait(&bar_afull[s], u & 1, TC_SPIN) || !mbar_wait(&bar_bfull[s], u & 1, TC_SPIN)) {
+        if ((!filler && !mbar_wait(&bar_afull[s], u & 1, TC_SPIN)) || !mbar_wait(&bar_bfull[s], u & 1, TC_SPIN)) {
           s_err = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t a0 = tb + TC_A_COL0 + (uint32_t)s * NPL * 32;
+        if (filler) {
+          // nothing to multiply: release this CTA's copy of the stage to every loader
+          for (int r = 0; r < CS; ++r) mbar_arrive_remote(&bar_bempty[s], (uint32_t)r);
+          continue;
+        }
+        const uint32_t a0 = tb + P.acol0 + (uint32_t)s * NPL * 32;
         const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
 #pragma unroll
         for (int pr = 0; pr < NPROD; ++pr) {
           const uint32_t a_pl = a0 + PA[pr] * 32;
-          const uint64_t bd = sdesc_sw128(bsm + PB[pr] * P.ntbox * 128);
+          const uint64_t bd = sdesc_sw128(bsm + PB[pr] * plane_bytes);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma_ts_f16(tb, a_pl + 8 * kk, bd + 2 * kk, idesc, (it > 0 || pr > 0 || kk > 0) ? 1u : 0u);
         }
-        tc_commit(&bar_empty[s]);
+        tc_commit(&bar_aempty[s]);
+        if (CS > 1) tc_commit_mc(&bar_bempty[s], cmask);
+        else tc_commit(&bar_bempty[s]);
       }
-      tc_commit(&bar_d);      // arrives when every MMA issued above has completed
+      if (!filler) tc_commit(&bar_d);      // arrives when every MMA issued above has completed
     }
-  } else {
-    // ------------------------------------------------------------- A producers + epilogue
-    const int q = warp & 3;                     // TMEM lane quadrant of this warp
+  } else if (!filler) {
+    // ------------------------------------------------------------- A' producers + epilogue
+    // Warps 2..9: quadrant q = warp & 3 (TMEM lanes 32q..32q+31 = tile rows), half hh of every
+    // K chunk (input points 32c + 16hh .. +15).
+    const int q = warp & 3;
+    const int hh = (warp - 2) >> 2;
     const int i = 32 * q + lane;                // row within the tile
     const int row = row0 + i;
     const bool vrow = row < rows_total;
@@ -261,47 +360,62 @@ __global__ void __launch_bounds__(192, 1) k_toeplitz_tc(Dev D, const ToeplitzJob
     if (!ok) s_err = 1;
     for (int it = 0; ok && it < nchunks; ++it) {
       const int s = it % S, u = it / S;
-      if (it >= S && !__all_sync(0xffffffffu, mbar_wait(&bar_empty[s], (u - 1) & 1, TC_SPIN))) {
+      if (it >= S && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (u - 1) & 1, TC_SPIN))) {
         s_err = 1;
         break;
       }
-      const int h = 32 * (c_begin + it) + lane;
-      const int ghl = h < p.N ? grid_of_h(h, p) : INT_MIN;
-      float re[32], im[32];
+      const int g0 = ghalf[2 * it + hh];
+      const uint32_t a0 = tb + lane_off + P.acol0 + (uint32_t)s * NPL * 32 + 8 * hh;
+      if (g0 >= 0) {
+        // the 16 points lie on one grid line: F(k - h_j) sits at window index x - j, and the
+        // pair (j, j + 1) = (2jp, 2jp + 1) is table word x - 2jp
+        const int x = vrow ? gk - g0 : 16;        // rows past the end read nothing (any in-range x)
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int g = __shfl_sync(0xffffffffu, ghl, j);
-        float2 v = make_float2(0.f, 0.f);
-        if (vrow && g != INT_MIN) v = win[gk - g];
-        re[j] = v.x;
-        im[j] = v.y;
-      }
-      const uint32_t a0 = tb + lane_off + TC_A_COL0 + (uint32_t)s * NPL * 32;
+        for (int part = 0; part < 2; ++part)
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const float* src = half ? im : re;
-        uint32_t wp[NPL][16];
+          for (int pl = 0; pl < NPL; ++pl) {
+            const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap + x;
+            uint32_t wv[8];
 #pragma unroll
-        for (int jp = 0; jp < 16; ++jp) {
-          uint32_t t3[3];
-          split_pair<NPL>(src[2 * jp], src[2 * jp + 1], t3);
+            for (int jp = 0; jp < 8; ++jp) wv[jp] = vrow ? T[-2 * jp] : 0u;
+            tmem_st_x8(a0 + pl * 32 + part * 16, wv);
+          }
+      } else {
+        // points on several grid lines: each half word from its own table entry
+        const int h = 32 * (c_begin + it) + 16 * hh + (lane & 15);
+        const int ghl = h < p.N ? grid_of_h(h, p) : INT_MIN;
+        int xs[16];
 #pragma unroll
-          for (int pl = 0; pl < NPL; ++pl) wp[pl][jp] = t3[pl];
+        for (int j = 0; j < 16; ++j) {
+          const int g = __shfl_sync(0xffffffffu, ghl, j);
+          xs[j] = (vrow && g != INT_MIN) ? gk - g : -1;
         }
 #pragma unroll
-        for (int pl = 0; pl < NPL; ++pl) tmem_st_x16(a0 + pl * 32 + half * 16, wp[pl]);
+        for (int part = 0; part < 2; ++part)
+#pragma unroll
+          for (int pl = 0; pl < NPL; ++pl) {
+            const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap;
+            uint32_t wv[8];
+#pragma unroll
+            for (int jp = 0; jp < 8; ++jp) {
+              const uint32_t lo = xs[2 * jp] >= 0 ? (T[xs[2 * jp]] & 0xFFFFu) : 0u;
+              const uint32_t hi = xs[2 * jp + 1] >= 0 ? (T[xs[2 * jp + 1]] << 16) : 0u;
+              wv[jp] = lo | hi;
+            }
+            tmem_st_x8(a0 + pl * 32 + part * 16, wv);
+          }
       }
       tmem_st_wait();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_afull[s]);
     }
-    // epilogue: D (TMEM) -> Y
+    // epilogue: D (TMEM) -> Y; the two warps of a quadrant take alternate 16-column groups
     if (__all_sync(0xffffffffu, mbar_wait(&bar_d, 0, TC_SPIN)) && !s_err) {
       tc_fence_after();
       int ldy;
       float2* Y = tc_buf(D, P.ybuf, p, ldy);
-      for (int c0 = 0; c0 < NT; c0 += 16) {
+      for (int c0 = 16 * hh; c0 < NT; c0 += 32) {
         uint32_t v[16];
         tmem_ld_x16(tb + lane_off + c0, v);
         tmem_ld_wait();
@@ -328,15 +442,15 @@ __global__ void __launch_bounds__(192, 1) k_toeplitz_tc(Dev D, const ToeplitzJob
   if (warp == 0) {
     tc_fence_after();
     // on an error path, let the MMAs already issued finish before the columns are released
-    if (s_err) mbar_wait(&bar_d, 0, TC_SPIN);
+    if (s_err && !filler) mbar_wait(&bar_d, 0, TC_SPIN);
     tmem_dealloc(tb, 512);
   }
+  if (CS > 1) cluster_sync();                     // no CTA leaves while a peer may still signal it
 }
 
 }  // namespace
 
 // ----------------------------------------------------------------------------- host side
-// Tensor map over the B' buffer: 2-D, inner dimension K (kpitch BF16), outer rows, 128B swizzle.
 // The driver's tensor-map encoder, looked up through the runtime (the library does not link
 // libcuda, so it also loads on machines without a GPU driver).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -351,12 +465,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows, int ntbox) {
+// Tensor map over the B' planes: 2-D (K innermost, kpitch BF16; rows), boxes of 64 K x 16 rows,
+// 128-byte swizzle.  Every box starts at K = 64c: 128-byte aligned.
+int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return -1;
   cuuint64_t dims[2] = {(cuuint64_t)kpitch, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kpitch * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)ntbox};
+  cuuint32_t box[2] = {64, (cuuint32_t)TC_BOXR};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xb, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -364,7 +480,13 @@ int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows, int nt
 }
 
 size_t tc_smem_bytes(int npl, int ntbox, int stages, int win_cap) {
-  return 1024 + (size_t)stages * npl * ntbox * 128 + (size_t)win_cap * 8;
+  return 1024 + (size_t)stages * npl * ntbox * 128 + (size_t)2 * npl * win_cap * 4;
+}
+
+void launch_split_tables(const Dev& D, cudaStream_t s) {
+  note_launch();
+  dim3 g(std::max(1, std::min((D.maxGd + 3) / 4 / 256 + 1, 64)), D.nprob);
+  k_split_tables<<<g, 256, 0, s>>>(D);
 }
 
 void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int npl, int ntbox, int kpitch, cudaStream_t s) {
@@ -373,27 +495,68 @@ void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int npl, int ntb
   k_xb_prep<<<g, 256, 0, s>>>(D, xbuf, wsel, (uint16_t*)xb, npl, ntbox, kpitch);
 }
 
-void launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel, int ybuf,
-                        int y_ext, int npl, int ntbox, int kpitch, int win_cap, int stages, const CUtensorMap& map,
-                        int* err, cudaStream_t s) {
-  if (nks > 1) launch_zero_buf(D, ybuf, wsel, y_ext, s);
-  TcParams P{adjoint, 0, wsel, ybuf, y_ext, ntbox, kpitch, win_cap, stages};
-  size_t sm = tc_smem_bytes(npl, ntbox, stages, win_cap);
-  note_launch();
-  // the attribute must cover this launch's dynamic shared memory (static + dynamic <= 227 KB)
-  if (npl == 3) {
-    static size_t set3 = 0;
-    if (sm > set3) {
-      cudaFuncSetAttribute(k_toeplitz_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      set3 = sm;
-    }
-    k_toeplitz_tc<3><<<njobs, 192, sm, s>>>(D, jobs, P, map, err);
-  } else {
-    static size_t set2 = 0;
-    if (sm > set2) {
-      cudaFuncSetAttribute(k_toeplitz_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      set2 = sm;
-    }
-    k_toeplitz_tc<2><<<njobs, 192, sm, s>>>(D, jobs, P, map, err);
+template <int NPL>
+static cudaError_t launch_tc_npl(const Dev& D, const ToeplitzJob* jobs, int njobs, const TcParams& P,
+                                 const CUtensorMap& map, int* err, size_t sm, cudaStream_t s) {
+  static size_t set = 0;
+  if (sm > set) {
+    // the attribute must cover this launch's dynamic shared memory (static + dynamic <= 227 KB)
+    cudaError_t e = cudaFuncSetAttribute(k_toeplitz_tc<NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    set = sm;
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs);
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_toeplitz_tc<NPL>, D, jobs, P, map, err);
+}
+
+cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel,
+                               int ybuf, int y_ext, int npl, int ntbox, int win_cap, int stages, int cs,
+                               const CUtensorMap& map, int* err, cudaStream_t s) {
+  if (nks > 1) launch_zero_buf(D, ybuf, wsel, y_ext, s);
+  const int acol0 = std::max(32, (ntbox + 31) / 32 * 32);
+  TcParams P{adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, acol0, cs};
+  const size_t sm = tc_smem_bytes(npl, ntbox, stages, win_cap);
+  note_launch();
+  return npl == 3 ? launch_tc_npl<3>(D, jobs, njobs, P, map, err, sm, s)
+                  : launch_tc_npl<2>(D, jobs, njobs, P, map, err, sm, s);
+}
+
+// Largest cluster size (<= want) for which `cs` CTAs with this shared memory fit on the GPU at once.
+int tc_max_cluster(int npl, int want, size_t sm) {
+  for (int cs = want; cs > 1; cs /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs * 16);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = sm;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e;
+    if (npl == 3) {
+      cudaFuncSetAttribute(k_toeplitz_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      e = cudaOccupancyMaxActiveClusters(&n, k_toeplitz_tc<3>, &cfg);
+    } else {
+      cudaFuncSetAttribute(k_toeplitz_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      e = cudaOccupancyMaxActiveClusters(&n, k_toeplitz_tc<2>, &cfg);
+    }
+    if (e == cudaSuccess && n > 0) return cs;
+    cudaGetLastError();
+  }
+  return 1;
 }

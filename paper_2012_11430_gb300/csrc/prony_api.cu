@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -57,13 +58,14 @@ int ensure(DBuf& b, size_t bytes) {
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
 struct prony_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   DBuf grid64, gF, gH, V, U, B1, B2, Y, small, P, st, jobs, flag, tout, cout, misc, misc2, misc3;
-  DBuf xb, tcjobs, tcerr;           // tensor-core path: B' planes, 128-row job list, error flag
+  DBuf xb, tabF, tabH, tcjobs, tcerr;   // tensor-core path: B' planes, split sample tables, jobs, error flag
   int* h_flag = nullptr;            // pinned
   std::vector<ProbState> h_st;
   // profiling of the Toeplitz launches
@@ -74,6 +76,15 @@ struct prony_ctx {
   std::vector<std::vector<ProbState>> snaps;
   prony_stats stats{};
   long long launch_base = 0;
+  cudaError_t launch_err = cudaSuccess;   // first failed tensor-core launch of the current call
+  // refinement: workspace and the CUDA graph of the last argument set
+  DBuf lmws;
+  struct LmKey {
+    const void *t, *c, *y, *loss, *ws;
+    int m, d, iters, lo[PRONY_DMAX], len[PRONY_DMAX];
+    double lambda0;
+  } lm_key{};
+  cudaGraphExec_t lm_exec = nullptr;
 };
 
 namespace {
@@ -105,7 +116,7 @@ long long ipow(long long b, int e) {
 // Tensor-core configuration of a batch (split BF16 planes).
 struct TcConf {
   bool on = false;
-  int npl = 3, ntbox = 16, kpitch = 64, stages = 2, win_cap = 0, nks = 1;
+  int npl = 3, ntbox = 16, kpitch = 64, stages = 2, win_cap = 0, nks = 1, cs = 1;
   int njobs_ext = 0, njobs_in = 0;
   ToeplitzJob* jobs_ext = nullptr;
   ToeplitzJob* jobs_in = nullptr;
@@ -144,7 +155,7 @@ int h_grid_of_h(int h, const ProbDesc& p) {
   }
   return g;
 }
-// largest window (float2 entries) over the CTAs of a problem for a K split into nks ranges
+// largest window (table words) over the CTAs of a problem for a K split into nks ranges
 int max_window(const ProbDesc& p, int L, int nks) {
   const int rows = ipow(L, p.d) > 0 ? (int)ipow(L, p.d) : 0;
   const int nc = (p.N + 31) / 32, cper = (nc + nks - 1) / nks;
@@ -155,9 +166,9 @@ int max_window(const ProbDesc& p, int L, int nks) {
       int cb = ks * cper, ce = std::min(nc, cb + cper);
       if (cb >= ce) continue;
       int hf = 32 * cb, hl = std::min(p.N, 32 * ce) - 1;
-      int lo = (h_grid_of_row(r0, L, p) - h_grid_of_h(hl, p)) & ~1;
+      int lo = (h_grid_of_row(r0, L, p) - h_grid_of_h(hl, p)) & ~3;
       int hi = h_grid_of_row(last, L, p) - h_grid_of_h(hf, p);
-      mx = std::max(mx, ((hi - lo + 1) + 1) & ~1);
+      mx = std::max(mx, ((hi - lo + 1) + 3) & ~3);
     }
   }
   return mx;
@@ -174,15 +185,18 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     tiles_ext += (p.Next + 127) / 128;
     tiles_in += (p.N + 127) / 128;
   }
-  T.kpitch = 64 * maxnc;
   const size_t stage = (size_t)T.npl * T.ntbox * 128;
-  const size_t avail = 227 * 1024 - 2048;
-  T.stages = T.npl == 3 ? 2 : 3;
-  while (T.stages > 1 && 1024 + T.stages * stage + 8 * 2048 > avail) --T.stages;
-  T.win_cap = (int)((avail - 1024 - T.stages * stage) / 8) & ~1;
+  const size_t avail = 227 * 1024 - 2048 - 4608;   // static shared memory of the kernel (chunk table)
+  // pipeline depth: A stages in TMEM after the accumulator columns, B stages in shared memory,
+  // leaving room for a window of the 2 npl split-plane tables of at least 64 KB
+  const int acol0 = std::max(32, (T.ntbox + 31) / 32 * 32);
+  T.stages = std::min(4, (512 - acol0) / (T.npl * 32));
+  while (T.stages > 1 && 1024 + T.stages * stage + 64 * 1024 > avail) --T.stages;
+  T.win_cap = (int)((avail - 1024 - T.stages * stage) / (8 * T.npl)) & ~3;
   if (T.win_cap < 256) return PRONY_EINVAL;
   // split K: enough CTAs to fill the GPU, and every window within the shared-memory capacity
   int nks = std::max(1, std::min(16, (2 * 152 + tiles_in - 1) / std::max(1, tiles_in)));
+  nks = std::max(nks, (maxnc + 511) / 512);        // at most 512 K chunks per CTA
   for (;; ++nks) {
     bool fits = true;
     for (const auto& p : B.P) {
@@ -192,16 +206,47 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     if (fits || nks >= maxnc) break;
   }
   T.nks = nks;
+  T.kpitch = 64 * maxnc;
+  // Cluster size: the CTAs of a cluster share the B' stages of one problem and K range; tiles
+  // of a problem are padded to a multiple of the cluster with filler CTAs, so a size is used
+  // only while the fillers stay below 1/8 of the CTAs.
+  int want = 4;
+  if (const char* e = getenv("PRONY_TC_CLUSTER")) {
+    const int v = atoi(e);
+    want = v >= 8 ? 8 : v >= 4 ? 4 : v >= 2 ? 2 : 1;
+  }
+  int cs = 1;
+  for (int c = want; c > 1; c /= 2) {
+    long long real = 0, padded = 0;
+    for (const auto& p : B.P) {
+      const long long te = (p.Next + 127) / 128, ti = (p.N + 127) / 128;
+      real += te + ti;
+      padded += (te + c - 1) / c * c + (ti + c - 1) / c * c;
+    }
+    if (8 * (padded - real) <= padded) { cs = c; break; }
+  }
+  if (cs > 1) cs = tc_max_cluster(T.npl, cs, tc_smem_bytes(T.npl, T.ntbox, T.stages, T.win_cap));
+  T.cs = cs;
   std::vector<ToeplitzJob> jobs;
-  for (int i = 0; i < (int)B.P.size(); ++i)
-    for (int mt = 0; mt < (B.P[i].Next + 127) / 128; ++mt)
-      for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
+  auto add_jobs = [&](bool ext) {
+    for (int i = 0; i < (int)B.P.size(); ++i) {
+      const int tiles = ((ext ? B.P[i].Next : B.P[i].N) + 127) / 128;
+      const int padded = (tiles + cs - 1) / cs * cs;
+      for (int ks = 0; ks < nks; ++ks)
+        for (int mt = 0; mt < padded; ++mt) jobs.push_back({i, mt, ks, nks});   // mt >= tiles: filler
+    }
+  };
+  add_jobs(true);
   T.njobs_ext = (int)jobs.size();
-  for (int i = 0; i < (int)B.P.size(); ++i)
-    for (int mt = 0; mt < (B.P[i].N + 127) / 128; ++mt)
-      for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
+  add_jobs(false);
   T.njobs_in = (int)jobs.size() - T.njobs_ext;
   int rc;
+  long long twords = 64;                              // split-plane tables (+ slack for window rounding)
+  for (const auto& p : B.P) twords = std::max(twords, p.toff + 6LL * p.Gd4 + 64);
+  if ((rc = ensure(ctx->tabF, 4 * (size_t)twords))) return rc;
+  if ((rc = ensure(ctx->tabH, 4 * (size_t)twords))) return rc;
+  B.D.tabF = (uint32_t*)ctx->tabF.p;
+  B.D.tabH = (uint32_t*)ctx->tabH.p;
   if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
   const long long rows = (long long)B.P.size() * T.npl * T.ntbox;
   if ((rc = ensure(ctx->xb, (size_t)rows * T.kpitch * 2))) return rc;
@@ -212,7 +257,7 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
   T.jobs_in = T.jobs_ext + T.njobs_ext;
   T.err = (int*)ctx->tcerr.p;
-  if (encode_xb_map(&T.map, ctx->xb.p, T.kpitch, rows, T.ntbox)) {
+  if (encode_xb_map(&T.map, ctx->xb.p, T.kpitch, rows)) {
     g_err = "cuTensorMapEncodeTiled failed for the B' planes";
     return PRONY_ECUDA;
   }
@@ -228,8 +273,10 @@ void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int
   if (B.tc.on) {
     const TcConf& T = B.tc;
     launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.npl, T.ntbox, T.kpitch, s);
-    launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, T.nks, adjoint, wsel, ybuf,
-                       ext, T.npl, T.ntbox, T.kpitch, T.win_cap, T.stages, T.map, T.err, s);
+    cudaError_t e = launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, T.nks,
+                                       adjoint, wsel, ybuf, ext, T.npl, T.ntbox, T.win_cap, T.stages, T.cs, T.map,
+                                       T.err, s);
+    if (e != cudaSuccess && ctx->launch_err == cudaSuccess) ctx->launch_err = e;
   } else {
     launch_toeplitz(D, ext ? B.jobs_ext : B.jobs_in, ext ? B.njobs_ext : B.njobs_in, B.nks, adjoint, xbuf, wsel, ybuf,
                     ext, B.maxw, prec, s);
@@ -241,7 +288,7 @@ void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int
 int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opts& o, Batch& B) {
   const int np = (int)hp.size();
   B.P.resize(np);
-  long long goff = 0, xoff = 0, yoff = 0;
+  long long goff = 0, xoff = 0, yoff = 0, toff = 0;
   int maxN = 0, maxNext = 0, maxGd = 0, maxR0 = 0, maxM = 0, maxD = 0;
   long long tiles_ext = 0, tiles_in = 0;
   for (int i = 0; i < np; ++i) {
@@ -261,6 +308,9 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
     p.xoff = xoff;
     p.yoff = yoff;
     p.ooff = h.out_off;
+    p.Gd4 = (p.Gd + 3) & ~3;
+    p.toff = toff;
+    toff += 6LL * p.Gd4;
     goff += p.Gd;
     xoff += (long long)p.N * p.r0;
     yoff += (long long)p.Next * p.r0;
@@ -386,6 +436,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     ctx->snaps.clear();
   }
   launch_prep(D, s);
+  if (B.tc.on) launch_split_tables(D, s);
   launch_init_v0(D, o.seed, s);
   tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
   if ((rc = toeplitz(0, 1))) return rc;
@@ -505,6 +556,12 @@ int check_precision(int prec) {
 // Error flag of the tensor-core kernels (bounded waits that gave up, window overflow).
 int check_tc_error(prony_ctx* ctx, const Batch& B) {
   if (!B.tc.on) return PRONY_OK;
+  if (ctx->launch_err != cudaSuccess) {
+    const cudaError_t e = ctx->launch_err;
+    ctx->launch_err = cudaSuccess;
+    g_err = std::string("tensor-core Toeplitz launch: ") + cudaGetErrorString(e);
+    return PRONY_ECUDA;
+  }
   int h = 0;
   CK(cudaMemcpyAsync(&h, B.tc.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -532,7 +589,7 @@ extern "C" {
 
 void prony_default_opts(prony_opts* o) {
   if (!o) return;
-  o->precision = PRONY_FP32;
+  o->precision = PRONY_BF16X3;
   o->oversample_p = -1;
   o->tol_rank = 0.0;
   o->tol_power = 0.0;
@@ -579,7 +636,9 @@ int prony_ctx_destroy(prony_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   DBuf* bufs[] = {&c->grid64, &c->gF, &c->gH, &c->V, &c->U, &c->B1, &c->B2, &c->Y, &c->small, &c->P,
-                  &c->st, &c->jobs, &c->flag, &c->tout, &c->cout, &c->misc, &c->misc2, &c->misc3};
+                  &c->st, &c->jobs, &c->flag, &c->tout, &c->cout, &c->misc, &c->misc2, &c->misc3,
+                  &c->xb, &c->tabF, &c->tabH, &c->tcjobs, &c->tcerr, &c->lmws};
+  if (c->lm_exec) cudaGraphExecDestroy(c->lm_exec);
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->h_flag) cudaFreeHost(c->h_flag);
@@ -782,6 +841,47 @@ int prony_expsum_fwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev,
   return PRONY_OK;
 }
 
+int prony_refine_lm_dev(prony_ctx* ctx, double* t_dev, prony_c128* c_dev, int m, int d, const int* lo,
+                        const int* len, const void* y_dev, int iters, double lambda0, double* loss_dev, void* stream) {
+  if (!ctx || !t_dev || !c_dev || !y_dev || !lo || !len || m < 1 || m > PRONY_MMAX || d < 1 || d > PRONY_DMAX ||
+      iters < 0 || m * (d + 2) > PRONY_LM_PMAX || !(lambda0 > 0.0))
+    return PRONY_EINVAL;
+  const long long K = box_count(d, len);
+  if (K <= 0) return PRONY_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+  if (iters == 0) return PRONY_OK;
+  int rc;
+  if ((rc = ensure(ctx->lmws, (size_t)lm_workspace_bytes(m, d)))) return rc;
+  prony_ctx::LmKey k{};
+  k.t = t_dev; k.c = c_dev; k.y = y_dev; k.loss = loss_dev; k.ws = ctx->lmws.p;
+  k.m = m; k.d = d; k.iters = iters; k.lambda0 = lambda0;
+  for (int l = 0; l < d; ++l) { k.lo[l] = lo[l]; k.len[l] = len[l]; }
+  if (!ctx->lm_exec || std::memcmp(&k, &ctx->lm_key, sizeof(k)) != 0) {
+    if (ctx->lm_exec) {
+      cudaGraphExecDestroy(ctx->lm_exec);
+      ctx->lm_exec = nullptr;
+    }
+    CK(lm_set_attributes(m, d));
+    // capture on the context stream (never the legacy default stream), launch on `s`
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    launch_refine_lm(t_dev, (double2*)c_dev, m, d, lo, len, K, (const float2*)y_dev, iters, lambda0, loss_dev,
+                     ctx->lmws.p, ctx->stream);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture(ctx->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&ctx->lm_exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    ctx->lm_key = k;
+  } else {
+    note_launches(1 + (long long)LM_LAUNCHES_PER_STEP * iters);
+  }
+  CK(cudaGraphLaunch(ctx->lm_exec, s));
+  CK(cudaStreamSynchronize(s));
+  return PRONY_OK;
+}
+
 int prony_expsum_bwd_dev(prony_ctx* ctx, const double* t_dev, const void* c_dev, int m, int d, const int* lo,
                          const int* len, const void* g_dev, double* grad_t_dev, void* grad_c_dev, void* stream) {
   if (!ctx || !t_dev || !c_dev || !g_dev || !grad_t_dev || !grad_c_dev || !lo || !len || m < 1 ||
@@ -832,6 +932,7 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
   CK(cudaMemcpyAsync(ctx->P.p, B.P.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->grid64.p, grid_dev, sizeof(double2) * B.P[0].Gd, cudaMemcpyDeviceToDevice, ctx->stream));
   launch_prep(B.D, ctx->stream);
+  if (B.tc.on) launch_split_tables(B.D, ctx->stream);
   // operate directly on the caller's buffers: X as V (ld N), Y as Y (ld L^d)
   Dev D = B.D;
   D.V = (float2*)X_dev;

@@ -31,6 +31,20 @@ def ctx():
     c.close()
 
 
+def _fp32():
+    from paper_2012_11430_gb300 import default_opts
+    return default_opts(precision="fp32")
+
+
+def test_default_precision_is_split_bf16(ctx):
+    from paper_2012_11430_gb300 import PRONY_BF16X3, default_opts
+    assert default_opts().precision == PRONY_BF16X3
+    P = W.config_problem("C1")
+    res = ctx.solve(P.grid, P.d, P.n, P.m)            # defaults
+    assert res.info["status"] == 0
+    assert np.max(W.torus_dist(res.t, P.t[np.lexsort(P.t.T[::-1])])) <= 1e-6
+
+
 def _random_grid(d, n, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     shape = (2 * n + 2,) * d
@@ -91,7 +105,7 @@ def _check_solution(res, t_ref, c_ref, t_tol=1e-6, c_tol=1e-5):
 ])
 def test_solve_noise_free_matches_oracle(ctx, name, d, n, m, seed):
     P = W.config_problem("C1") if seed is None else W.make_problem(name, d, n, m, seed)
-    res = ctx.solve(P.grid, P.d, P.n, P.m)
+    res = ctx.solve(P.grid, P.d, P.n, P.m, _fp32())
     t_o, c_o, info_o = O.prony(P.grid, P.d, P.n, P.m)
     assert res.info["status"] == 0, res.info
     _check_solution(res, t_o, c_o)
@@ -107,7 +121,7 @@ def _phase_invariants(S):
 
 def test_build_S_matches_oracle(ctx):
     P = W.config_problem("C1")
-    S, sig, U, V, info = ctx.build_S(P.grid, P.d, P.n, P.m, want_uv=True)
+    S, sig, U, V, info = ctx.build_S(P.grid, P.d, P.n, P.m, _fp32(), want_uv=True)
     S_o, s_o, U_o, V_o = O.prony_S(P.grid, P.d, P.n, P.m)
     assert np.max(np.abs(sig - s_o) / s_o) <= 1e-5
     for l in range(P.d):
@@ -127,7 +141,7 @@ def test_build_S_matches_oracle(ctx):
 
 def test_solve_noisy_C2_forward_error_within_oracle(ctx):
     P = W.config_problem("C2")
-    res = ctx.solve(P.grid, P.d, P.n, P.m)
+    res = ctx.solve(P.grid, P.d, P.n, P.m, _fp32())
     t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
     te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
     te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
@@ -158,11 +172,11 @@ def test_invalid_arguments(ctx):
 def test_batched_matches_single_and_oracle(ctx):
     probs = W.batch_problems(count=12, n_lo=5, n_hi=12, snr_db=None)
     outs, rc = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
-                                 [p.m for p in probs])
+                                 [p.m for p in probs], _fp32())
     for p, r in zip(probs, outs):
         t_o, c_o, _ = O.prony(p.grid, p.d, p.n, p.m)
         _check_solution(r, t_o, c_o)
-        single = ctx.solve(p.grid, p.d, p.n, p.m)
+        single = ctx.solve(p.grid, p.d, p.n, p.m, _fp32())
         # a batch splits the K dimension differently than a single problem: FP32 rounding differs
         assert np.max(W.torus_dist(single.t, r.t)) <= 1e-6
 
@@ -236,3 +250,21 @@ def test_solve_noisy_C2_tensor_core(ctx, prec):
     te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
     assert te_g <= 1.5 * te_o + 1e-6, (te_g, te_o, res.info)
     assert ce_g <= 1.5 * ce_o + 1e-6, (ce_g, ce_o, res.info)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_batched_mixed_iteration_counts(ctx, prec):
+    """Problems that stop iterating earlier than others in the same batch keep their results."""
+    from paper_2012_11430_gb300 import default_opts
+    probs = [W.make_problem(f"clean{i}", 2, 15, 5, 300 + i) for i in range(3)]
+    probs += [W.make_problem(f"noisy{i}", 2, 31, 10, 400 + i, snr_db=25.0) for i in range(3)]
+    opts = default_opts(precision=prec)
+    outs, rc = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
+                                 [p.m for p in probs], opts)
+    iters = {o.info["power_iters"] for o in outs}
+    assert len(iters) > 1, iters                  # the batch really mixes iteration counts
+    for p, r in zip(probs, outs):
+        single = ctx.solve(p.grid, p.d, p.n, p.m, opts)
+        assert r.info["status"] == 0 and np.all(np.isfinite(r.c))
+        assert np.max(W.torus_dist(single.t, r.t)) <= 1e-6
+        assert np.linalg.norm(single.c - r.c) <= 1e-5 * np.linalg.norm(single.c)

@@ -306,6 +306,29 @@ def test_expsum_gradient_finite_differences():
             assert abs(fd - want) <= 1e-6 * max(1.0, abs(fd))
 
 
+def test_refine_least_squares_recovers_truth_and_is_stationary():
+    """Noise-free samples: the least-squares fit from a perturbed start returns the true
+    (t, c) (loss 0 is the global minimum).  Noisy samples: the fit is a stationary point of
+    L (gradient, pinned above by finite differences, vanishes) whose loss is below the loss
+    at the truth and at the start."""
+    k = O.box_set([16, 16], 2) - 7
+    P = _problem(2, 7, 4, 131)
+    y = O.expsum(P.t, P.c, k)
+    rng = np.random.default_rng(5)
+    t0 = P.t + 2e-3 * rng.standard_normal(P.t.shape)
+    c0 = P.c * (1 + 0.02 * rng.standard_normal(P.m))
+    t, c, L = O.refine_least_squares(t0, c0, k, y)
+    assert np.max(W.torus_dist(t, P.t)) < 1e-12 and np.max(np.abs(c - P.c)) < 1e-12 and L < 1e-20
+    yn = y + 0.2 * (rng.standard_normal(len(y)) + 1j * rng.standard_normal(len(y)))
+    t, c, L = O.refine_least_squares(t0, c0, k, yn)
+    gt, gc = O.expsum_grad(t, c, k, O.expsum(t, c, k) - yn)
+    gt0, gc0 = O.expsum_grad(t0, c0, k, O.expsum(t0, c0, k) - yn)
+    assert np.max(np.abs(gt)) < 1e-6 * np.max(np.abs(gt0)) and np.max(np.abs(gc)) < 1e-6 * np.max(np.abs(gc0))
+    loss = lambda tt, cc: float(np.sum(np.abs(O.expsum(tt, cc, k) - yn) ** 2))  # noqa: E731
+    assert abs(L - loss(t, c)) <= 1e-9 * L
+    assert L < loss(P.t, P.c) and L < loss(t0, c0)
+
+
 # --------------------------------------------------------------------- planted mistakes
 @pytest.mark.parametrize("mistake", ["t_sign", "shift_sign", "transpose_T", "drop_sigma"])
 def test_pins_catch_planted_mistakes(monkeypatch, mistake):
