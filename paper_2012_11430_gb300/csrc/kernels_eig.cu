@@ -108,9 +108,9 @@ __global__ void __launch_bounds__(256) k_svd_S(Dev D) {
   __shared__ int s_rank[PRONY_MMAX];
   const ProbDesc& p = D.P[blockIdx.x];
   ProbState& st = D.st[blockIdx.x];
-  if (st.status == ST_ENAN) return;
+  if (st.done || st.status == ST_ENAN) return;
   const int a = st.wu, b = st.wv;
-  if (b <= 0 || a <= 0) return;
+  if (b <= 0 || a <= 0 || b > p.m || a > p.r0) return;
   const int LM = D.L.LDM, LR = D.L.LDR;
   char* sb = D.small + p.soff;
   const double2* Q = (const double2*)(sb + D.L.q);            // a x b, ld LM
@@ -294,6 +294,7 @@ __global__ void k_canon(Dev D) {
   const ProbDesc& p = D.P[blockIdx.x];
   ProbState& st = D.st[blockIdx.x];
   const int b = st.wv, a = st.wu;
+  if (st.done || b <= 0 || a <= 0 || b > p.m || a > p.r0) return;
   const int LM = D.L.LDM;
   __shared__ double2 ph[PRONY_MMAX];
   const unsigned long long* am = (const unsigned long long*)(D.small + p.soff + D.L.argmx);
@@ -335,9 +336,9 @@ __global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
   __shared__ int s_fail, s_pr;
   const ProbDesc& p = D.P[blockIdx.x];
   ProbState& st = D.st[blockIdx.x];
-  if (st.status == ST_ENAN) return;
+  if (st.done || st.status == ST_ENAN) return;
   const int m = st.wv;
-  if (m <= 0) return;
+  if (m <= 0 || m > p.m) return;                // shared memory holds 3 maxM^2 entries
   const int LM = D.L.LDM;
   const int LD = m;                             // smem leading dimension
   float2* H = esm;                              // m x m  (C_mu, then Schur form, then W^{-1} work)

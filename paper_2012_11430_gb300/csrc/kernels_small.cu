@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   __syncthreads();
   if (threadIdx.x == 0) {
     float tr = 0.f, mx = 0.f;
+    bool finite = true;
     for (int i = 0; i < w; ++i) {
       float dd = A[i * LR + i].x;
+      finite = finite && isfinite(dd);
       tr += fmaxf(dd, 0.f);
       mx = fmaxf(mx, dd);
     }
@@ -67,9 +69,17 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
     s_maxd0 = mx;
     s_rho = w;
     s_rank = -1;
-    s_stop = 0;
+    s_stop = finite && isfinite(tr) ? 0 : 2;
+    if (s_stop) {                       // non-finite block: the problem stops with ENAN
+      st.status = ST_ENAN;
+      st.done = 1;
+      st.w_in = w;
+      st.w_out = 0;
+      set_width(st, target, 0);
+    }
   }
   __syncthreads();
+  if (s_stop) return;
   const float tol2 = (float)(tol * tol);
   int limit = w;  // columns that may be accepted (never more than m after the rank step)
   if (mode == QR_RANK) limit = min(w, p.m);
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(256) k_solve_c(Dev D) {
   const ProbDesc& p = D.P[blockIdx.x];
   ProbState& st = D.st[blockIdx.x];
   const int m = st.rank_used, d = p.d, LD = PRONY_MMAX;
-  if (m <= 0) return;
+  if (st.done || m <= 0 || m > p.m) return;
   double* t = (double*)(D.small + p.soff + D.L.t);
   double2* b = (double2*)(D.small + p.soff + D.L.rhs);
   double2* cout = (double2*)(D.small + p.soff + D.L.c);
@@ -326,11 +336,20 @@ __global__ void k_check(Dev D, double tol_power, int max_iter, int* all_done) {
 
 // After the power loop: problems that stopped iterating take part in the finishing steps
 // again (non-finite input stays excluded).
+// A problem that failed (non-finite data, an empty U or V block, or a V block that never went
+// through the rank step and is still wider than m) takes no part: rank_used = 0, so every
+// finishing kernel skips it and its outputs are zero.
 __global__ void k_reset_done(Dev D) {
   int pi = blockIdx.x * blockDim.x + threadIdx.x;
   if (pi >= D.nprob) return;
   ProbState& s = D.st[pi];
-  s.done = (s.status == ST_ENAN || s.wv <= 0 || s.wu <= 0) ? 1 : 0;
+  const ProbDesc& p = D.P[pi];
+  const bool failed = s.status == ST_ENAN || s.wv <= 0 || s.wu <= 0 || s.wv > p.m || s.wu > p.r0;
+  if (failed) {
+    if (s.status == ST_OK) set_status(s, ST_ERANK);
+    s.rank_used = 0;
+  }
+  s.done = failed ? 1 : 0;
 }
 
 }  // namespace

@@ -294,7 +294,8 @@ __global__ void k_argmax(Dev D, int buf) {
   int ld;
   const float2* X = buf_base(D, buf, p, ld);
   unsigned long long* am = (unsigned long long*)(D.small + p.soff + D.L.argmx);
-  const int w = s.wv;
+  if (s.done) return;
+  const int w = min(s.wv, p.m);                 // argmx holds LDM >= m entries
   for (int j = 0; j < w; ++j) {
     unsigned long long best = 0ull;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < p.N; r += gridDim.x * blockDim.x) {
@@ -325,6 +326,7 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
   const ProbDesc& p = D.P[pi];
   ProbState& s = D.st[pi];
   const int m = s.rank_used;
+  if (s.done || m <= 0 || m > p.m) return;
   const int n1 = p.n + 1;
   const double* t = (const double*)(D.small + p.soff + D.L.t);
   const double2* c = (const double2*)(D.small + p.soff + D.L.c);

@@ -158,6 +158,28 @@ def test_nonfinite_input_reports_enan(ctx):
     assert res.info["status"] == PRONY_ENAN
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_degenerate_inputs_fail_cleanly(ctx, prec):
+    """An all-zero grid (empty U block at the first QR) and a grid whose products overflow FP32
+    stop with an error status and zero outputs; the other problems of the batch are unaffected."""
+    from paper_2012_11430_gb300 import PRONY_ERANK, PRONY_ENAN, PRONY_ENOCONV, default_opts
+    opts = default_opts(precision=prec)
+    P = W.config_problem("C1")
+    zero = np.zeros_like(P.grid)
+    huge = P.grid * 1e36
+    res = ctx.solve(zero, P.d, P.n, P.m, opts, allow=(PRONY_ERANK, PRONY_ENAN, PRONY_ENOCONV))
+    assert res.info["status"] in (PRONY_ERANK, PRONY_ENAN)
+    assert np.all(res.t == 0) and np.all(res.c == 0)
+    res = ctx.solve(huge, P.d, P.n, P.m, opts, allow=(0, PRONY_ERANK, PRONY_ENAN, PRONY_ENOCONV))
+    assert res.info["status"] != 0 or np.max(W.torus_dist(res.t, P.t[np.lexsort(P.t.T[::-1])])) <= 1e-6
+    outs, rc = ctx.solve_batched([P.grid, zero, P.grid, huge], [2] * 4, [P.n] * 4, [P.m] * 4, opts)
+    t_ref = P.t[np.lexsort(P.t.T[::-1])]
+    for i in (0, 2):
+        assert outs[i].info["status"] == 0
+        assert np.max(W.torus_dist(outs[i].t, t_ref)) <= 1e-6
+    assert outs[1].info["status"] in (PRONY_ERANK, PRONY_ENAN) and np.all(outs[1].c == 0)
+
+
 def test_invalid_arguments(ctx):
     from paper_2012_11430_gb300 import PronyError
     P = W.config_problem("C1")
