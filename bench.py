@@ -53,7 +53,11 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 
 
-SPLIT_PRODUCTS = {"bf16x3": 6, "bf16x2": 3}
+# tensor-core products per useful product; TF32 runs at half the BF16 rate (nominal 1.1 vs 2.25 PF)
+SPLIT_PRODUCTS = {"bf16x3": 6, "bf16x2": 3, "tf32x3": 6}
+TC_KERNEL = {"bf16x3": "k_toeplitz_tc<1> (tcgen05 kind::f16, 3 BF16 planes)",
+             "bf16x2": "k_toeplitz_tc<3> (tcgen05 kind::f16, 2 BF16 planes)",
+             "tf32x3": "k_toeplitz_tc<2> (tcgen05 kind::tf32, TF32 hi + lo)"}
 
 
 def measured_peaks() -> dict:
@@ -77,9 +81,10 @@ def roofline(prec, achieved, traffic, launches, stats, total_ms) -> dict:
     if prec in SPLIT_PRODUCTS:
         pk = measured_peaks()
         peak = pk["bf16"] / SPLIT_PRODUCTS[prec]
-        return {"bound": "tensor", "kernel": f"k_toeplitz_tc<{3 if prec == 'bf16x3' else 2}> (tcgen05, A in TMEM)",
+        return {"bound": "tensor", "kernel": TC_KERNEL[prec],
                 "peak": peak, "frac": achieved / peak,
-                "peak_source": f"BF16 dense {pk['bf16']:.0f} TFLOP/s {pk['src']} / {SPLIT_PRODUCTS[prec]} split products",
+                "peak_source": (f"BF16 dense {pk['bf16']:.0f} TFLOP/s {pk['src']} / {SPLIT_PRODUCTS[prec]}"
+                                + (" (3 TF32 products at half the BF16 rate)" if prec == "tf32x3" else " split products")),
                 "tensor_pipe_frac": achieved * SPLIT_PRODUCTS[prec] / pk["bf16"], **common}
     return {"bound": "alu", "kernel": "k_toeplitz_simt (FP32 FFMA)", "peak": FP32_PEAK_TFLOPS,
             "frac": achieved / FP32_PEAK_TFLOPS,

@@ -28,6 +28,7 @@
 // releases its share of B'.
 #include "common.cuh"
 #include "tc_ptx.cuh"
+#include "../../include/prony.h"
 
 #include <cudaTypedefs.h>
 
@@ -106,20 +107,54 @@ __device__ __forceinline__ uint32_t sw128(int row, int k) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 3) ^ (row & 7)) << 4) | ((k & 7) << 1)));
 }
 
+// Split an FP32 value into TF32 hi + lo (round to nearest, ties away; both exactly TF32).
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t* w) {
+  const float hi = tf32_round(x);
+  w[0] = __float_as_uint(hi);
+  w[1] = __float_as_uint(tf32_round(x - hi));
+}
+
+// The three operand encodings.  Per 32-point K chunk (64 real K values) and plane:
+//   BF16X3 / BF16X2  32 TMEM columns (two BF16 per column), 4 MMAs of K = 16, B rows of 128 bytes
+//   TF32X3           64 TMEM columns (one TF32 per column), 8 MMAs of K = 8, B rows split into
+//                    two 128-byte halves (K 0-31, 32-63), each a swizzle atom of its own
+template <int KIND>
+struct TcKind {
+  static constexpr bool TF32 = KIND == PRONY_TF32X3;
+  static constexpr int NPL = KIND == PRONY_BF16X3 ? 3 : 2;     // planes per operand
+  static constexpr int NPROD = NPL == 3 ? 6 : 3;               // products a + b <= NPL - 1
+  static constexpr int PCOLS = TF32 ? 64 : 32;                 // TMEM columns of a plane
+  static constexpr int KSTEPS = TF32 ? 8 : 4;                  // MMAs per plane product and chunk
+  static constexpr int KHALVES = TF32 ? 2 : 1;                 // 128-byte B row segments per chunk
+  static constexpr int NTAB = 2 * NPL;                         // window tables (Re / Im x planes)
+};
+
+__device__ __forceinline__ void mma_ts(bool tf32, uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (tf32) mma_ts_tf32(d, a, b, idesc, acc);
+  else mma_ts_f16(d, a, b, idesc, acc);
+}
+
 // X (N x w complex64, column-major) -> B' planes, K-major: plane pl of problem pi, row 2j / 2j+1,
 // K index 64c + q (q < 32: Re-F block of input point 32c + q, q >= 32: Im-F block).  Rows of a
-// problem from 2w up to its MMA width NT are zero.
-__global__ void k_xb_prep(Dev D, int xbuf, int wsel, uint16_t* xb, int npl, int ntbox, int kpitch) {
+// problem from 2w up to its MMA width NT are zero.  Elements are BF16 (uint16) or TF32 (uint32).
+template <typename E>
+__global__ void k_xb_prep(Dev D, int xbuf, int wsel, E* xb, int kind, int ntbox, int kpitch) {
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
   const ProbState& s = D.st[pi];
   if (s.done) return;
+  const int npl = kind == PRONY_BF16X3 ? 3 : 2;
   const int w = tc_width(s, p, wsel);
   const int nt = ((2 * w + 15) / 16) * 16;
   const int nc = (p.N + 31) / 32;
   int ldx;
   const float2* X = tc_buf(D, xbuf, p, ldx);
-  uint16_t* out = xb + (size_t)pi * npl * ntbox * kpitch;
+  E* out = xb + (size_t)pi * npl * ntbox * kpitch;
   const long long total = (long long)nt * nc * 32;        // (row, chunk, point in chunk)
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
@@ -133,20 +168,32 @@ __global__ void k_xb_prep(Dev D, int xbuf, int wsel, uint16_t* xb, int npl, int 
     float vr, vi;                          // value in the Re-F block and in the Im-F block
     if ((row & 1) == 0) { vr = x.x; vi = -x.y; }
     else { vr = x.y; vi = x.x; }
-    uint32_t wr[3];
-    if (npl == 3) split_pair<3>(vr, vi, wr);
-    else split_pair<2>(vr, vi, wr);
+    uint32_t wr[3], wi[3];
+    if (sizeof(E) == 4) {
+      split_tf32(vr, wr);
+      split_tf32(vi, wi);
+    } else if (npl == 3) {
+      split_pair<3>(vr, vi, wr);
+    } else {
+      split_pair<2>(vr, vi, wr);
+    }
     for (int pl = 0; pl < npl; ++pl) {
-      uint16_t* dst = out + ((size_t)pl * ntbox + row) * kpitch + 64 * c;
-      dst[jj] = (uint16_t)(wr[pl] & 0xFFFF);
-      dst[32 + jj] = (uint16_t)(wr[pl] >> 16);
+      E* dst = out + ((size_t)pl * ntbox + row) * kpitch + 64 * c;
+      if (sizeof(E) == 4) {
+        dst[jj] = (E)wr[pl];
+        dst[32 + jj] = (E)wi[pl];
+      } else {
+        dst[jj] = (E)(wr[pl] & 0xFFFF);
+        dst[32 + jj] = (E)(wr[pl] >> 16);
+      }
     }
   }
 }
 
-// Split planes of the sample grid, paired with the preceding entry (the A' operand of two
-// consecutive input points on a grid line is one table word).  One pass per solve.
-__global__ void k_split_tables(Dev D) {
+// Split planes of the sample grid, table a = part * NPL + plane.  BF16: each word pairs entry x
+// (low half) with entry x - 1 (high half), so the A' operand of two consecutive input points on
+// a grid line is one word; TF32: one word per entry.  One pass per solve.
+__global__ void k_split_tables(Dev D, int tf32) {
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < p.Gd4; x += gridDim.x * blockDim.x) {
@@ -155,14 +202,25 @@ __global__ void k_split_tables(Dev D) {
       const float2* F = (side ? D.gH : D.gF) + p.grid;
       uint32_t* tab = (side ? D.tabH : D.tabF) + p.toff;
       const float2 v = x < p.Gd ? F[x] : make_float2(0.f, 0.f);
-      const float2 v1 = (x >= 1 && x - 1 < p.Gd) ? F[x - 1] : make_float2(0.f, 0.f);
-      uint32_t wr[3], wi[3];
-      split_pair<3>(v.x, v1.x, wr);
-      split_pair<3>(v.y, v1.y, wi);
+      if (tf32) {
+        uint32_t wr[2], wi[2];
+        split_tf32(v.x, wr);
+        split_tf32(v.y, wi);
 #pragma unroll
-      for (int pl = 0; pl < 3; ++pl) {
-        tab[(long long)pl * p.Gd4 + x] = wr[pl];
-        tab[(long long)(3 + pl) * p.Gd4 + x] = wi[pl];
+        for (int pl = 0; pl < 2; ++pl) {
+          tab[(long long)pl * p.Gd4 + x] = wr[pl];
+          tab[(long long)(2 + pl) * p.Gd4 + x] = wi[pl];
+        }
+      } else {
+        const float2 v1 = (x >= 1 && x - 1 < p.Gd) ? F[x - 1] : make_float2(0.f, 0.f);
+        uint32_t wr[3], wi[3];
+        split_pair<3>(v.x, v1.x, wr);
+        split_pair<3>(v.y, v1.y, wi);
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+          tab[(long long)pl * p.Gd4 + x] = wr[pl];
+          tab[(long long)(3 + pl) * p.Gd4 + x] = wi[pl];
+        }
       }
     }
   }
@@ -172,17 +230,38 @@ struct TcParams {
   int adjoint, wsel, ybuf, y_ext;
   int ntbox;                      // B' rows reserved per plane and problem (>= every NT)
   int win_cap;                    // window capacity (words per table, a multiple of 4)
-  int stages;                     // pipeline depth (A stages in TMEM, B stages in shared memory)
-  int acol0;                      // first TMEM column of the A stages (D uses [0, acol0))
+  int stages;                     // B stages in shared memory (A stages: from the TMEM left by D)
   int cs;                         // cluster size (CTAs sharing the B' stages)
 };
 
-template <int NPL>
+// Tensor-memory layout of a CTA whose B' tile has NT rows per plane.  With the planes stacked
+// along N (NPL * NT <= 256), one MMA per A plane a multiplies A_a by B_0..B_{NPL-1-a} at once and
+// D holds one NT-column block per B plane (summed in the epilogue); otherwise every product
+// A_a B_b is its own MMA into a single NT-column block.  A stages follow D.
+struct TcLayout {
+  bool stacked;
+  int dcols, acol0, sa;
+};
+template <int KIND>
+__device__ inline TcLayout tc_layout(int NT) {
+  using K = TcKind<KIND>;
+  TcLayout t;
+  t.stacked = K::NPL * NT <= 256;
+  t.dcols = t.stacked ? K::NPL * NT : NT;
+  t.acol0 = max(32, (t.dcols + 31) / 32 * 32);
+  t.sa = min(TC_MAXSTAGE, (512 - t.acol0) / (K::NPL * K::PCOLS));
+  return t;
+}
+
+template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P, const __grid_constant__ CUtensorMap bmap, int* err) {
-  constexpr int NPROD = NPL == 3 ? 6 : 3;
+  using K = TcKind<KIND>;
+  constexpr int NPL = K::NPL;
+  constexpr int NPROD = K::NPROD;
   constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
   constexpr int PB[6] = {0, 1, 0, 2, 1, 0};
+  constexpr int GPL = K::TF32 ? 2 : 3;            // planes per part in the global tables
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t bar_win, bar_d;
   __shared__ uint64_t bar_bfull[TC_MAXSTAGE], bar_afull[TC_MAXSTAGE], bar_aempty[TC_MAXSTAGE],
@@ -208,12 +287,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (c_begin >= c_end) return;
   const int nchunks = c_end - c_begin;
   const int NT = ((2 * w + 15) / 16) * 16;
-  const int S = P.stages;
+  const int S = P.stages;                         // B stages
+  const TcLayout lay = tc_layout<KIND>(NT);
+  const int SA = lay.sa;                          // A stages
   const int CS = P.cs;
   const uint32_t crank = CS > 1 ? cluster_ctarank() : 0u;
   const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
   bool filler = row0 >= rows_total;
-  if (nchunks > TC_MAXCH || NT > P.ntbox) {       // host sizing rules these out (cluster-uniform)
+  if (nchunks > TC_MAXCH || NT > P.ntbox || SA < 1) {   // host sizing rules these out (cluster-uniform)
     if (threadIdx.x == 0) atomicExch(err, 3);
     return;
   }
@@ -235,12 +316,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t* gtab = (P.adjoint ? D.tabH : D.tabF) + p.toff;
 
   // shared memory: B stages (1024-aligned, the same offsets in every CTA), then the window of
-  // the 2 NPL split-plane tables
+  // the split-plane tables.  A B stage holds KHALVES x NPL x NT rows of 128 bytes: for each
+  // 128-byte K segment the planes are stacked with a stride of NT rows, so one descriptor spans
+  // B_0 .. B_{NPL-1}.
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
-  const uint32_t plane_bytes = (uint32_t)P.ntbox * 128u;
-  const uint32_t stage_bytes = (uint32_t)NPL * plane_bytes;
+  const uint32_t stage_bytes = (uint32_t)(K::KHALVES * NPL * P.ntbox) * 128u;
+  const uint32_t half_bytes = (uint32_t)(NPL * NT) * 128u;
   unsigned char* Bs = sm;
   uint32_t* wtab = (uint32_t*)(sm + (size_t)S * stage_bytes);   // table a at wtab + a * win_cap
 
@@ -256,9 +339,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(&bar_d, 1);
     for (int i = 0; i < S; ++i) {
       mbar_init(&bar_bfull[i], 1);
+      mbar_init(&bar_bempty[i], CS);            // one release per CTA of the cluster
+    }
+    for (int i = 0; i < SA; ++i) {
       mbar_init(&bar_afull[i], TC_APROD);
       mbar_init(&bar_aempty[i], 1);
-      mbar_init(&bar_bempty[i], CS);            // one release per CTA of the cluster
     }
     s_err = 0;
     fence_barrier_init();
@@ -279,18 +364,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------- TMA: window and B' share
     if (lane == 0) {
       if (!filler) {
-        mbar_arrive_expect_tx(&bar_win, (uint32_t)(2 * NPL * wlen) * 4u);
+        mbar_arrive_expect_tx(&bar_win, (uint32_t)(K::NTAB * wlen) * 4u);
 #pragma unroll
         for (int part = 0; part < 2; ++part)
 #pragma unroll
           for (int pl = 0; pl < NPL; ++pl)
-            tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap, gtab + (long long)(3 * part + pl) * p.Gd4 + wlo,
+            tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap, gtab + (long long)(GPL * part + pl) * p.Gd4 + wlo,
                         (uint32_t)wlen * 4u, &bar_win);
       }
-      const int ng = NT / TC_BOXR, units = NPL * ng;
+      const int ng = NT / TC_BOXR, units = K::KHALVES * NPL * ng;
       const int u_lo = (int)crank * units / CS, u_hi = ((int)crank + 1) * units / CS;
       const int yrow0 = job.prob * NPL * P.ntbox;
-      const uint32_t stage_tx = (uint32_t)(NPL * NT * 128);
+      const uint32_t stage_tx = (uint32_t)K::KHALVES * half_bytes;
       int issued = 0;
       for (int it = 0; it < nchunks; ++it) {
         const int s = it % S, u = it / S;
@@ -298,9 +383,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (it >= S && !mbar_wait(&bar_bempty[s], (u - 1) & 1, TC_SPIN)) { s_err = 1; break; }
         mbar_arrive_expect_tx(&bar_bfull[s], stage_tx);
         for (int un = u_lo; un < u_hi; ++un) {
-          const int pl = un / ng, g = un % ng;
-          unsigned char* dst = Bs + (size_t)s * stage_bytes + (size_t)pl * plane_bytes + (size_t)g * TC_BOXR * 128;
-          const int x = 64 * (c_begin + it), y = yrow0 + pl * P.ntbox + g * TC_BOXR;
+          const int kh = un / (NPL * ng), rem = un % (NPL * ng), pl = rem / ng, g = rem % ng;
+          unsigned char* dst = Bs + (size_t)s * stage_bytes + (size_t)kh * half_bytes + (size_t)(pl * NT + g * TC_BOXR) * 128;
+          const int x = 64 * (c_begin + it) + 32 * kh, y = yrow0 + pl * P.ntbox + g * TC_BOXR;
           if (CS > 1) tma_load_2d_mc(dst, &bmap, x, y, &bar_bfull[s], cmask);
           else tma_load_2d(dst, &bmap, x, y, &bar_bfull[s]);
         }
@@ -316,10 +401,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(TC_BM, NT);
+      uint32_t idesc[NPL];                        // stacked: A_a times B_0..B_{NPL-1-a}
+#pragma unroll
+      for (int a = 0; a < NPL; ++a) {
+        const int n = lay.stacked ? (NPL - a) * NT : NT;
+        idesc[a] = K::TF32 ? idesc_tf32_f32(TC_BM, n) : idesc_bf16_f32(TC_BM, n);
+      }
       for (int it = 0; it < nchunks; ++it) {
-        const int s = it % S, u = it / S;
-        if ((!filler && !mbar_wait(&bar_afull[s], u & 1, TC_SPIN)) || !mbar_wait(&bar_bfull[s], u & 1, TC_SPIN)) {
+        const int s = it % S, u = it / S, sa = it % SA, ua = it / SA;
+        if ((!filler && !mbar_wait(&bar_afull[sa], ua & 1, TC_SPIN)) || !mbar_wait(&bar_bfull[s], u & 1, TC_SPIN)) {
           s_err = 1;
           break;
         }
@@ -329,17 +419,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int r = 0; r < CS; ++r) mbar_arrive_remote(&bar_bempty[s], (uint32_t)r);
           continue;
         }
-        const uint32_t a0 = tb + P.acol0 + (uint32_t)s * NPL * 32;
+        const uint32_t a0 = tb + lay.acol0 + (uint32_t)sa * NPL * K::PCOLS;
         const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
 #pragma unroll
-        for (int pr = 0; pr < NPROD; ++pr) {
-          const uint32_t a_pl = a0 + PA[pr] * 32;
-          const uint64_t bd = sdesc_sw128(bsm + PB[pr] * plane_bytes);
+        for (int kk = 0; kk < K::KSTEPS; ++kk) {
+          // K step kk: 8 TMEM columns of A; 32 bytes into the 128-byte segment kk / 4 of B
+          const uint32_t bseg = bsm + (uint32_t)(kk >> 2) * half_bytes;
+          const uint64_t bdk = sdesc_sw128(bseg) + 2 * (kk & 3);
+          if (lay.stacked) {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            mma_ts_f16(tb, a_pl + 8 * kk, bd + 2 * kk, idesc, (it > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+            for (int a = 0; a < NPL; ++a)
+              mma_ts(K::TF32, tb, a0 + a * K::PCOLS + 8 * kk, bdk, idesc[a], (it > 0 || kk > 0 || a > 0) ? 1u : 0u);
+          } else {
+#pragma unroll
+            for (int pr = 0; pr < NPROD; ++pr) {
+              const uint64_t bd = sdesc_sw128(bseg + (uint32_t)(PB[pr] * NT) * 128u) + 2 * (kk & 3);
+              mma_ts(K::TF32, tb, a0 + PA[pr] * K::PCOLS + 8 * kk, bd, idesc[0], (it > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+            }
+          }
         }
-        tc_commit(&bar_aempty[s]);
+        tc_commit(&bar_aempty[sa]);
         if (CS > 1) tc_commit_mc(&bar_bempty[s], cmask);
         else tc_commit(&bar_bempty[s]);
       }
@@ -358,30 +457,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
     if (!ok) s_err = 1;
+    constexpr int NW = K::TF32 ? 16 : 8;          // words per part and plane: 16 points
     for (int it = 0; ok && it < nchunks; ++it) {
-      const int s = it % S, u = it / S;
-      if (it >= S && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (u - 1) & 1, TC_SPIN))) {
+      const int s = it % SA, u = it / SA;
+      if (it >= SA && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (u - 1) & 1, TC_SPIN))) {
         s_err = 1;
         break;
       }
       const int g0 = ghalf[2 * it + hh];
-      const uint32_t a0 = tb + lane_off + P.acol0 + (uint32_t)s * NPL * 32 + 8 * hh;
+      // TMEM column of (plane pl, part, point j of this half): BF16 two points per column at
+      // pl * 32 + part * 16 + hh * 8 + j / 2; TF32 one point per column at pl * 64 + part * 32 + hh * 16 + j
+      const uint32_t a0 = tb + lane_off + lay.acol0 + (uint32_t)s * NPL * K::PCOLS + hh * NW;
+      // all table words of the chunk are loaded before the first tensor-memory store (the stores
+      // are compiler barriers), so the loads overlap
+      uint32_t wv[2][NPL][NW];
       if (g0 >= 0) {
-        // the 16 points lie on one grid line: F(k - h_j) sits at window index x - j, and the
-        // pair (j, j + 1) = (2jp, 2jp + 1) is table word x - 2jp
+        // the 16 points lie on one grid line: F(k - h_j) sits at window index x - j; a BF16 word
+        // pairs the points (2jp, 2jp + 1) at table entry x - 2jp
         const int x = vrow ? gk - g0 : 16;        // rows past the end read nothing (any in-range x)
 #pragma unroll
         for (int part = 0; part < 2; ++part)
 #pragma unroll
           for (int pl = 0; pl < NPL; ++pl) {
             const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap + x;
-            uint32_t wv[8];
 #pragma unroll
-            for (int jp = 0; jp < 8; ++jp) wv[jp] = vrow ? T[-2 * jp] : 0u;
-            tmem_st_x8(a0 + pl * 32 + part * 16, wv);
+            for (int e = 0; e < NW; ++e) wv[part][pl][e] = vrow ? T[-(16 / NW) * e] : 0u;
           }
       } else {
-        // points on several grid lines: each half word from its own table entry
+        // points on several grid lines: each point from its own table entry
         const int h = 32 * (c_begin + it) + 16 * hh + (lane & 15);
         const int ghl = h < p.N ? grid_of_h(h, p) : INT_MIN;
         int xs[16];
@@ -395,16 +498,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int pl = 0; pl < NPL; ++pl) {
             const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap;
-            uint32_t wv[8];
 #pragma unroll
-            for (int jp = 0; jp < 8; ++jp) {
-              const uint32_t lo = xs[2 * jp] >= 0 ? (T[xs[2 * jp]] & 0xFFFFu) : 0u;
-              const uint32_t hi = xs[2 * jp + 1] >= 0 ? (T[xs[2 * jp + 1]] << 16) : 0u;
-              wv[jp] = lo | hi;
+            for (int e = 0; e < NW; ++e) {
+              if (K::TF32) {
+                wv[part][pl][e] = xs[e] >= 0 ? T[xs[e]] : 0u;
+              } else {
+                const uint32_t lo = xs[2 * e] >= 0 ? (T[xs[2 * e]] & 0xFFFFu) : 0u;
+                const uint32_t hi = xs[2 * e + 1] >= 0 ? (T[xs[2 * e + 1]] << 16) : 0u;
+                wv[part][pl][e] = lo | hi;
+              }
             }
-            tmem_st_x8(a0 + pl * 32 + part * 16, wv);
           }
       }
+#pragma unroll
+      for (int part = 0; part < 2; ++part)
+#pragma unroll
+        for (int pl = 0; pl < NPL; ++pl) {
+          const uint32_t col = a0 + pl * K::PCOLS + part * (K::PCOLS / 2);
+          if (K::TF32) tmem_st_x16(col, wv[part][pl]);
+          else tmem_st_x8(col, wv[part][pl]);
+        }
       tmem_st_wait();
       tc_fence_before();
       __syncwarp();
@@ -419,6 +532,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t v[16];
         tmem_ld_x16(tb + lane_off + c0, v);
         tmem_ld_wait();
+        if (lay.stacked) {                        // sum the per-plane column blocks
+          for (int b = 1; b < NPL; ++b) {
+            uint32_t vb[16];
+            tmem_ld_x16(tb + lane_off + b * NT + c0, vb);
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(vb[e]));
+          }
+        }
         if (vrow) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -465,43 +587,50 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map over the B' planes: 2-D (K innermost, kpitch BF16; rows), boxes of 64 K x 16 rows,
-// 128-byte swizzle.  Every box starts at K = 64c: 128-byte aligned.
-int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows) {
+// Tensor map over the B' planes: 2-D (K innermost, kpitch elements; rows), boxes of 128 bytes of K
+// (64 BF16 or 32 TF32) x 16 rows, 128-byte swizzle.  Every box starts at a multiple of 128 bytes.
+int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows, int tf32) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return -1;
+  const int eb = tf32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)kpitch, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)kpitch * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)TC_BOXR};
+  cuuint64_t strides[1] = {(cuuint64_t)kpitch * eb};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)TC_BOXR};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xb, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xb, dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
-size_t tc_smem_bytes(int npl, int ntbox, int stages, int win_cap) {
-  return 1024 + (size_t)stages * npl * ntbox * 128 + (size_t)2 * npl * win_cap * 4;
+int tc_planes(int kind) { return kind == PRONY_BF16X3 ? 3 : 2; }
+size_t tc_stage_bytes(int kind, int ntbox) { return (size_t)(kind == PRONY_TF32X3 ? 2 : 1) * tc_planes(kind) * ntbox * 128; }
+size_t tc_elem_bytes(int kind) { return kind == PRONY_TF32X3 ? 4 : 2; }
+
+size_t tc_smem_bytes(int kind, int ntbox, int stages, int win_cap) {
+  return 1024 + (size_t)stages * tc_stage_bytes(kind, ntbox) + (size_t)2 * tc_planes(kind) * win_cap * 4;
 }
 
-void launch_split_tables(const Dev& D, cudaStream_t s) {
+void launch_split_tables(const Dev& D, int kind, cudaStream_t s) {
   note_launch();
   dim3 g(std::max(1, std::min((D.maxGd + 3) / 4 / 256 + 1, 64)), D.nprob);
-  k_split_tables<<<g, 256, 0, s>>>(D);
+  k_split_tables<<<g, 256, 0, s>>>(D, kind == PRONY_TF32X3 ? 1 : 0);
 }
 
-void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int npl, int ntbox, int kpitch, cudaStream_t s) {
+void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, int ntbox, int kpitch, cudaStream_t s) {
   note_launch();
   dim3 g(std::max(1, std::min(((D.maxN + 31) / 32) * 4, 1024)), D.nprob);
-  k_xb_prep<<<g, 256, 0, s>>>(D, xbuf, wsel, (uint16_t*)xb, npl, ntbox, kpitch);
+  if (kind == PRONY_TF32X3) k_xb_prep<uint32_t><<<g, 256, 0, s>>>(D, xbuf, wsel, (uint32_t*)xb, kind, ntbox, kpitch);
+  else k_xb_prep<uint16_t><<<g, 256, 0, s>>>(D, xbuf, wsel, (uint16_t*)xb, kind, ntbox, kpitch);
 }
 
-template <int NPL>
-static cudaError_t launch_tc_npl(const Dev& D, const ToeplitzJob* jobs, int njobs, const TcParams& P,
+template <int KIND>
+static cudaError_t launch_tc_kind(const Dev& D, const ToeplitzJob* jobs, int njobs, const TcParams& P,
                                  const CUtensorMap& map, int* err, size_t sm, cudaStream_t s) {
   static size_t set = 0;
   if (sm > set) {
     // the attribute must cover this launch's dynamic shared memory (static + dynamic <= 227 KB)
-    cudaError_t e = cudaFuncSetAttribute(k_toeplitz_tc<NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_toeplitz_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     set = sm;
   }
@@ -517,23 +646,36 @@ static cudaError_t launch_tc_npl(const Dev& D, const ToeplitzJob* jobs, int njob
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_toeplitz_tc<NPL>, D, jobs, P, map, err);
+  return cudaLaunchKernelEx(&cfg, k_toeplitz_tc<KIND>, D, jobs, P, map, err);
 }
 
 cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel,
-                               int ybuf, int y_ext, int npl, int ntbox, int win_cap, int stages, int cs,
+                               int ybuf, int y_ext, int kind, int ntbox, int win_cap, int stages, int cs,
                                const CUtensorMap& map, int* err, cudaStream_t s) {
   if (nks > 1) launch_zero_buf(D, ybuf, wsel, y_ext, s);
-  const int acol0 = std::max(32, (ntbox + 31) / 32 * 32);
-  TcParams P{adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, acol0, cs};
-  const size_t sm = tc_smem_bytes(npl, ntbox, stages, win_cap);
+  TcParams P{adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, cs};
+  const size_t sm = tc_smem_bytes(kind, ntbox, stages, win_cap);
   note_launch();
-  return npl == 3 ? launch_tc_npl<3>(D, jobs, njobs, P, map, err, sm, s)
-                  : launch_tc_npl<2>(D, jobs, njobs, P, map, err, sm, s);
+  switch (kind) {
+    case PRONY_BF16X3: return launch_tc_kind<PRONY_BF16X3>(D, jobs, njobs, P, map, err, sm, s);
+    case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2>(D, jobs, njobs, P, map, err, sm, s);
+    default: return launch_tc_kind<PRONY_TF32X3>(D, jobs, njobs, P, map, err, sm, s);
+  }
+}
+
+template <int KIND>
+static int max_active_clusters(const cudaLaunchConfig_t& cfg, size_t sm) {
+  int n = 0;
+  cudaFuncSetAttribute(k_toeplitz_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (cudaOccupancyMaxActiveClusters(&n, k_toeplitz_tc<KIND>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 // Largest cluster size (<= want) for which `cs` CTAs with this shared memory fit on the GPU at once.
-int tc_max_cluster(int npl, int want, size_t sm) {
+int tc_max_cluster(int kind, int want, size_t sm) {
   for (int cs = want; cs > 1; cs /= 2) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs * 16);
@@ -546,17 +688,10 @@ int tc_max_cluster(int npl, int want, size_t sm) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int n = 0;
-    cudaError_t e;
-    if (npl == 3) {
-      cudaFuncSetAttribute(k_toeplitz_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      e = cudaOccupancyMaxActiveClusters(&n, k_toeplitz_tc<3>, &cfg);
-    } else {
-      cudaFuncSetAttribute(k_toeplitz_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      e = cudaOccupancyMaxActiveClusters(&n, k_toeplitz_tc<2>, &cfg);
-    }
-    if (e == cudaSuccess && n > 0) return cs;
-    cudaGetLastError();
+    int n = kind == PRONY_BF16X3 ? max_active_clusters<PRONY_BF16X3>(cfg, sm)
+            : kind == PRONY_BF16X2 ? max_active_clusters<PRONY_BF16X2>(cfg, sm)
+                                   : max_active_clusters<PRONY_TF32X3>(cfg, sm);
+    if (n > 0) return cs;
   }
   return 1;
 }

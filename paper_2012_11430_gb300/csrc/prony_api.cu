@@ -116,7 +116,7 @@ long long ipow(long long b, int e) {
 // Tensor-core configuration of a batch (split BF16 planes).
 struct TcConf {
   bool on = false;
-  int npl = 3, ntbox = 16, kpitch = 64, stages = 2, win_cap = 0, nks = 1, cs = 1;
+  int kind = PRONY_BF16X3, ntbox = 16, kpitch = 64, stages = 2, win_cap = 0, nks = 1, cs = 1;
   int njobs_ext = 0, njobs_in = 0;
   ToeplitzJob* jobs_ext = nullptr;
   ToeplitzJob* jobs_in = nullptr;
@@ -134,7 +134,7 @@ struct Batch {
   TcConf tc;
 };
 
-bool is_tc(int prec) { return prec == PRONY_BF16X3 || prec == PRONY_BF16X2; }
+bool is_tc(int prec) { return prec == PRONY_BF16X3 || prec == PRONY_BF16X2 || prec == PRONY_TF32X3; }
 
 // host copies of the device index maps (window sizing)
 int h_grid_of_row(int row, int L, const ProbDesc& p) {
@@ -177,7 +177,8 @@ int max_window(const ProbDesc& p, int L, int nks) {
 int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   TcConf& T = B.tc;
   T.on = true;
-  T.npl = prec == PRONY_BF16X3 ? 3 : 2;
+  T.kind = prec;
+  const int npl = tc_planes(prec);
   T.ntbox = ((2 * maxw + 15) / 16) * 16;
   int maxnc = 0, tiles_ext = 0, tiles_in = 0;
   for (const auto& p : B.P) {
@@ -185,14 +186,15 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     tiles_ext += (p.Next + 127) / 128;
     tiles_in += (p.N + 127) / 128;
   }
-  const size_t stage = (size_t)T.npl * T.ntbox * 128;
+  const size_t stage = tc_stage_bytes(prec, T.ntbox);
   const size_t avail = 227 * 1024 - 2048 - 4608;   // static shared memory of the kernel (chunk table)
-  // pipeline depth: A stages in TMEM after the accumulator columns, B stages in shared memory,
-  // leaving room for a window of the 2 npl split-plane tables of at least 64 KB
-  const int acol0 = std::max(32, (T.ntbox + 31) / 32 * 32);
-  T.stages = std::min(4, (512 - acol0) / (T.npl * 32));
+  // B stages in shared memory (the kernel derives its A stages from the tensor memory that its
+  // accumulator leaves free), leaving room for a window of the 2 npl split-plane tables of at
+  // least 64 KB
+  if (T.ntbox > 256) return PRONY_EINVAL;
+  T.stages = 4;
   while (T.stages > 1 && 1024 + T.stages * stage + 64 * 1024 > avail) --T.stages;
-  T.win_cap = (int)((avail - 1024 - T.stages * stage) / (8 * T.npl)) & ~3;
+  T.win_cap = (int)((avail - 1024 - T.stages * stage) / (8 * npl)) & ~3;
   if (T.win_cap < 256) return PRONY_EINVAL;
   // split K: enough CTAs to fill the GPU, and every window within the shared-memory capacity
   int nks = std::max(1, std::min(16, (2 * 152 + tiles_in - 1) / std::max(1, tiles_in)));
@@ -225,7 +227,7 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     }
     if (8 * (padded - real) <= padded) { cs = c; break; }
   }
-  if (cs > 1) cs = tc_max_cluster(T.npl, cs, tc_smem_bytes(T.npl, T.ntbox, T.stages, T.win_cap));
+  if (cs > 1) cs = tc_max_cluster(prec, cs, tc_smem_bytes(prec, T.ntbox, T.stages, T.win_cap));
   T.cs = cs;
   std::vector<ToeplitzJob> jobs;
   auto add_jobs = [&](bool ext) {
@@ -248,8 +250,8 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   B.D.tabF = (uint32_t*)ctx->tabF.p;
   B.D.tabH = (uint32_t*)ctx->tabH.p;
   if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
-  const long long rows = (long long)B.P.size() * T.npl * T.ntbox;
-  if ((rc = ensure(ctx->xb, (size_t)rows * T.kpitch * 2))) return rc;
+  const long long rows = (long long)B.P.size() * npl * T.ntbox;
+  if ((rc = ensure(ctx->xb, (size_t)rows * T.kpitch * tc_elem_bytes(prec)))) return rc;
   if ((rc = ensure(ctx->tcerr, 256))) return rc;
   CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
@@ -257,7 +259,7 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
   T.jobs_in = T.jobs_ext + T.njobs_ext;
   T.err = (int*)ctx->tcerr.p;
-  if (encode_xb_map(&T.map, ctx->xb.p, T.kpitch, rows)) {
+  if (encode_xb_map(&T.map, ctx->xb.p, T.kpitch, rows, prec == PRONY_TF32X3)) {
     g_err = "cuTensorMapEncodeTiled failed for the B' planes";
     return PRONY_ECUDA;
   }
@@ -272,9 +274,9 @@ void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int
   if (adjoint < 0) adjoint = ext ? 0 : 1;
   if (B.tc.on) {
     const TcConf& T = B.tc;
-    launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.npl, T.ntbox, T.kpitch, s);
+    launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.kind, T.ntbox, T.kpitch, s);
     cudaError_t e = launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, T.nks,
-                                       adjoint, wsel, ybuf, ext, T.npl, T.ntbox, T.win_cap, T.stages, T.cs, T.map,
+                                       adjoint, wsel, ybuf, ext, T.kind, T.ntbox, T.win_cap, T.stages, T.cs, T.map,
                                        T.err, s);
     if (e != cudaSuccess && ctx->launch_err == cudaSuccess) ctx->launch_err = e;
   } else {
@@ -436,7 +438,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     ctx->snaps.clear();
   }
   launch_prep(D, s);
-  if (B.tc.on) launch_split_tables(D, s);
+  if (B.tc.on) launch_split_tables(D, B.tc.kind, s);
   launch_init_v0(D, o.seed, s);
   tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
   if ((rc = toeplitz(0, 1))) return rc;
@@ -932,7 +934,7 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
   CK(cudaMemcpyAsync(ctx->P.p, B.P.data(), sizeof(ProbDesc), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->grid64.p, grid_dev, sizeof(double2) * B.P[0].Gd, cudaMemcpyDeviceToDevice, ctx->stream));
   launch_prep(B.D, ctx->stream);
-  if (B.tc.on) launch_split_tables(B.D, ctx->stream);
+  if (B.tc.on) launch_split_tables(B.D, B.tc.kind, ctx->stream);
   // operate directly on the caller's buffers: X as V (ld N), Y as Y (ld L^d)
   Dev D = B.D;
   D.V = (float2*)X_dev;

@@ -207,10 +207,13 @@ def test_batched_matches_single_and_oracle(ctx):
 # Split-BF16 products: three planes represent an FP32 value exactly; the three dropped products
 # (relative 2^-24, 2^-24, 2^-32) add ~3 u32 per term; two planes round each operand to 16 bits
 # (x = x0 + x1 with |error| <= 2^-17 |x|) and drop x1 y1, ~3 * 2^-16 per term.
-TC_REL = {"bf16x3": lambda N: (2 * N + 32) * U32, "bf16x2": lambda N: (2 * N + 16) * U32 + 3 * 2.0 ** -16}
+# 3xTF32: x = hi + lo with hi, lo TF32 (11 significant bits each) leaves |x - hi - lo| <= 2^-22 |x|;
+# the dropped product lo_a lo_b is below 2^-22 |a b|: ~4 * 2^-22 per term on top of FP32 accumulation.
+TC_REL = {"bf16x3": lambda N: (2 * N + 32) * U32, "bf16x2": lambda N: (2 * N + 16) * U32 + 3 * 2.0 ** -16,
+          "tf32x3": lambda N: (2 * N + 16) * U32 + 4 * 2.0 ** -22}
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "tf32x3"])
 @pytest.mark.parametrize("d,n,r,L_ext,adjoint", [
     (1, 7, 3, 1, 0), (1, 40, 5, 0, 1), (2, 15, 10, 1, 0), (2, 15, 10, 0, 1), (2, 9, 5, 1, 0),
     (2, 9, 17, 0, 1), (3, 4, 7, 1, 0), (3, 4, 7, 0, 1), (2, 31, 40, 1, 0), (2, 63, 20, 1, 0),
@@ -236,14 +239,15 @@ def test_toeplitz_product_tensor_core(ctx, prec, d, n, r, L_ext, adjoint):
     assert np.all(np.abs(Y - ref) <= bound + 1e-30), float(np.max(np.abs(Y - ref) / (bound + 1e-30)))
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("name,d,n,m,seed", [
     ("C1", 2, 15, 5, None), ("d1", 1, 40, 3, 5), ("d2rag", 2, 9, 7, 7), ("d3", 3, 5, 4, 8),
     ("d2m12", 2, 23, 12, 10),
 ])
-def test_solve_tensor_core_bf16x3_matches_oracle(ctx, name, d, n, m, seed):
+def test_solve_tensor_core_matches_oracle(ctx, prec, name, d, n, m, seed):
     from paper_2012_11430_gb300 import default_opts
     P = W.config_problem("C1") if seed is None else W.make_problem(name, d, n, m, seed)
-    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision="bf16x3"))
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision=prec))
     t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m)
     assert res.info["status"] == 0, res.info
     _check_solution(res, t_o, c_o)
@@ -262,7 +266,7 @@ def test_build_S_tensor_core_matches_oracle(ctx):
         assert np.linalg.norm(S_al - S_o[l]) / np.linalg.norm(S_o[l]) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "tf32x3"])
 def test_solve_noisy_C2_tensor_core(ctx, prec):
     from paper_2012_11430_gb300 import default_opts
     P = W.config_problem("C2")
@@ -290,3 +294,24 @@ def test_batched_mixed_iteration_counts(ctx, prec):
         assert r.info["status"] == 0 and np.all(np.isfinite(r.c))
         assert np.max(W.torus_dist(single.t, r.t)) <= 1e-6
         assert np.linalg.norm(single.c - r.c) <= 1e-5 * np.linalg.norm(single.c)
+
+
+@pytest.fixture(scope="module")
+def c3_problem():
+    P = W.config_problem("C3")
+    t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
+    return P, W.match_to_truth(t_o, c_o, P.t, P.c)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32x3", "bf16x2"])
+def test_precision_study_C3(ctx, c3_problem, prec):
+    """d=3, n=19 (N=8000), m=40, 50 dB: every arithmetic of the Toeplitz products stays within
+    1.5x the FP64 oracle's forward error (+1e-6); the errors are printed for the record."""
+    from paper_2012_11430_gb300 import default_opts
+    P, (te_o, ce_o) = c3_problem
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision=prec))
+    te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
+    print(f"C3 {prec}: t error {te_g:.3e} (oracle {te_o:.3e}), c error {ce_g:.3e} (oracle {ce_o:.3e}), "
+          f"iterations {res.info['power_iters']}")
+    assert res.info["status"] == 0, res.info
+    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6
