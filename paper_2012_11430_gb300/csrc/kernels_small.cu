@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
     if (mode == QR_RANK) {
       st.rank_det = s_rank >= 0 ? s_rank : w;
       st.rank_used = rho;
-      if (rho < p.m) set_status(st, ST_ERANK);
+      if (rho < p.m || st.rank_det < p.m) set_status(st, ST_ERANK);   // Section 2.2: rank below m
     }
     if (rho == 0) {
       set_status(st, ST_ERANK);

@@ -133,11 +133,16 @@ __global__ void k_zero_small(Dev D, long long off, long long bytes) {
 }
 
 // ----------------------------------------------------------------------------- tall-skinny Gram
-// out[a][b] += sum_r conj(X[r, a]) Z[r, b] over a block of GRAM_CHUNK rows.  Each thread owns a
-// 2x2 tile of (a, b) and a residue class of rows; partial sums (FP32) meet in shared memory and
-// each block adds its totals to the FP64 output with one atomic per entry.
+// out[a][b] += sum_r conj(X[r, a]) Z[r, b] over a block of GRAM_CHUNK rows.  Rows are staged in
+// shared memory GRAM_ROWS at a time, transposed (row-major, padded) so that threads reading
+// neighbouring columns hit different banks.  Each thread owns a 4x4 tile of (a, b); when there
+// are fewer tiles than threads, threads split the staged rows into row groups, and when there are
+// more, the tiles are processed in batches of blockDim.x (every batch re-stages the rows).  FP32
+// partial sums meet in shared memory and each block adds its totals to the FP64 output with one
+// atomic per entry.
 constexpr int GRAM_ROWS = 32;       // rows staged per pass
 constexpr int GRAM_CHUNK = 512;     // rows per block
+constexpr int GRAM_T = 4;           // register tile (GRAM_T x GRAM_T complex accumulators)
 
 __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
                                               long long out_off, int out_ld) {
@@ -151,68 +156,74 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
   if (r_begin >= p.N || a <= 0 || b <= 0) return;
   const int r_end = min(p.N, r_begin + GRAM_CHUNK);
   const int LR = D.L.LDR;
-  float2* Xs = smem;                              // [a][GRAM_ROWS]
-  float2* Zs = smem + LR * GRAM_ROWS;             // [b][GRAM_ROWS]
-  float* acc_s = (float*)(smem + 2 * LR * GRAM_ROWS);   // [a][b] complex as 2 floats
+  const int lda = a + 1, ldb = b + 1;             // padded row strides of the staged rows
+  float2* Xs = smem;                              // [GRAM_ROWS][lda]
+  float2* Zs = smem + GRAM_ROWS * (LR + 1);       // [GRAM_ROWS][ldb]
+  float* acc_s = (float*)(smem + 2 * GRAM_ROWS * (LR + 1));   // [a][b] complex as 2 floats
   int ldx, ldz;
   const float2* X = buf_base(D, xbuf, p, ldx);
   const float2* Z = buf_base(D, zbuf, p, ldz);
-  const int na = (a + 1) >> 1, nb = (b + 1) >> 1, ntile = na * nb;
-  const int RG = max(1, min(GRAM_ROWS, (int)blockDim.x / ntile));
-  const int tile = threadIdx.x % ntile, grp = threadIdx.x / ntile;
-  const bool active = grp < RG && (int)threadIdx.x < ntile * RG;
-  const int ta = tile / nb, tb = tile % nb;
-  for (int e = threadIdx.x; e < 2 * a * b; e += blockDim.x) acc_s[e] = 0.f;
-  float2 acc[2][2] = {{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}};
-  for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS) {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < (a + b) * GRAM_ROWS; idx += blockDim.x) {
-      int rr = idx % GRAM_ROWS, col = idx / GRAM_ROWS;
-      int r = r0 + rr;
-      if (col < a) {
-        Xs[col * GRAM_ROWS + rr] =
-            r < r_end ? X[(long long)col * ldx + buf_row(xbuf, p, r, xshift)] : make_float2(0.f, 0.f);
-      } else {
-        int cz = col - a;
-        Zs[cz * GRAM_ROWS + rr] =
-            r < r_end ? Z[(long long)cz * ldz + buf_row(zbuf, p, r, zshift)] : make_float2(0.f, 0.f);
-      }
-    }
-    __syncthreads();
-    if (active) {
-      const int ia0 = 2 * ta, jb0 = 2 * tb;
-      for (int rr = grp; rr < GRAM_ROWS; rr += RG) {
-        float2 xa[2], zb[2];
+  const int na = (a + GRAM_T - 1) / GRAM_T, nb = (b + GRAM_T - 1) / GRAM_T, ntile = na * nb;
+  const int nthr = blockDim.x;
+  const int per_batch = min(ntile, nthr);
+  const int RG = max(1, min(GRAM_ROWS, nthr / per_batch));   // row groups (1 when tiles >= threads)
+  const int nbatch = (ntile + per_batch - 1) / per_batch;
+  for (int e = threadIdx.x; e < 2 * a * b; e += nthr) acc_s[e] = 0.f;
+  for (int batch = 0; batch < nbatch; ++batch) {
+    const int tile = batch * per_batch + threadIdx.x % per_batch, grp = threadIdx.x / per_batch;
+    const bool active = grp < RG && tile < ntile;
+    const int ia0 = GRAM_T * (tile / nb), jb0 = GRAM_T * (tile % nb);
+    float2 acc[GRAM_T][GRAM_T];
 #pragma unroll
-        for (int i = 0; i < 2; ++i) xa[i] = ia0 + i < a ? Xs[(ia0 + i) * GRAM_ROWS + rr] : make_float2(0.f, 0.f);
+    for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) zb[j] = jb0 + j < b ? Zs[(jb0 + j) * GRAM_ROWS + rr] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            acc[i][j].x += xa[i].x * zb[j].x + xa[i].y * zb[j].y;
-            acc[i][j].y += xa[i].x * zb[j].y - xa[i].y * zb[j].x;
-          }
-      }
-    }
-  }
-  __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        int ia = 2 * ta + i, jb = 2 * tb + j;
-        if (ia < a && jb < b) {
-          atomicAdd(&acc_s[2 * (ia * b + jb)], acc[i][j].x);
-          atomicAdd(&acc_s[2 * (ia * b + jb) + 1], acc[i][j].y);
+      for (int j = 0; j < GRAM_T; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS) {
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < (a + b) * GRAM_ROWS; idx += nthr) {
+        const int rr = idx % GRAM_ROWS, col = idx / GRAM_ROWS;
+        const int r = r0 + rr;
+        if (col < a) {
+          Xs[rr * lda + col] = r < r_end ? X[(long long)col * ldx + buf_row(xbuf, p, r, xshift)] : make_float2(0.f, 0.f);
+        } else {
+          const int cz = col - a;
+          Zs[rr * ldb + cz] = r < r_end ? Z[(long long)cz * ldz + buf_row(zbuf, p, r, zshift)] : make_float2(0.f, 0.f);
         }
       }
+      __syncthreads();
+      if (active) {
+        for (int rr = grp; rr < GRAM_ROWS; rr += RG) {
+          float2 xa[GRAM_T], zb[GRAM_T];
+#pragma unroll
+          for (int i = 0; i < GRAM_T; ++i) xa[i] = ia0 + i < a ? Xs[rr * lda + ia0 + i] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int j = 0; j < GRAM_T; ++j) zb[j] = jb0 + j < b ? Zs[rr * ldb + jb0 + j] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int i = 0; i < GRAM_T; ++i)
+#pragma unroll
+            for (int j = 0; j < GRAM_T; ++j) {
+              acc[i][j].x += xa[i].x * zb[j].x + xa[i].y * zb[j].y;   // conj(x) z
+              acc[i][j].y += xa[i].x * zb[j].y - xa[i].y * zb[j].x;
+            }
+        }
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < GRAM_T; ++i)
+#pragma unroll
+        for (int j = 0; j < GRAM_T; ++j) {
+          const int ia = ia0 + i, jb = jb0 + j;
+          if (ia < a && jb < b) {
+            atomicAdd(&acc_s[2 * (ia * b + jb)], acc[i][j].x);
+            atomicAdd(&acc_s[2 * (ia * b + jb) + 1], acc[i][j].y);
+          }
+        }
+    }
   }
   __syncthreads();
   double2* out = (double2*)(D.small + p.soff + out_off);
-  for (int e = threadIdx.x; e < a * b; e += blockDim.x) {
+  for (int e = threadIdx.x; e < a * b; e += nthr) {
     int ia = e / b, jb = e % b;
     atomicAdd(&out[ia * out_ld + jb].x, (double)acc_s[2 * e]);
     atomicAdd(&out[ia * out_ld + jb].y, (double)acc_s[2 * e + 1]);
@@ -543,7 +554,7 @@ void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_
 void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
                  int out_ld, cudaStream_t s) {
   static size_t set = 0;
-  size_t sm = sizeof(float2) * (2 * (size_t)D.L.LDR * GRAM_ROWS + (size_t)D.L.LDR * D.L.LDR);
+  size_t sm = sizeof(float2) * (2 * (size_t)(D.L.LDR + 1) * GRAM_ROWS + (size_t)D.L.LDR * D.L.LDR);
   if (sm > set) {
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;

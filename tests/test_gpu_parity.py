@@ -315,3 +315,21 @@ def test_precision_study_C3(ctx, c3_problem, prec):
           f"iterations {res.info['power_iters']}")
     assert res.info["status"] == 0, res.info
     assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_detect_rank_mode(ctx, prec):
+    """Unknown number of terms (Algorithm 3's rank determination, Section 2.2): called with an
+    overestimate m' > m and rank_mode = 1, the solver detects rank m from the pivoted QR and
+    returns exactly the m true terms (the remaining m' - m slots zero); with rank_mode = 0 it
+    reports the detected rank and PRONY_ERANK."""
+    from paper_2012_11430_gb300 import PRONY_ERANK, default_opts
+    P = W.make_problem("rank", 2, 15, 5, 77)
+    m_over = 8
+    res = ctx.solve(P.grid, P.d, P.n, m_over, default_opts(precision=prec, rank_mode=1))
+    assert res.info["rank_detected"] == P.m and res.info["rank_used"] == P.m, res.info
+    order = np.lexsort(P.t.T[::-1])
+    _check_solution(type(res)(res.t[:P.m], res.c[:P.m], res.info), P.t[order], P.c[order])
+    assert np.all(res.c[P.m:] == 0)
+    res0 = ctx.solve(P.grid, P.d, P.n, m_over, default_opts(precision=prec), allow=(PRONY_ERANK,))
+    assert res0.info["status"] == PRONY_ERANK and res0.info["rank_detected"] == P.m
