@@ -262,17 +262,17 @@ void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, 
                      int ybuf, int y_ext, int maxw, int precision, cudaStream_t s);
 
 // kernels_tc.cu (tensor-core Toeplitz products: split BF16 planes or TF32 hi + lo)
-int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows, int tf32);
 int tc_planes(int kind);
 size_t tc_stage_bytes(int kind, int ntbox);
 size_t tc_elem_bytes(int kind);
 size_t tc_smem_bytes(int kind, int ntbox, int stages, int win_cap);
+long long tc_prob_stride(int kind, int ntbox, int maxnc);
 int tc_max_cluster(int kind, int want, size_t smem);
 void launch_split_tables(const Dev& D, int kind, cudaStream_t s);
-void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, int ntbox, int kpitch, cudaStream_t s);
+void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, long long prob_stride, cudaStream_t s);
 cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel,
                                int ybuf, int y_ext, int kind, int ntbox, int win_cap, int stages, int cs,
-                               const CUtensorMap& map, int* err, cudaStream_t s);
+                               const void* xb, long long prob_stride, int* err, cudaStream_t s);
 
 // kernels_refine.cu (Levenberg-Marquardt refinement of (t, c))
 long long lm_workspace_bytes(int m, int d);

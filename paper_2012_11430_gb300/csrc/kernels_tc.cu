@@ -8,15 +8,16 @@
 // a + b <= NPL - 1 are accumulated in FP32 in tensor memory (3 products for two planes,
 // 6 for three planes, which represent FP32 inputs exactly).
 //
-// B' depends on the problem and the K chunk only, so one small kernel (k_xb_prep) writes its
-// planes once per product, K-major, and the CTAs read them with 2-D TMA in the 128-byte swizzle
-// layout of the MMA.  The CTAs of a thread-block cluster work on consecutive 128-row tiles of
-// the same problem and K range: each loads a share of every B' stage and multicasts it to all,
+// B' depends on the problem and the K chunk only, so one small kernel (k_xb_prep) writes it once
+// per product, already in the shared-memory image the MMA reads (planes stacked, rows of 128
+// bytes, 128-byte swizzle), one contiguous tile per K chunk; a CTA moves its share of a stage
+// with one bulk copy.  The CTAs of a thread-block cluster work on consecutive 128-row tiles of
+// the same problem and K range: each copies a share of every B' stage and multicasts it to all,
 // which divides the L2 -> SM traffic of B' by the cluster size.
 //
 // One CTA = 128 output rows x all 2w columns x a range of K chunks.  Warp roles:
-//   warp 0      TMA: the CTA's window of the split-plane sample tables (cp.async.bulk) and its
-//               share of the B' stages (multicast)
+//   warp 0      bulk copies: the CTA's window of the split-plane sample tables and its share of
+//               every B' stage (multicast)
 //   warp 1      MMA issue (one thread): tcgen05.mma, A from tensor memory, B from shared memory
 //   warps 2-9   A' producers: each chunk's Toeplitz tile is gathered from the window (its BF16
 //               planes are split once per solve, k_split_tables, two input points per word) and
@@ -30,8 +31,6 @@
 #include "tc_ptx.cuh"
 #include "../../include/prony.h"
 
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -43,7 +42,6 @@ constexpr uint32_t TC_SPIN = 1u << 24;      // bounded mbarrier polls (~seconds)
 constexpr int TC_MAXSTAGE = 8;
 constexpr int TC_APROD = 8;                 // A' warps (two per TMEM lane quadrant)
 constexpr int TC_THREADS = 32 * (2 + TC_APROD);
-constexpr int TC_BOXR = 16;                // rows of one B' TMA box
 constexpr int TC_MAXCH = 512;               // K chunks per CTA (host splits K to stay below)
 
 __device__ inline int tc_width(const ProbState& s, const ProbDesc& p, int sel) {
@@ -139,53 +137,72 @@ __device__ __forceinline__ void mma_ts(bool tf32, uint32_t d, uint32_t a, uint64
   else mma_ts_f16(d, a, b, idesc, acc);
 }
 
-// X (N x w complex64, column-major) -> B' planes, K-major: plane pl of problem pi, row 2j / 2j+1,
-// K index 64c + q (q < 32: Re-F block of input point 32c + q, q >= 32: Im-F block).  Rows of a
-// problem from 2w up to its MMA width NT are zero.  Elements are BF16 (uint16) or TF32 (uint32).
-template <typename E>
-__global__ void k_xb_prep(Dev D, int xbuf, int wsel, E* xb, int kind, int ntbox, int kpitch) {
+// X (N x w complex64, column-major) -> B' tiles.  B' row 2j / 2j+1 (output column), K index
+// 64c + q (q < 32: Re-F block of input point 32c + q, q >= 32: Im-F block): row 2j holds
+// (Re X_j, -Im X_j), row 2j+1 (Im X_j, Re X_j); rows from 2w up to NT are zero.  Chunk c of a
+// problem is one contiguous tile in the shared-memory image of a B stage: KHALVES segments of
+// NPL planes of NT rows of 128 bytes (BF16: 64 K per row; TF32: 32 K per row and segment), the
+// 16-byte groups of row R swizzled by R mod 8 (the 128-byte swizzle of the MMA descriptor).
+// One thread writes one 16-byte group of every plane.
+template <int KIND>
+__global__ void k_xb_prep(Dev D, int xbuf, int wsel, unsigned char* xb, long long prob_stride) {
+  using K = TcKind<KIND>;
+  constexpr int NPL = K::NPL;
+  constexpr int EPG = K::TF32 ? 4 : 8;               // elements per 16-byte group
+  constexpr int GPC = 64 / EPG;                       // groups per chunk row (all segments)
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
   const ProbState& s = D.st[pi];
   if (s.done) return;
-  const int npl = kind == PRONY_BF16X3 ? 3 : 2;
   const int w = tc_width(s, p, wsel);
-  const int nt = ((2 * w + 15) / 16) * 16;
+  const int NT = ((2 * w + 15) / 16) * 16;
   const int nc = (p.N + 31) / 32;
+  const size_t tile_bytes = (size_t)K::KHALVES * NPL * NT * 128;
   int ldx;
   const float2* X = tc_buf(D, xbuf, p, ldx);
-  E* out = xb + (size_t)pi * npl * ntbox * kpitch;
-  const long long total = (long long)nt * nc * 32;        // (row, chunk, point in chunk)
+  unsigned char* out = xb + prob_stride * pi;
+  const long long total = (long long)nc * NT * GPC;   // (chunk, row, group)
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
-    const int jj = (int)(q % 32);
-    const long long t = q / 32;
-    const int c = (int)(t % nc);
-    const int row = (int)(t / nc);
-    const int h = 32 * c + jj;
+    const int g = (int)(q % GPC);
+    const long long t = q / GPC;
+    const int row = (int)(t % NT);
+    const int c = (int)(t / NT);
     const int j = row >> 1;
-    const float2 x = (h < p.N && j < w) ? X[(long long)j * ldx + h] : make_float2(0.f, 0.f);
-    float vr, vi;                          // value in the Re-F block and in the Im-F block
-    if ((row & 1) == 0) { vr = x.x; vi = -x.y; }
-    else { vr = x.y; vi = x.x; }
-    uint32_t wr[3], wi[3];
-    if (sizeof(E) == 4) {
-      split_tf32(vr, wr);
-      split_tf32(vi, wi);
-    } else if (npl == 3) {
-      split_pair<3>(vr, vi, wr);
-    } else {
-      split_pair<2>(vr, vi, wr);
+    const int k0 = g * EPG;                            // K index of the group's first element
+    const bool im_block = k0 >= 32;
+    const int h0 = 32 * c + (k0 & 31);
+    float v[EPG];
+#pragma unroll
+    for (int e = 0; e < EPG; ++e) {
+      const int h = h0 + e;
+      const float2 x = (h < p.N && j < w) ? X[(long long)j * ldx + h] : make_float2(0.f, 0.f);
+      v[e] = (row & 1) == 0 ? (im_block ? -x.y : x.x) : (im_block ? x.x : x.y);
     }
-    for (int pl = 0; pl < npl; ++pl) {
-      E* dst = out + ((size_t)pl * ntbox + row) * kpitch + 64 * c;
-      if (sizeof(E) == 4) {
-        dst[jj] = (E)wr[pl];
-        dst[32 + jj] = (E)wi[pl];
-      } else {
-        dst[jj] = (E)(wr[pl] & 0xFFFF);
-        dst[32 + jj] = (E)(wr[pl] >> 16);
+    uint32_t pw[3][4];                                 // planes x 16 bytes
+    if (K::TF32) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint32_t w2[2];
+        split_tf32(v[e], w2);
+        pw[0][e] = w2[0];
+        pw[1][e] = w2[1];
       }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint32_t w3[3];
+        split_pair<NPL>(v[2 * e], v[2 * e + 1], w3);
+#pragma unroll
+        for (int pl = 0; pl < NPL; ++pl) pw[pl][e] = w3[pl];
+      }
+    }
+    const int seg = K::TF32 ? (g >> 3) : 0, gs = K::TF32 ? (g & 7) : g;   // segment, group in the row
+    unsigned char* tile = out + (size_t)c * tile_bytes + (size_t)seg * NPL * NT * 128;
+#pragma unroll
+    for (int pl = 0; pl < NPL; ++pl) {
+      const int R = pl * NT + row;                     // row within the segment (NT is a multiple of 8)
+      *(uint4*)(tile + (size_t)R * 128 + ((gs ^ (R & 7)) << 4)) = make_uint4(pw[pl][0], pw[pl][1], pw[pl][2], pw[pl][3]);
     }
   }
 }
@@ -227,6 +244,8 @@ __global__ void k_split_tables(Dev D, int tf32) {
 }
 
 struct TcParams {
+  const unsigned char* xb;        // B' tiles (k_xb_prep)
+  long long prob_stride;          // bytes of B' tiles per problem
   int adjoint, wsel, ybuf, y_ext;
   int ntbox;                      // B' rows reserved per plane and problem (>= every NT)
   int win_cap;                    // window capacity (words per table, a multiple of 4)
@@ -237,7 +256,9 @@ struct TcParams {
 // Tensor-memory layout of a CTA whose B' tile has NT rows per plane.  With the planes stacked
 // along N (NPL * NT <= 256), one MMA per A plane a multiplies A_a by B_0..B_{NPL-1-a} at once and
 // D holds one NT-column block per B plane (summed in the epilogue); otherwise every product
-// A_a B_b is its own MMA into a single NT-column block.  A stages follow D.
+// A_a B_b is its own MMA into a single NT-column block.  A stages follow D; an A stage holds half
+// a chunk (16 input points: their Re and Im K blocks, every plane), so the A pipeline is twice as
+// deep as with whole-chunk stages in the same tensor memory.
 struct TcLayout {
   bool stacked;
   int dcols, acol0, sa;
@@ -249,13 +270,13 @@ __device__ inline TcLayout tc_layout(int NT) {
   t.stacked = K::NPL * NT <= 256;
   t.dcols = t.stacked ? K::NPL * NT : NT;
   t.acol0 = max(32, (t.dcols + 31) / 32 * 32);
-  t.sa = min(TC_MAXSTAGE, (512 - t.acol0) / (K::NPL * K::PCOLS));
+  t.sa = min(TC_MAXSTAGE, (512 - t.acol0) / (K::NPL * K::PCOLS / 2));   // half-chunk A stages
   return t;
 }
 
 template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P, const __grid_constant__ CUtensorMap bmap, int* err) {
+    k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P, int* err) {
   using K = TcKind<KIND>;
   constexpr int NPL = K::NPL;
   constexpr int NPROD = K::NPROD;
@@ -289,7 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int NT = ((2 * w + 15) / 16) * 16;
   const int S = P.stages;                         // B stages
   const TcLayout lay = tc_layout<KIND>(NT);
-  const int SA = lay.sa;                          // A stages
+  const int SA = lay.sa;                          // A stages (half chunks)
   const int CS = P.cs;
   const uint32_t crank = CS > 1 ? cluster_ctarank() : 0u;
   const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
@@ -342,7 +363,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&bar_bempty[i], CS);            // one release per CTA of the cluster
     }
     for (int i = 0; i < SA; ++i) {
-      mbar_init(&bar_afull[i], TC_APROD);
+      mbar_init(&bar_afull[i], TC_APROD / 2);   // the four warps (one per lane quadrant) of a half
       mbar_init(&bar_aempty[i], 1);
     }
     s_err = 0;
@@ -372,22 +393,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap, gtab + (long long)(GPL * part + pl) * p.Gd4 + wlo,
                         (uint32_t)wlen * 4u, &bar_win);
       }
-      const int ng = NT / TC_BOXR, units = K::KHALVES * NPL * ng;
-      const int u_lo = (int)crank * units / CS, u_hi = ((int)crank + 1) * units / CS;
-      const int yrow0 = job.prob * NPL * P.ntbox;
-      const uint32_t stage_tx = (uint32_t)K::KHALVES * half_bytes;
+      // this CTA's share of each B' tile: a contiguous range of whole 1 KB blocks
+      const uint32_t tile_bytes = (uint32_t)K::KHALVES * half_bytes;
+      const int kb = (int)(tile_bytes >> 10);
+      const uint32_t off = (uint32_t)((int)crank * kb / CS) << 10;
+      const uint32_t len = (uint32_t)(((int)crank + 1) * kb / CS - (int)crank * kb / CS) << 10;
+      const unsigned char* src0 = P.xb + P.prob_stride * job.prob + (size_t)c_begin * tile_bytes;
       int issued = 0;
       for (int it = 0; it < nchunks; ++it) {
         const int s = it % S, u = it / S;
         // stage s is free once every CTA of the cluster has consumed its previous contents
         if (it >= S && !mbar_wait(&bar_bempty[s], (u - 1) & 1, TC_SPIN)) { s_err = 1; break; }
-        mbar_arrive_expect_tx(&bar_bfull[s], stage_tx);
-        for (int un = u_lo; un < u_hi; ++un) {
-          const int kh = un / (NPL * ng), rem = un % (NPL * ng), pl = rem / ng, g = rem % ng;
-          unsigned char* dst = Bs + (size_t)s * stage_bytes + (size_t)kh * half_bytes + (size_t)(pl * NT + g * TC_BOXR) * 128;
-          const int x = 64 * (c_begin + it) + 32 * kh, y = yrow0 + pl * P.ntbox + g * TC_BOXR;
-          if (CS > 1) tma_load_2d_mc(dst, &bmap, x, y, &bar_bfull[s], cmask);
-          else tma_load_2d(dst, &bmap, x, y, &bar_bfull[s]);
+        mbar_arrive_expect_tx(&bar_bfull[s], tile_bytes);
+        if (len > 0) {
+          unsigned char* dst = Bs + (size_t)s * stage_bytes + off;
+          const unsigned char* src = src0 + (size_t)it * tile_bytes + off;
+          if (CS > 1) tma_load_1d_mc(dst, src, len, &bar_bfull[s], cmask);
+          else tma_load_1d(dst, src, len, &bar_bfull[s]);
         }
         ++issued;
       }
@@ -408,37 +430,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         idesc[a] = K::TF32 ? idesc_tf32_f32(TC_BM, n) : idesc_bf16_f32(TC_BM, n);
       }
       for (int it = 0; it < nchunks; ++it) {
-        const int s = it % S, u = it / S, sa = it % SA, ua = it / SA;
-        if ((!filler && !mbar_wait(&bar_afull[sa], ua & 1, TC_SPIN)) || !mbar_wait(&bar_bfull[s], u & 1, TC_SPIN)) {
+        const int s = it % S, u = it / S;
+        if (!mbar_wait(&bar_bfull[s], u & 1, TC_SPIN)) {
           s_err = 1;
           break;
         }
-        tc_fence_after();
         if (filler) {
           // nothing to multiply: release this CTA's copy of the stage to every loader
+          tc_fence_after();
           for (int r = 0; r < CS; ++r) mbar_arrive_remote(&bar_bempty[s], (uint32_t)r);
           continue;
         }
-        const uint32_t a0 = tb + lay.acol0 + (uint32_t)sa * NPL * K::PCOLS;
         const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
+        bool ok = true;
 #pragma unroll
-        for (int kk = 0; kk < K::KSTEPS; ++kk) {
-          // K step kk: 8 TMEM columns of A; 32 bytes into the 128-byte segment kk / 4 of B
-          const uint32_t bseg = bsm + (uint32_t)(kk >> 2) * half_bytes;
-          const uint64_t bdk = sdesc_sw128(bseg) + 2 * (kk & 3);
-          if (lay.stacked) {
+        for (int half = 0; half < 2; ++half) {
+          // half-chunk stage: points 16 half .. +15, i.e. the K steps of their Re and Im blocks
+          const int hs = 2 * it + half, sa = hs % SA, ua = hs / SA;
+          if (!mbar_wait(&bar_afull[sa], ua & 1, TC_SPIN)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = tb + lay.acol0 + (uint32_t)sa * NPL * (K::PCOLS / 2);
 #pragma unroll
-            for (int a = 0; a < NPL; ++a)
-              mma_ts(K::TF32, tb, a0 + a * K::PCOLS + 8 * kk, bdk, idesc[a], (it > 0 || kk > 0 || a > 0) ? 1u : 0u);
-          } else {
+          for (int k2 = 0; k2 < K::KSTEPS / 2; ++k2) {
+            // k2 < KSTEPS/4: Re block, else Im block; 8 TMEM columns per K step
+            const int part = k2 / (K::KSTEPS / 4), kin = k2 % (K::KSTEPS / 4);
+            const int kk = part * (K::KSTEPS / 2) + half * (K::KSTEPS / 4) + kin;   // K step within the chunk
+            const uint32_t bseg = bsm + (uint32_t)(kk >> 2) * half_bytes;
+            const uint64_t bdk = sdesc_sw128(bseg) + 2 * (kk & 3);
+            const uint32_t acol = a0 + part * (K::PCOLS / 4) + 8 * kin;
+            const uint32_t first = (it == 0 && half == 0 && k2 == 0) ? 0u : 1u;
+            if (lay.stacked) {
 #pragma unroll
-            for (int pr = 0; pr < NPROD; ++pr) {
-              const uint64_t bd = sdesc_sw128(bseg + (uint32_t)(PB[pr] * NT) * 128u) + 2 * (kk & 3);
-              mma_ts(K::TF32, tb, a0 + PA[pr] * K::PCOLS + 8 * kk, bd, idesc[0], (it > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+              for (int a = 0; a < NPL; ++a)
+                mma_ts(K::TF32, tb, acol + a * (K::PCOLS / 2), bdk, idesc[a], (a > 0) ? 1u : first);
+            } else {
+#pragma unroll
+              for (int pr = 0; pr < NPROD; ++pr) {
+                const uint64_t bd = sdesc_sw128(bseg + (uint32_t)(PB[pr] * NT) * 128u) + 2 * (kk & 3);
+                mma_ts(K::TF32, tb, acol + PA[pr] * (K::PCOLS / 2), bd, idesc[0], (pr > 0) ? 1u : first);
+              }
             }
           }
+          tc_commit(&bar_aempty[sa]);
         }
-        tc_commit(&bar_aempty[sa]);
+        if (!ok) {
+          s_err = 1;
+          break;
+        }
         if (CS > 1) tc_commit_mc(&bar_bempty[s], cmask);
         else tc_commit(&bar_bempty[s]);
       }
@@ -459,15 +497,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (!ok) s_err = 1;
     constexpr int NW = K::TF32 ? 16 : 8;          // words per part and plane: 16 points
     for (int it = 0; ok && it < nchunks; ++it) {
-      const int s = it % SA, u = it / SA;
-      if (it >= SA && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (u - 1) & 1, TC_SPIN))) {
+      const int hs = 2 * it + hh, s = hs % SA, u = hs / SA;     // this warp's half-chunk stage
+      if (hs >= SA && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (u - 1) & 1, TC_SPIN))) {
         s_err = 1;
         break;
       }
       const int g0 = ghalf[2 * it + hh];
-      // TMEM column of (plane pl, part, point j of this half): BF16 two points per column at
-      // pl * 32 + part * 16 + hh * 8 + j / 2; TF32 one point per column at pl * 64 + part * 32 + hh * 16 + j
-      const uint32_t a0 = tb + lane_off + lay.acol0 + (uint32_t)s * NPL * K::PCOLS + hh * NW;
+      // TMEM column of (plane pl, part, point j of this half) in the half-chunk stage: BF16 two
+      // points per column at pl * 16 + part * 8 + j / 2; TF32 one point per column at
+      // pl * 32 + part * 16 + j
+      const uint32_t a0 = tb + lane_off + lay.acol0 + (uint32_t)s * NPL * (K::PCOLS / 2);
       // all table words of the chunk are loaded before the first tensor-memory store (the stores
       // are compiler barriers), so the loads overlap
       uint32_t wv[2][NPL][NW];
@@ -514,7 +553,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int part = 0; part < 2; ++part)
 #pragma unroll
         for (int pl = 0; pl < NPL; ++pl) {
-          const uint32_t col = a0 + pl * K::PCOLS + part * (K::PCOLS / 2);
+          const uint32_t col = a0 + pl * (K::PCOLS / 2) + part * (K::PCOLS / 4);
           if (K::TF32) tmem_st_x16(col, wv[part][pl]);
           else tmem_st_x8(col, wv[part][pl]);
         }
@@ -573,36 +612,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }  // namespace
 
 // ----------------------------------------------------------------------------- host side
-// The driver's tensor-map encoder, looked up through the runtime (the library does not link
-// libcuda, so it also loads on machines without a GPU driver).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
-
-// Tensor map over the B' planes: 2-D (K innermost, kpitch elements; rows), boxes of 128 bytes of K
-// (64 BF16 or 32 TF32) x 16 rows, 128-byte swizzle.  Every box starts at a multiple of 128 bytes.
-int encode_xb_map(CUtensorMap* map, void* xb, int kpitch, long long rows, int tf32) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return -1;
-  const int eb = tf32 ? 4 : 2;
-  cuuint64_t dims[2] = {(cuuint64_t)kpitch, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)kpitch * eb};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)TC_BOXR};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xb, dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? 0 : (int)r;
-}
-
 int tc_planes(int kind) { return kind == PRONY_BF16X3 ? 3 : 2; }
 size_t tc_stage_bytes(int kind, int ntbox) { return (size_t)(kind == PRONY_TF32X3 ? 2 : 1) * tc_planes(kind) * ntbox * 128; }
 size_t tc_elem_bytes(int kind) { return kind == PRONY_TF32X3 ? 4 : 2; }
@@ -617,16 +626,23 @@ void launch_split_tables(const Dev& D, int kind, cudaStream_t s) {
   k_split_tables<<<g, 256, 0, s>>>(D, kind == PRONY_TF32X3 ? 1 : 0);
 }
 
-void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, int ntbox, int kpitch, cudaStream_t s) {
+// Bytes of B' tiles reserved per problem: every chunk at the widest tile of the batch.
+long long tc_prob_stride(int kind, int ntbox, int maxnc) { return (long long)maxnc * (long long)tc_stage_bytes(kind, ntbox); }
+
+void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, long long prob_stride, cudaStream_t s) {
   note_launch();
   dim3 g(std::max(1, std::min(((D.maxN + 31) / 32) * 4, 1024)), D.nprob);
-  if (kind == PRONY_TF32X3) k_xb_prep<uint32_t><<<g, 256, 0, s>>>(D, xbuf, wsel, (uint32_t*)xb, kind, ntbox, kpitch);
-  else k_xb_prep<uint16_t><<<g, 256, 0, s>>>(D, xbuf, wsel, (uint16_t*)xb, kind, ntbox, kpitch);
+  unsigned char* b = (unsigned char*)xb;
+  switch (kind) {
+    case PRONY_BF16X3: k_xb_prep<PRONY_BF16X3><<<g, 256, 0, s>>>(D, xbuf, wsel, b, prob_stride); break;
+    case PRONY_BF16X2: k_xb_prep<PRONY_BF16X2><<<g, 256, 0, s>>>(D, xbuf, wsel, b, prob_stride); break;
+    default: k_xb_prep<PRONY_TF32X3><<<g, 256, 0, s>>>(D, xbuf, wsel, b, prob_stride); break;
+  }
 }
 
 template <int KIND>
-static cudaError_t launch_tc_kind(const Dev& D, const ToeplitzJob* jobs, int njobs, const TcParams& P,
-                                 const CUtensorMap& map, int* err, size_t sm, cudaStream_t s) {
+static cudaError_t launch_tc_kind(const Dev& D, const ToeplitzJob* jobs, int njobs, const TcParams& P, int* err,
+                                  size_t sm, cudaStream_t s) {
   static size_t set = 0;
   if (sm > set) {
     // the attribute must cover this launch's dynamic shared memory (static + dynamic <= 227 KB)
@@ -646,20 +662,20 @@ static cudaError_t launch_tc_kind(const Dev& D, const ToeplitzJob* jobs, int njo
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_toeplitz_tc<KIND>, D, jobs, P, map, err);
+  return cudaLaunchKernelEx(&cfg, k_toeplitz_tc<KIND>, D, jobs, P, err);
 }
 
 cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel,
                                int ybuf, int y_ext, int kind, int ntbox, int win_cap, int stages, int cs,
-                               const CUtensorMap& map, int* err, cudaStream_t s) {
+                               const void* xb, long long prob_stride, int* err, cudaStream_t s) {
   if (nks > 1) launch_zero_buf(D, ybuf, wsel, y_ext, s);
-  TcParams P{adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, cs};
+  TcParams P{(const unsigned char*)xb, prob_stride, adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, cs};
   const size_t sm = tc_smem_bytes(kind, ntbox, stages, win_cap);
   note_launch();
   switch (kind) {
-    case PRONY_BF16X3: return launch_tc_kind<PRONY_BF16X3>(D, jobs, njobs, P, map, err, sm, s);
-    case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2>(D, jobs, njobs, P, map, err, sm, s);
-    default: return launch_tc_kind<PRONY_TF32X3>(D, jobs, njobs, P, map, err, sm, s);
+    case PRONY_BF16X3: return launch_tc_kind<PRONY_BF16X3>(D, jobs, njobs, P, err, sm, s);
+    case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2>(D, jobs, njobs, P, err, sm, s);
+    default: return launch_tc_kind<PRONY_TF32X3>(D, jobs, njobs, P, err, sm, s);
   }
 }
 

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 #include <atomic>
@@ -77,6 +78,7 @@ struct prony_ctx {
   prony_stats stats{};
   long long launch_base = 0;
   cudaError_t launch_err = cudaSuccess;   // first failed tensor-core launch of the current call
+  std::map<std::string, std::pair<int, int>> tc_tuned;   // batch shape -> (cluster size, K split)
   // refinement: workspace and the CUDA graph of the last argument set
   DBuf lmws;
   struct LmKey {
@@ -116,11 +118,14 @@ long long ipow(long long b, int e) {
 // Tensor-core configuration of a batch (split BF16 planes).
 struct TcConf {
   bool on = false;
-  int kind = PRONY_BF16X3, ntbox = 16, kpitch = 64, stages = 2, win_cap = 0, nks = 1, cs = 1;
+  bool tuned = false;                 // cs / nks chosen (from the context's cache or by timing)
+  int nks_min = 1, cs_max = 1;        // tuning range
+  std::string key;                    // batch shape signature
+  int kind = PRONY_BF16X3, ntbox = 16, stages = 2, win_cap = 0, nks = 1, cs = 1;
+  long long prob_stride = 0;          // bytes of B' tiles per problem
   int njobs_ext = 0, njobs_in = 0;
   ToeplitzJob* jobs_ext = nullptr;
   ToeplitzJob* jobs_in = nullptr;
-  CUtensorMap map;
   int* err = nullptr;
 };
 
@@ -174,6 +179,35 @@ int max_window(const ProbDesc& p, int L, int nks) {
   return mx;
 }
 
+// Job list of the tensor-core products for a cluster size and K split: per problem and K range,
+// its 128-row tiles padded to a multiple of the cluster size (mt >= tiles: filler CTA).
+int tc_set_jobs(prony_ctx* ctx, Batch& B, int cs, int nks) {
+  TcConf& T = B.tc;
+  std::vector<ToeplitzJob> jobs;
+  auto add_jobs = [&](bool ext) {
+    for (int i = 0; i < (int)B.P.size(); ++i) {
+      const int tiles = ((ext ? B.P[i].Next : B.P[i].N) + 127) / 128;
+      const int padded = (tiles + cs - 1) / cs * cs;
+      const int nk = std::min(nks, std::max(1, (B.P[i].N + 31) / 32));
+      for (int ks = 0; ks < nk; ++ks)
+        for (int mt = 0; mt < padded; ++mt) jobs.push_back({i, mt, ks, nk});
+    }
+  };
+  add_jobs(true);
+  T.njobs_ext = (int)jobs.size();
+  add_jobs(false);
+  T.njobs_in = (int)jobs.size() - T.njobs_ext;
+  int rc;
+  if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
+  CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
+  T.jobs_in = T.jobs_ext + T.njobs_ext;
+  T.cs = cs;
+  T.nks = nks;
+  return PRONY_OK;
+}
+
 int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   TcConf& T = B.tc;
   T.on = true;
@@ -207,18 +241,18 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     }
     if (fits || nks >= maxnc) break;
   }
-  T.nks = nks;
-  T.kpitch = 64 * maxnc;
-  // Cluster size: the CTAs of a cluster share the B' stages of one problem and K range; tiles
-  // of a problem are padded to a multiple of the cluster with filler CTAs, so a size is used
-  // only while the fillers stay below 1/8 of the CTAs.
-  int want = 4;
+  T.nks_min = nks;
+  T.prob_stride = tc_prob_stride(prec, T.ntbox, maxnc);
+  // Cluster sizes: the CTAs of a cluster share the B' stages of one problem and K range; tiles
+  // of a problem are padded to a multiple of the cluster with filler CTAs, so a size is a
+  // candidate only while the fillers stay below 1/8 of the CTAs.
+  int cs_max = 4;
   if (const char* e = getenv("PRONY_TC_CLUSTER")) {
     const int v = atoi(e);
-    want = v >= 8 ? 8 : v >= 4 ? 4 : v >= 2 ? 2 : 1;
+    cs_max = v >= 4 ? 4 : v >= 2 ? 2 : 1;
   }
   int cs = 1;
-  for (int c = want; c > 1; c /= 2) {
+  for (int c = cs_max; c > 1; c /= 2) {
     long long real = 0, padded = 0;
     for (const auto& p : B.P) {
       const long long te = (p.Next + 127) / 128, ti = (p.N + 127) / 128;
@@ -228,20 +262,15 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     if (8 * (padded - real) <= padded) { cs = c; break; }
   }
   if (cs > 1) cs = tc_max_cluster(prec, cs, tc_smem_bytes(prec, T.ntbox, T.stages, T.win_cap));
-  T.cs = cs;
-  std::vector<ToeplitzJob> jobs;
-  auto add_jobs = [&](bool ext) {
-    for (int i = 0; i < (int)B.P.size(); ++i) {
-      const int tiles = ((ext ? B.P[i].Next : B.P[i].N) + 127) / 128;
-      const int padded = (tiles + cs - 1) / cs * cs;
-      for (int ks = 0; ks < nks; ++ks)
-        for (int mt = 0; mt < padded; ++mt) jobs.push_back({i, mt, ks, nks});   // mt >= tiles: filler
-    }
-  };
-  add_jobs(true);
-  T.njobs_ext = (int)jobs.size();
-  add_jobs(false);
-  T.njobs_in = (int)jobs.size() - T.njobs_ext;
+  T.cs_max = cs;
+  // batch shape signature for the tuning cache
+  T.key = std::to_string(prec) + ":" + std::to_string(B.P.size()) + ":" + std::to_string(maxw) + ":" +
+          std::to_string(maxnc) + ":" + std::to_string(tiles_ext) + ":" + std::to_string(tiles_in) + ":" +
+          std::to_string(nks) + ":" + std::to_string(cs);
+  auto hit = ctx->tc_tuned.find(T.key);
+  T.tuned = hit != ctx->tc_tuned.end() || getenv("PRONY_TC_TUNE") != nullptr && atoi(getenv("PRONY_TC_TUNE")) == 0;
+  const int cs0 = hit != ctx->tc_tuned.end() ? hit->second.first : std::min(2, cs);
+  const int nks0 = hit != ctx->tc_tuned.end() ? hit->second.second : nks;
   int rc;
   long long twords = 64;                              // split-plane tables (+ slack for window rounding)
   for (const auto& p : B.P) twords = std::max(twords, p.toff + 6LL * p.Gd4 + 64);
@@ -249,21 +278,11 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   if ((rc = ensure(ctx->tabH, 4 * (size_t)twords))) return rc;
   B.D.tabF = (uint32_t*)ctx->tabF.p;
   B.D.tabH = (uint32_t*)ctx->tabH.p;
-  if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
-  const long long rows = (long long)B.P.size() * npl * T.ntbox;
-  if ((rc = ensure(ctx->xb, (size_t)rows * T.kpitch * tc_elem_bytes(prec)))) return rc;
+  if ((rc = ensure(ctx->xb, (size_t)B.P.size() * (size_t)T.prob_stride))) return rc;
   if ((rc = ensure(ctx->tcerr, 256))) return rc;
-  CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
-                     ctx->stream));
   CK(cudaMemsetAsync(ctx->tcerr.p, 0, sizeof(int), ctx->stream));
-  T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
-  T.jobs_in = T.jobs_ext + T.njobs_ext;
   T.err = (int*)ctx->tcerr.p;
-  if (encode_xb_map(&T.map, ctx->xb.p, T.kpitch, rows, prec == PRONY_TF32X3)) {
-    g_err = "cuTensorMapEncodeTiled failed for the B' planes";
-    return PRONY_ECUDA;
-  }
-  return PRONY_OK;
+  return tc_set_jobs(ctx, B, cs0, nks0);
 }
 
 // One Toeplitz block product for every live problem of the batch.
@@ -274,15 +293,72 @@ void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int
   if (adjoint < 0) adjoint = ext ? 0 : 1;
   if (B.tc.on) {
     const TcConf& T = B.tc;
-    launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.kind, T.ntbox, T.kpitch, s);
+    launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.kind, T.prob_stride, s);
     cudaError_t e = launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, T.nks,
-                                       adjoint, wsel, ybuf, ext, T.kind, T.ntbox, T.win_cap, T.stages, T.cs, T.map,
-                                       T.err, s);
+                                       adjoint, wsel, ybuf, ext, T.kind, T.ntbox, T.win_cap, T.stages, T.cs,
+                                       ctx->xb.p, T.prob_stride, T.err, s);
     if (e != cudaSuccess && ctx->launch_err == cudaSuccess) ctx->launch_err = e;
   } else {
     launch_toeplitz(D, ext ? B.jobs_ext : B.jobs_in, ext ? B.njobs_ext : B.njobs_in, B.nks, adjoint, xbuf, wsel, ybuf,
                     ext, B.maxw, prec, s);
   }
+}
+
+// Autotuner of the tensor-core products: the first product of a batch shape not seen before is
+// timed (CUDA events on the context stream, one untimed and one timed launch per candidate)
+// for every cluster size up to cs_max and the K splits nks_min and 2 nks_min; the fastest
+// configuration is kept for the batch and cached in the context under the shape signature.
+int tc_autotune(prony_ctx* ctx, Batch& B, const Dev& D, int prec, cudaStream_t s) {
+  TcConf& T = B.tc;
+  std::vector<std::pair<int, int>> cand;
+  for (int cs = 1; cs <= T.cs_max; cs *= 2)
+    for (int f = 1; f <= 2; ++f) {
+      const int nks = T.nks_min * f;
+      if (f == 2 && (nks > 16 || nks > T.nks_min + 8)) continue;
+      cand.push_back({cs, nks});
+    }
+  // room for the largest job list first, so that no candidate reallocates it
+  size_t maxjobs = 0;
+  for (const auto& p : B.P)
+    maxjobs += (size_t)2 * T.nks_min * ((p.Next + 127) / 128 + 4 + (p.N + 127) / 128 + 4);
+  int rc;
+  if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * maxjobs))) return rc;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  std::pair<int, int> pick = {T.cs, T.nks};
+  for (const auto& c : cand) {
+    if ((rc = tc_set_jobs(ctx, B, c.first, c.second))) break;
+    toeplitz_product(ctx, B, D, 1, BUF_V, W_V, BUF_Y, prec, s);
+    cudaEventRecord(e0, s);
+    toeplitz_product(ctx, B, D, 1, BUF_V, W_V, BUF_Y, prec, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {                       // a sticky error: report it
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(e, "tensor-core autotuning");
+    }
+    if (ctx->launch_err != cudaSuccess) {         // this configuration does not launch: skip it
+      ctx->launch_err = cudaSuccess;
+      cudaGetLastError();
+      continue;
+    }
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if ((rc = tc_set_jobs(ctx, B, pick.first, pick.second))) return rc;
+  ctx->tc_tuned[T.key] = pick;
+  T.tuned = true;
+  return PRONY_OK;
 }
 
 // Lay out a batch in the context workspace.  Grid samples are copied from `src`
@@ -441,6 +517,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   if (B.tc.on) launch_split_tables(D, B.tc.kind, s);
   launch_init_v0(D, o.seed, s);
   tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+  if (B.tc.on && !B.tc.tuned && (rc = tc_autotune(ctx, B, D, prec, s))) return rc;
   if ((rc = toeplitz(0, 1))) return rc;
   if (ctx->prof) {
     ctx->snaps.emplace_back(D.nprob);
