@@ -457,6 +457,8 @@ def main():
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "parallelism": f"independent problems, {ws} GPU(s), no collective",
                    "passed_gate": f"{passed}/{B} on rank 0",
+                   "tc_config": {"cluster": stats.get("tc_cluster"), "k_split": stats.get("tc_ksplit"),
+                                 "chosen_by": "autotuner (first product of the batch shape, timed)"},
                    "errors_rank0": {"t_max": max(e[0] for e in errs), "c_max": max(e[1] for e in errs)}},
         "roofline": roofline(args.precision, achieved, traffic, launches, stats, total_ms),
         "cpu_baseline": cpu,

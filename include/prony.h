@@ -206,6 +206,8 @@ typedef struct {
   double toeplitz_ms;        /* summed CUDA-event durations of the Toeplitz launches */
   double toeplitz_flops;     /* summed algorithmic flops of those launches */
   double toeplitz_bytes;     /* summed algorithmic bytes of those launches */
+  int tc_cluster;            /* tensor-core path of the last batch: CTAs per cluster (0: not used) */
+  int tc_ksplit;             /* and the K split of its products, as chosen by the autotuner */
 } prony_stats;
 
 int prony_set_profiling(prony_ctx* ctx, int enable);   /* also resets the statistics */

@@ -400,10 +400,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t len = (uint32_t)(((int)crank + 1) * kb / CS - (int)crank * kb / CS) << 10;
       const unsigned char* src0 = P.xb + P.prob_stride * job.prob + (size_t)c_begin * tile_bytes;
       int issued = 0;
+      int s = 0;
+      uint32_t ph = 0;                            // stage and round parity (no divisions in the loop)
       for (int it = 0; it < nchunks; ++it) {
-        const int s = it % S, u = it / S;
         // stage s is free once every CTA of the cluster has consumed its previous contents
-        if (it >= S && !mbar_wait(&bar_bempty[s], (u - 1) & 1, TC_SPIN)) { s_err = 1; break; }
+        if (it >= S && !mbar_wait(&bar_bempty[s], ph ^ 1u, TC_SPIN)) { s_err = 1; break; }
         mbar_arrive_expect_tx(&bar_bfull[s], tile_bytes);
         if (len > 0) {
           unsigned char* dst = Bs + (size_t)s * stage_bytes + off;
@@ -412,6 +413,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           else tma_load_1d(dst, src, len, &bar_bfull[s]);
         }
         ++issued;
+        if (++s == S) { s = 0; ph ^= 1u; }
       }
       // Tail: the last stages are released by every CTA of the cluster, so every copy into this
       // CTA and every copy this CTA multicast have landed before it exits.
@@ -429,9 +431,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int n = lay.stacked ? (NPL - a) * NT : NT;
         idesc[a] = K::TF32 ? idesc_tf32_f32(TC_BM, n) : idesc_bf16_f32(TC_BM, n);
       }
+      int s = 0, sa = 0;
+      uint32_t ph = 0, pha = 0;                   // B stage / A half-stage and their round parities
       for (int it = 0; it < nchunks; ++it) {
-        const int s = it % S, u = it / S;
-        if (!mbar_wait(&bar_bfull[s], u & 1, TC_SPIN)) {
+        if (!mbar_wait(&bar_bfull[s], ph, TC_SPIN)) {
           s_err = 1;
           break;
         }
@@ -439,6 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           // nothing to multiply: release this CTA's copy of the stage to every loader
           tc_fence_after();
           for (int r = 0; r < CS; ++r) mbar_arrive_remote(&bar_bempty[s], (uint32_t)r);
+          if (++s == S) { s = 0; ph ^= 1u; }
           continue;
         }
         const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
@@ -446,8 +450,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
           // half-chunk stage: points 16 half .. +15, i.e. the K steps of their Re and Im blocks
-          const int hs = 2 * it + half, sa = hs % SA, ua = hs / SA;
-          if (!mbar_wait(&bar_afull[sa], ua & 1, TC_SPIN)) { ok = false; break; }
+          if (!mbar_wait(&bar_afull[sa], pha, TC_SPIN)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = tb + lay.acol0 + (uint32_t)sa * NPL * (K::PCOLS / 2);
 #pragma unroll
@@ -472,6 +475,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
           }
           tc_commit(&bar_aempty[sa]);
+          if (++sa == SA) { sa = 0; pha ^= 1u; }
         }
         if (!ok) {
           s_err = 1;
@@ -479,6 +483,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (CS > 1) tc_commit_mc(&bar_bempty[s], cmask);
         else tc_commit(&bar_bempty[s]);
+        if (++s == S) { s = 0; ph ^= 1u; }
       }
       if (!filler) tc_commit(&bar_d);      // arrives when every MMA issued above has completed
     }
@@ -496,9 +501,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
     if (!ok) s_err = 1;
     constexpr int NW = K::TF32 ? 16 : 8;          // words per part and plane: 16 points
+    // this warp's half-chunk stages: hs = 2 it + hh, stage hs mod SA, round hs / SA (stepped, no divisions)
+    int s = hh % SA, u = hh / SA;
     for (int it = 0; ok && it < nchunks; ++it) {
-      const int hs = 2 * it + hh, s = hs % SA, u = hs / SA;     // this warp's half-chunk stage
-      if (hs >= SA && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (u - 1) & 1, TC_SPIN))) {
+      if (2 * it + hh >= SA && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (uint32_t)(u - 1) & 1u, TC_SPIN))) {
         s_err = 1;
         break;
       }
@@ -561,6 +567,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_afull[s]);
+      s += 2;
+      while (s >= SA) { s -= SA; ++u; }
     }
     // epilogue: D (TMEM) -> Y; the two warps of a quadrant take alternate 16-column groups
     if (__all_sync(0xffffffffu, mbar_wait(&bar_d, 0, TC_SPIN)) && !s_err) {

@@ -565,6 +565,8 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
         fl += 8.0 * rows * q.N * w;
         by += 8.0 * q.Gd + 8.0 * q.N * w + 8.0 * rows * w;
       }
+      ctx->stats.tc_cluster = B.tc.on ? B.tc.cs : 0;
+      ctx->stats.tc_ksplit = B.tc.on ? B.tc.nks : 0;
       ctx->stats.toeplitz_launches += 1;
       ctx->stats.toeplitz_ms += ms;
       ctx->stats.toeplitz_flops += fl;
