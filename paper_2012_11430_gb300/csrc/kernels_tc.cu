@@ -24,7 +24,8 @@
 //               written straight into tensor memory (tcgen05.st); two warps per TMEM
 //               lane quadrant, each taking half of the chunk's input points; then the epilogue
 // The Toeplitz matrix is never formed in HBM: each A' element is F at grid index gk(k) - gh(h).
-// Stages of A (TMEM) and B (shared memory) form an mbarrier pipeline; every wait is bounded.
+// A pipeline stage is one K chunk (its B' tile in shared memory and its A' tile in tensor
+// memory); one full and one empty mbarrier per stage; every wait is bounded.
 // A CTA whose tile lies past the last row of its problem (a cluster filler) only loads and
 // releases its share of B'.
 #include "common.cuh"
@@ -256,9 +257,7 @@ struct TcParams {
 // Tensor-memory layout of a CTA whose B' tile has NT rows per plane.  With the planes stacked
 // along N (NPL * NT <= 256), one MMA per A plane a multiplies A_a by B_0..B_{NPL-1-a} at once and
 // D holds one NT-column block per B plane (summed in the epilogue); otherwise every product
-// A_a B_b is its own MMA into a single NT-column block.  A stages follow D; an A stage holds half
-// a chunk (16 input points: their Re and Im K blocks, every plane), so the A pipeline is twice as
-// deep as with whole-chunk stages in the same tensor memory.
+// A_a B_b is its own MMA into a single NT-column block.  The A stages follow D.
 struct TcLayout {
   bool stacked;
   int dcols, acol0, sa;
@@ -270,7 +269,7 @@ __device__ inline TcLayout tc_layout(int NT) {
   t.stacked = K::NPL * NT <= 256;
   t.dcols = t.stacked ? K::NPL * NT : NT;
   t.acol0 = max(32, (t.dcols + 31) / 32 * 32);
-  t.sa = min(TC_MAXSTAGE, (512 - t.acol0) / (K::NPL * K::PCOLS / 2));   // half-chunk A stages
+  t.sa = min(TC_MAXSTAGE, (512 - t.acol0) / (K::NPL * K::PCOLS));   // whole-chunk A stages
   return t;
 }
 
@@ -285,8 +284,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr int GPL = K::TF32 ? 2 : 3;            // planes per part in the global tables
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t bar_win, bar_d;
-  __shared__ uint64_t bar_bfull[TC_MAXSTAGE], bar_afull[TC_MAXSTAGE], bar_aempty[TC_MAXSTAGE],
-      bar_bempty[TC_MAXSTAGE];
+  __shared__ uint64_t bar_full[TC_MAXSTAGE], bar_empty[TC_MAXSTAGE];
   __shared__ uint32_t s_tmem;
   __shared__ int s_err;
   __shared__ int ghalf[2 * TC_MAXCH];   // grid offset of each half chunk on one grid line, else -1
@@ -308,14 +306,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (c_begin >= c_end) return;
   const int nchunks = c_end - c_begin;
   const int NT = ((2 * w + 15) / 16) * 16;
-  const int S = P.stages;                         // B stages
   const TcLayout lay = tc_layout<KIND>(NT);
-  const int SA = lay.sa;                          // A stages (half chunks)
+  // One pipeline stage = one K chunk: its B' tile in shared memory and its A' tile in tensor
+  // memory, filled together (full barrier: eight A' warps + the loader's byte count) and
+  // released together by one commit of the MMAs that read them.
+  const int S = min(P.stages, lay.sa);
   const int CS = P.cs;
   const uint32_t crank = CS > 1 ? cluster_ctarank() : 0u;
   const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
   bool filler = row0 >= rows_total;
-  if (nchunks > TC_MAXCH || NT > P.ntbox || SA < 1) {   // host sizing rules these out (cluster-uniform)
+  if (nchunks > TC_MAXCH || NT > P.ntbox || S < 1) {   // host sizing rules these out (cluster-uniform)
     if (threadIdx.x == 0) atomicExch(err, 3);
     return;
   }
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t stage_bytes = (uint32_t)(K::KHALVES * NPL * P.ntbox) * 128u;
   const uint32_t half_bytes = (uint32_t)(NPL * NT) * 128u;
   unsigned char* Bs = sm;
-  uint32_t* wtab = (uint32_t*)(sm + (size_t)S * stage_bytes);   // table a at wtab + a * win_cap
+  uint32_t* wtab = (uint32_t*)(sm + (size_t)P.stages * stage_bytes);   // table a at wtab + a * win_cap
 
   if (filler && CS == 1) return;                 // no cluster to serve
 
@@ -359,12 +359,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(&bar_win, 1);
     mbar_init(&bar_d, 1);
     for (int i = 0; i < S; ++i) {
-      mbar_init(&bar_bfull[i], 1);
-      mbar_init(&bar_bempty[i], CS);            // one release per CTA of the cluster
-    }
-    for (int i = 0; i < SA; ++i) {
-      mbar_init(&bar_afull[i], TC_APROD / 2);   // the four warps (one per lane quadrant) of a half
-      mbar_init(&bar_aempty[i], 1);
+      mbar_init(&bar_full[i], TC_APROD + 1);    // eight A' warps + the loader (with the byte count)
+      mbar_init(&bar_empty[i], CS);             // one release per CTA of the cluster
     }
     s_err = 0;
     fence_barrier_init();
@@ -382,7 +378,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tb = s_tmem;
 
   if (warp == 0) {
-    // ------------------------------------------------------------- TMA: window and B' share
+    // ------------------------------------------------------------- bulk copies: window and B' share
     if (lane == 0) {
       if (!filler) {
         mbar_arrive_expect_tx(&bar_win, (uint32_t)(K::NTAB * wlen) * 4u);
@@ -404,13 +400,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t ph = 0;                            // stage and round parity (no divisions in the loop)
       for (int it = 0; it < nchunks; ++it) {
         // stage s is free once every CTA of the cluster has consumed its previous contents
-        if (it >= S && !mbar_wait(&bar_bempty[s], ph ^ 1u, TC_SPIN)) { s_err = 1; break; }
-        mbar_arrive_expect_tx(&bar_bfull[s], tile_bytes);
+        if (it >= S && !mbar_wait_spin(&bar_empty[s], ph ^ 1u, TC_SPIN)) { s_err = 1; break; }
+        mbar_arrive_expect_tx(&bar_full[s], tile_bytes);
         if (len > 0) {
           unsigned char* dst = Bs + (size_t)s * stage_bytes + off;
           const unsigned char* src = src0 + (size_t)it * tile_bytes + off;
-          if (CS > 1) tma_load_1d_mc(dst, src, len, &bar_bfull[s], cmask);
-          else tma_load_1d(dst, src, len, &bar_bfull[s]);
+          if (CS > 1) tma_load_1d_mc(dst, src, len, &bar_full[s], cmask);
+          else tma_load_1d(dst, src, len, &bar_full[s]);
         }
         ++issued;
         if (++s == S) { s = 0; ph ^= 1u; }
@@ -419,7 +415,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // CTA and every copy this CTA multicast have landed before it exits.
       if (!s_err)
         for (int it = max(0, issued - S); it < issued; ++it)
-          if (!mbar_wait(&bar_bempty[it % S], (it / S) & 1, TC_SPIN)) { s_err = 1; break; }
+          if (!mbar_wait_spin(&bar_empty[it % S], (it / S) & 1, TC_SPIN)) { s_err = 1; break; }
       if (!filler && !mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
     }
   } else if (warp == 1) {
@@ -431,178 +427,167 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int n = lay.stacked ? (NPL - a) * NT : NT;
         idesc[a] = K::TF32 ? idesc_tf32_f32(TC_BM, n) : idesc_bf16_f32(TC_BM, n);
       }
-      int s = 0, sa = 0;
-      uint32_t ph = 0, pha = 0;                   // B stage / A half-stage and their round parities
+      int s = 0;
+      uint32_t ph = 0;
       for (int it = 0; it < nchunks; ++it) {
-        if (!mbar_wait(&bar_bfull[s], ph, TC_SPIN)) {
+        if (!mbar_wait_spin(&bar_full[s], ph, TC_SPIN)) {
           s_err = 1;
           break;
         }
-        if (filler) {
-          // nothing to multiply: release this CTA's copy of the stage to every loader
-          tc_fence_after();
-          for (int r = 0; r < CS; ++r) mbar_arrive_remote(&bar_bempty[s], (uint32_t)r);
-          if (++s == S) { s = 0; ph ^= 1u; }
-          continue;
-        }
-        const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
-        bool ok = true;
+        tc_fence_after();
+        if (!filler) {
+          const uint32_t a0 = tb + lay.acol0 + (uint32_t)s * NPL * K::PCOLS;
+          const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          // half-chunk stage: points 16 half .. +15, i.e. the K steps of their Re and Im blocks
-          if (!mbar_wait(&bar_afull[sa], pha, TC_SPIN)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t a0 = tb + lay.acol0 + (uint32_t)sa * NPL * (K::PCOLS / 2);
-#pragma unroll
-          for (int k2 = 0; k2 < K::KSTEPS / 2; ++k2) {
-            // k2 < KSTEPS/4: Re block, else Im block; 8 TMEM columns per K step
-            const int part = k2 / (K::KSTEPS / 4), kin = k2 % (K::KSTEPS / 4);
-            const int kk = part * (K::KSTEPS / 2) + half * (K::KSTEPS / 4) + kin;   // K step within the chunk
+          for (int kk = 0; kk < K::KSTEPS; ++kk) {
+            // K step kk: 8 TMEM columns of A; 32 bytes into the 128-byte segment kk / 4 of B
             const uint32_t bseg = bsm + (uint32_t)(kk >> 2) * half_bytes;
             const uint64_t bdk = sdesc_sw128(bseg) + 2 * (kk & 3);
-            const uint32_t acol = a0 + part * (K::PCOLS / 4) + 8 * kin;
-            const uint32_t first = (it == 0 && half == 0 && k2 == 0) ? 0u : 1u;
+            const uint32_t first = (it == 0 && kk == 0) ? 0u : 1u;
             if (lay.stacked) {
 #pragma unroll
               for (int a = 0; a < NPL; ++a)
-                mma_ts(K::TF32, tb, acol + a * (K::PCOLS / 2), bdk, idesc[a], (a > 0) ? 1u : first);
+                mma_ts(K::TF32, tb, a0 + a * K::PCOLS + 8 * kk, bdk, idesc[a], (a > 0) ? 1u : first);
             } else {
 #pragma unroll
               for (int pr = 0; pr < NPROD; ++pr) {
                 const uint64_t bd = sdesc_sw128(bseg + (uint32_t)(PB[pr] * NT) * 128u) + 2 * (kk & 3);
-                mma_ts(K::TF32, tb, acol + PA[pr] * (K::PCOLS / 2), bd, idesc[0], (pr > 0) ? 1u : first);
+                mma_ts(K::TF32, tb, a0 + PA[pr] * K::PCOLS + 8 * kk, bd, idesc[0], (pr > 0) ? 1u : first);
               }
             }
           }
-          tc_commit(&bar_aempty[sa]);
-          if (++sa == SA) { sa = 0; pha ^= 1u; }
         }
-        if (!ok) {
-          s_err = 1;
-          break;
+        // release the stage (B' in every CTA of the cluster, A' here) once these MMAs are done;
+        // a filler CTA issued none and releases its copy of the stage directly
+        if (filler) {
+          for (int r = 0; r < CS; ++r) mbar_arrive_remote(&bar_empty[s], (uint32_t)r);
+        } else if (CS > 1) {
+          tc_commit_mc(&bar_empty[s], cmask);
+        } else {
+          tc_commit(&bar_empty[s]);
         }
-        if (CS > 1) tc_commit_mc(&bar_bempty[s], cmask);
-        else tc_commit(&bar_bempty[s]);
         if (++s == S) { s = 0; ph ^= 1u; }
       }
       if (!filler) tc_commit(&bar_d);      // arrives when every MMA issued above has completed
     }
-  } else if (!filler) {
+  } else {
     // ------------------------------------------------------------- A' producers + epilogue
     // Warps 2..9: quadrant q = warp & 3 (TMEM lanes 32q..32q+31 = tile rows), half hh of every
-    // K chunk (input points 32c + 16hh .. +15).
+    // K chunk (input points 32c + 16hh .. +15).  A filler CTA's warps only signal the stages.
     const int q = warp & 3;
     const int hh = (warp - 2) >> 2;
     const int i = 32 * q + lane;                // row within the tile
     const int row = row0 + i;
-    const bool vrow = row < rows_total;
+    const bool vrow = row < rows_total && !filler;
     const int gk = vrow ? grid_of_row(row, L, p) - wlo : 0;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    bool ok = __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
+    bool ok = filler || __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
     if (!ok) s_err = 1;
     constexpr int NW = K::TF32 ? 16 : 8;          // words per part and plane: 16 points
-    // this warp's half-chunk stages: hs = 2 it + hh, stage hs mod SA, round hs / SA (stepped, no divisions)
-    int s = hh % SA, u = hh / SA;
+    int s = 0;
+    uint32_t ph = 0;
     for (int it = 0; ok && it < nchunks; ++it) {
-      if (2 * it + hh >= SA && !__all_sync(0xffffffffu, mbar_wait(&bar_aempty[s], (uint32_t)(u - 1) & 1u, TC_SPIN))) {
+      if (it >= S && !__all_sync(0xffffffffu, mbar_wait_spin(&bar_empty[s], ph ^ 1u, TC_SPIN))) {
         s_err = 1;
         break;
       }
-      const int g0 = ghalf[2 * it + hh];
-      // TMEM column of (plane pl, part, point j of this half) in the half-chunk stage: BF16 two
-      // points per column at pl * 16 + part * 8 + j / 2; TF32 one point per column at
-      // pl * 32 + part * 16 + j
-      const uint32_t a0 = tb + lane_off + lay.acol0 + (uint32_t)s * NPL * (K::PCOLS / 2);
-      // all table words of the chunk are loaded before the first tensor-memory store (the stores
-      // are compiler barriers), so the loads overlap
-      uint32_t wv[2][NPL][NW];
-      if (g0 >= 0) {
-        // the 16 points lie on one grid line: F(k - h_j) sits at window index x - j; a BF16 word
-        // pairs the points (2jp, 2jp + 1) at table entry x - 2jp
-        const int x = vrow ? gk - g0 : 16;        // rows past the end read nothing (any in-range x)
+      if (!filler) {
+        const int g0 = ghalf[2 * it + hh];
+        // TMEM column of (plane pl, part, point j of this half): BF16 two points per column at
+        // pl * 32 + part * 16 + hh * 8 + j / 2; TF32 one point per column at pl * 64 + part * 32 + hh * 16 + j
+        const uint32_t a0 = tb + lane_off + lay.acol0 + (uint32_t)s * NPL * K::PCOLS + hh * NW;
+        // all table words of the chunk are loaded before the first tensor-memory store (the
+        // stores are compiler barriers), so the loads overlap
+        uint32_t wv[2][NPL][NW];
+        if (g0 >= 0) {
+          // the 16 points lie on one grid line: F(k - h_j) sits at window index x - j; a BF16
+          // word pairs the points (2jp, 2jp + 1) at table entry x - 2jp
+          const int x = vrow ? gk - g0 : 16;      // rows past the end read nothing (any in-range x)
 #pragma unroll
-        for (int part = 0; part < 2; ++part)
+          for (int part = 0; part < 2; ++part)
 #pragma unroll
-          for (int pl = 0; pl < NPL; ++pl) {
-            const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap + x;
+            for (int pl = 0; pl < NPL; ++pl) {
+              const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap + x;
 #pragma unroll
-            for (int e = 0; e < NW; ++e) wv[part][pl][e] = vrow ? T[-(16 / NW) * e] : 0u;
+              for (int e = 0; e < NW; ++e) wv[part][pl][e] = vrow ? T[-(16 / NW) * e] : 0u;
+            }
+        } else {
+          // points on several grid lines: each point from its own table entry
+          const int h = 32 * (c_begin + it) + 16 * hh + (lane & 15);
+          const int ghl = h < p.N ? grid_of_h(h, p) : INT_MIN;
+          int xs[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int g = __shfl_sync(0xffffffffu, ghl, j);
+            xs[j] = (vrow && g != INT_MIN) ? gk - g : -1;
           }
-      } else {
-        // points on several grid lines: each point from its own table entry
-        const int h = 32 * (c_begin + it) + 16 * hh + (lane & 15);
-        const int ghl = h < p.N ? grid_of_h(h, p) : INT_MIN;
-        int xs[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int g = __shfl_sync(0xffffffffu, ghl, j);
-          xs[j] = (vrow && g != INT_MIN) ? gk - g : -1;
+          for (int part = 0; part < 2; ++part)
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+              const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap;
+#pragma unroll
+              for (int e = 0; e < NW; ++e) {
+                if (K::TF32) {
+                  wv[part][pl][e] = xs[e] >= 0 ? T[xs[e]] : 0u;
+                } else {
+                  const uint32_t lo = xs[2 * e] >= 0 ? (T[xs[2 * e]] & 0xFFFFu) : 0u;
+                  const uint32_t hi = xs[2 * e + 1] >= 0 ? (T[xs[2 * e + 1]] << 16) : 0u;
+                  wv[part][pl][e] = lo | hi;
+                }
+              }
+            }
         }
 #pragma unroll
         for (int part = 0; part < 2; ++part)
 #pragma unroll
           for (int pl = 0; pl < NPL; ++pl) {
-            const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap;
+            const uint32_t col = a0 + pl * K::PCOLS + part * (K::PCOLS / 2);
+            if (K::TF32) tmem_st_x16(col, wv[part][pl]);
+            else tmem_st_x8(col, wv[part][pl]);
+          }
+        tmem_st_wait();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_full[s]);
+      if (++s == S) { s = 0; ph ^= 1u; }
+    }
+    // epilogue: D (TMEM) -> Y; the two warps of a quadrant take alternate 16-column groups
+    if (!filler) {
+      if (__all_sync(0xffffffffu, mbar_wait(&bar_d, 0, TC_SPIN)) && !s_err) {
+        tc_fence_after();
+        int ldy;
+        float2* Y = tc_buf(D, P.ybuf, p, ldy);
+        for (int c0 = 16 * hh; c0 < NT; c0 += 32) {
+          uint32_t v[16];
+          tmem_ld_x16(tb + lane_off + c0, v);
+          tmem_ld_wait();
+          if (lay.stacked) {                      // sum the per-plane column blocks
+            for (int b = 1; b < NPL; ++b) {
+              uint32_t vb[16];
+              tmem_ld_x16(tb + lane_off + b * NT + c0, vb);
+              tmem_ld_wait();
 #pragma unroll
-            for (int e = 0; e < NW; ++e) {
-              if (K::TF32) {
-                wv[part][pl][e] = xs[e] >= 0 ? T[xs[e]] : 0u;
-              } else {
-                const uint32_t lo = xs[2 * e] >= 0 ? (T[xs[2 * e]] & 0xFFFFu) : 0u;
-                const uint32_t hi = xs[2 * e + 1] >= 0 ? (T[xs[2 * e + 1]] << 16) : 0u;
-                wv[part][pl][e] = lo | hi;
+              for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(vb[e]));
+            }
+          }
+          if (vrow) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int j = c0 / 2 + e;
+              if (j < w) {
+                float2 val = make_float2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
+                float2* yp = &Y[(long long)j * ldy + row];
+                if (job.nks == 1) *yp = val;
+                else atomicAdd(yp, val);
               }
             }
           }
+        }
+      } else {
+        s_err = 1;
       }
-#pragma unroll
-      for (int part = 0; part < 2; ++part)
-#pragma unroll
-        for (int pl = 0; pl < NPL; ++pl) {
-          const uint32_t col = a0 + pl * (K::PCOLS / 2) + part * (K::PCOLS / 4);
-          if (K::TF32) tmem_st_x16(col, wv[part][pl]);
-          else tmem_st_x8(col, wv[part][pl]);
-        }
-      tmem_st_wait();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_afull[s]);
-      s += 2;
-      while (s >= SA) { s -= SA; ++u; }
-    }
-    // epilogue: D (TMEM) -> Y; the two warps of a quadrant take alternate 16-column groups
-    if (__all_sync(0xffffffffu, mbar_wait(&bar_d, 0, TC_SPIN)) && !s_err) {
-      tc_fence_after();
-      int ldy;
-      float2* Y = tc_buf(D, P.ybuf, p, ldy);
-      for (int c0 = 16 * hh; c0 < NT; c0 += 32) {
-        uint32_t v[16];
-        tmem_ld_x16(tb + lane_off + c0, v);
-        tmem_ld_wait();
-        if (lay.stacked) {                        // sum the per-plane column blocks
-          for (int b = 1; b < NPL; ++b) {
-            uint32_t vb[16];
-            tmem_ld_x16(tb + lane_off + b * NT + c0, vb);
-            tmem_ld_wait();
-#pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(vb[e]));
-          }
-        }
-        if (vrow) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int j = c0 / 2 + e;
-            if (j < w) {
-              float2 val = make_float2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
-              float2* yp = &Y[(long long)j * ldy + row];
-              if (job.nks == 1) *yp = val;
-              else atomicAdd(yp, val);
-            }
-          }
-        }
-      }
-    } else {
-      s_err = 1;
     }
   }
   tc_fence_before();

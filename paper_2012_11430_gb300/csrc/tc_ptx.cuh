@@ -34,11 +34,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
 // Bounded wait on the phase with the given parity.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
   for (uint32_t i = 0; i < max_iter; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+// Bounded wait by polling (mbarrier.test_wait never suspends the thread): cheaper than try_wait
+// on the pipeline's critical path, where the phase has usually completed already.  A few polls
+// first, then try_wait, which suspends instead of spinning for long waits.
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity, uint32_t max_iter) {
+  for (int i = 0; i < 64; ++i)
+    if (mbar_test_wait(bar, parity)) return true;
+  return mbar_wait(bar, parity, max_iter);
 }
 
 // ----------------------------------------------------------------------------- TMA
