@@ -133,42 +133,42 @@ __global__ void k_zero_small(Dev D, long long off, long long bytes) {
 }
 
 // ----------------------------------------------------------------------------- tall-skinny Gram
-// out[a][b] += sum_r conj(X[r, a]) Z[r, b] over a block of GRAM_CHUNK rows.  Rows are staged in
-// shared memory GRAM_ROWS at a time, transposed (row-major, padded) so that threads reading
-// neighbouring columns hit different banks.  Each thread owns a 4x4 tile of (a, b); when there
-// are fewer tiles than threads, threads split the staged rows into row groups, and when there are
-// more, the tiles are processed in batches of blockDim.x (every batch re-stages the rows).  FP32
-// partial sums meet in shared memory and each block adds its totals to the FP64 output with one
-// atomic per entry.
-constexpr int GRAM_ROWS = 32;       // rows staged per pass
-constexpr int GRAM_CHUNK = 512;     // rows per block
+// out[a][b] += sum_r conj(X[r, a]) Z[r, b] over a block of `chunk` rows (chosen by the launcher
+// so that the batch gives a few blocks per SM: few blocks per problem means few FP64 atomics on
+// the same output entries).  Rows are staged in shared memory GRAM_ROWS at a time, transposed
+// (row-major, padded) so that threads reading neighbouring columns hit different banks.  Each
+// thread owns a 4x4 tile of (a, b); when there are fewer tiles than threads, threads split the
+// staged rows into row groups, whose partial sums are added by a tree in shared memory; when
+// there are more, the tiles are processed in batches of blockDim.x (every batch re-stages the
+// rows).  Each block adds its totals to the FP64 output with one atomic per entry.
+constexpr int GRAM_ROWS = 64;       // rows staged per pass
 constexpr int GRAM_T = 4;           // register tile (GRAM_T x GRAM_T complex accumulators)
 
 __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
-                                              long long out_off, int out_ld) {
+                                              long long out_off, int out_ld, int chunk) {
   extern __shared__ float2 smem[];
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
   const ProbState& s = D.st[pi];
   if (s.done) return;
   const int a = width_of(s, p, xw), b = width_of(s, p, zw);
-  const int r_begin = blockIdx.x * GRAM_CHUNK;
+  const int r_begin = blockIdx.x * chunk;
   if (r_begin >= p.N || a <= 0 || b <= 0) return;
-  const int r_end = min(p.N, r_begin + GRAM_CHUNK);
+  const int r_end = min(p.N, r_begin + chunk);
   const int LR = D.L.LDR;
   const int lda = a + 1, ldb = b + 1;             // padded row strides of the staged rows
   float2* Xs = smem;                              // [GRAM_ROWS][lda]
   float2* Zs = smem + GRAM_ROWS * (LR + 1);       // [GRAM_ROWS][ldb]
-  float* acc_s = (float*)(smem + 2 * GRAM_ROWS * (LR + 1));   // [a][b] complex as 2 floats
+  float2* red = Zs + GRAM_ROWS * (LR + 1);        // [RG][per_batch][16] partial sums (aliased per batch)
   int ldx, ldz;
   const float2* X = buf_base(D, xbuf, p, ldx);
   const float2* Z = buf_base(D, zbuf, p, ldz);
   const int na = (a + GRAM_T - 1) / GRAM_T, nb = (b + GRAM_T - 1) / GRAM_T, ntile = na * nb;
   const int nthr = blockDim.x;
   const int per_batch = min(ntile, nthr);
-  const int RG = max(1, min(GRAM_ROWS, nthr / per_batch));   // row groups (1 when tiles >= threads)
+  const int RG = max(1, min(8, nthr / per_batch));     // row groups (1 when tiles >= threads)
   const int nbatch = (ntile + per_batch - 1) / per_batch;
-  for (int e = threadIdx.x; e < 2 * a * b; e += nthr) acc_s[e] = 0.f;
+  double2* out = (double2*)(D.small + p.soff + out_off);
   for (int batch = 0; batch < nbatch; ++batch) {
     const int tile = batch * per_batch + threadIdx.x % per_batch, grp = threadIdx.x / per_batch;
     const bool active = grp < RG && tile < ntile;
@@ -208,35 +208,53 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
         }
       }
     }
-    if (active) {
+    // row groups: partial sums meet in shared memory, group 0 adds them (fixed order)
+    if (RG > 1) {
+      __syncthreads();
+      if (active && grp > 0) {
+        float2* dst = red + ((size_t)(grp - 1) * per_batch + (tile - batch * per_batch)) * 16;
+#pragma unroll
+        for (int i = 0; i < GRAM_T; ++i)
+#pragma unroll
+          for (int j = 0; j < GRAM_T; ++j) dst[i * GRAM_T + j] = acc[i][j];
+      }
+      __syncthreads();
+      if (active && grp == 0) {
+        for (int g = 1; g < RG; ++g) {
+          const float2* src = red + ((size_t)(g - 1) * per_batch + (tile - batch * per_batch)) * 16;
+#pragma unroll
+          for (int i = 0; i < GRAM_T; ++i)
+#pragma unroll
+            for (int j = 0; j < GRAM_T; ++j) {
+              acc[i][j].x += src[i * GRAM_T + j].x;
+              acc[i][j].y += src[i * GRAM_T + j].y;
+            }
+        }
+      }
+    }
+    if (active && grp == 0) {
 #pragma unroll
       for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
         for (int j = 0; j < GRAM_T; ++j) {
           const int ia = ia0 + i, jb = jb0 + j;
           if (ia < a && jb < b) {
-            atomicAdd(&acc_s[2 * (ia * b + jb)], acc[i][j].x);
-            atomicAdd(&acc_s[2 * (ia * b + jb) + 1], acc[i][j].y);
+            atomicAdd(&out[ia * out_ld + jb].x, (double)acc[i][j].x);
+            atomicAdd(&out[ia * out_ld + jb].y, (double)acc[i][j].y);
           }
         }
     }
   }
-  __syncthreads();
-  double2* out = (double2*)(D.small + p.soff + out_off);
-  for (int e = threadIdx.x; e < a * b; e += nthr) {
-    int ia = e / b, jb = e % b;
-    atomicAdd(&out[ia * out_ld + jb].x, (double)acc_s[2 * e]);
-    atomicAdd(&out[ia * out_ld + jb].y, (double)acc_s[2 * e + 1]);
-  }
 }
 
 // ----------------------------------------------------------------------------- X M products
-// OUT[r, j] = sum_i X[r, i] M[i][j] (- Z[r, j] with OUT = Z - X M for the residual), 64 rows per
-// block; M is staged once per block, each thread takes one row and every fourth column.
-constexpr int APPLY_ROWS = 64;
-
+// OUT[r, j] = sum_i X[r, i] M[i][j] (- Z[r, j] with OUT = Z - X M for the residual).  A block
+// takes `rows` rows (128, or 64 when the blocks are wide), stages them and M in shared memory
+// once, then each thread computes one row and four columns at a time (one X value and four
+// broadcast M values per four complex products).  X and OUT may be the same buffer: every
+// block reads its rows before writing them.
 __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw, long long m_off, int m_double,
-                                               int zbuf, int outbuf, int norm_only) {
+                                               int zbuf, int outbuf, int norm_only, int rows) {
   extern __shared__ float2 smem[];
   __shared__ double shr[32];
   const int pi = blockIdx.y;
@@ -244,51 +262,65 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
   ProbState& s = D.st[pi];
   if (s.done) return;
   const int a = width_of(s, p, xw), b = width_of(s, p, outw);
-  const int r0 = blockIdx.x * APPLY_ROWS;
+  const int r0 = blockIdx.x * rows;
   if (r0 >= p.N || b <= 0) return;
-  float2* Ms = smem;                              // [a][b]  (ld b)
-  float2* Xs = smem + D.L.LDR * D.L.LDR;          // [a][APPLY_ROWS]
-  for (int idx = threadIdx.x; idx < a * b; idx += blockDim.x) {
-    int i = idx / b, j = idx % b;
-    float2 v;
-    if (m_double) {
-      double2 dv = ((const double2*)(D.small + p.soff + m_off))[i * D.L.LDM + j];
-      v = make_float2((float)dv.x, (float)dv.y);
-    } else {
-      v = ((const float2*)(D.small + p.soff + m_off))[i * D.L.LDR + j];
+  const int ldm = (b + 3) & ~3;                   // M rows padded to whole groups of four columns
+  float2* Ms = smem;                              // [a][ldm]
+  float2* Xs = smem + (size_t)D.L.LDR * ((D.L.LDR + 3) & ~3);   // [a][rows]
+  for (int idx = threadIdx.x; idx < a * ldm; idx += blockDim.x) {
+    const int i = idx / ldm, j = idx % ldm;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < b) {
+      if (m_double) {
+        const double2 dv = ((const double2*)(D.small + p.soff + m_off))[i * D.L.LDM + j];
+        v = make_float2((float)dv.x, (float)dv.y);
+      } else {
+        v = ((const float2*)(D.small + p.soff + m_off))[i * D.L.LDR + j];
+      }
     }
     Ms[idx] = v;
   }
   int ldx;
   const float2* X = buf_base(D, xbuf, p, ldx);
-  for (int idx = threadIdx.x; idx < a * APPLY_ROWS; idx += blockDim.x) {
-    int rr = idx % APPLY_ROWS, col = idx / APPLY_ROWS;
-    int r = r0 + rr;
+  for (int idx = threadIdx.x; idx < a * rows; idx += blockDim.x) {
+    const int rr = idx % rows, col = idx / rows;
+    const int r = r0 + rr;
     Xs[idx] = (r < p.N) ? X[(long long)col * ldx + buf_row(xbuf, p, r, -1)] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int rr = threadIdx.x % APPLY_ROWS, cg = threadIdx.x / APPLY_ROWS;
-  const int ngrp = blockDim.x / APPLY_ROWS;
+  const int rr = threadIdx.x % rows, cg = threadIdx.x / rows;
+  const int ngrp = blockDim.x / rows;
   const int r = r0 + rr;
   int ldz = 0, ldo = 0;
   const float2* Z = zbuf >= 0 ? buf_base(D, zbuf, p, ldz) : nullptr;
   float2* O = norm_only ? nullptr : buf_base(D, outbuf, p, ldo);
   double nrm = 0.0;
   if (r < p.N) {
-    for (int j = cg; j < b; j += ngrp) {
-      float2 acc = make_float2(0.f, 0.f);
+    for (int j0 = 4 * cg; j0 < b; j0 += 4 * ngrp) {
+      float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       for (int i = 0; i < a; ++i) {
-        float2 x = Xs[i * APPLY_ROWS + rr], mm = Ms[i * b + j];
-        acc.x += x.x * mm.x - x.y * mm.y;
-        acc.y += x.x * mm.y + x.y * mm.x;
+        const float2 x = Xs[i * rows + rr];
+        const float2* mrow = Ms + i * ldm + j0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 mm = mrow[e];
+          acc[e].x += x.x * mm.x - x.y * mm.y;
+          acc[e].y += x.x * mm.y + x.y * mm.x;
+        }
       }
-      if (Z) {
-        float2 z = Z[(long long)j * ldz + buf_row(zbuf, p, r, -1)];
-        acc.x = z.x - acc.x;
-        acc.y = z.y - acc.y;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = j0 + e;
+        if (j >= b) break;
+        float2 v = acc[e];
+        if (Z) {
+          const float2 z = Z[(long long)j * ldz + buf_row(zbuf, p, r, -1)];
+          v.x = z.x - v.x;
+          v.y = z.y - v.y;
+        }
+        if (norm_only) nrm += (double)v.x * v.x + (double)v.y * v.y;
+        else O[(long long)j * ldo + buf_row(outbuf, p, r, -1)] = v;
       }
-      if (norm_only) nrm += (double)acc.x * acc.x + (double)acc.y * acc.y;
-      else O[(long long)j * ldo + buf_row(outbuf, p, r, -1)] = acc;
     }
   }
   if (norm_only) {
@@ -554,27 +586,34 @@ void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_
 void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
                  int out_ld, cudaStream_t s) {
   static size_t set = 0;
-  size_t sm = sizeof(float2) * (2 * (size_t)(D.L.LDR + 1) * GRAM_ROWS + (size_t)D.L.LDR * D.L.LDR);
+  // staged rows of X and Z, then the row-group partial sums: (RG - 1) x tiles x 16 entries with
+  // RG = min(8, 256 / tiles) when tiles <= 128, at most 224 x 16 (32 tiles, 8 groups)
+  const size_t sm = sizeof(float2) * (2 * (size_t)(D.L.LDR + 1) * GRAM_ROWS + (size_t)224 * 16);
   if (sm > set) {
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;
   }
-  dim3 g((D.maxN + GRAM_CHUNK - 1) / GRAM_CHUNK, D.nprob);
+  // rows per block: enough blocks for ~3 per SM over the batch, at least GRAM_ROWS, at most N
+  long long rows_total = (long long)D.maxN * D.nprob;
+  int chunk = (int)std::min<long long>(D.maxN, std::max<long long>(GRAM_ROWS, rows_total / (152 * 3)));
+  chunk = (chunk + GRAM_ROWS - 1) / GRAM_ROWS * GRAM_ROWS;
+  dim3 g((D.maxN + chunk - 1) / chunk, D.nprob);
   note_launch();
-  k_gram<<<g, 256, sm, s>>>(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld);
+  k_gram<<<g, 256, sm, s>>>(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld, chunk);
 }
 
 void launch_apply(const Dev& D, int xbuf, int xw, int outw, long long m_off, int m_double, int zbuf, int outbuf,
                   int norm_only, cudaStream_t s) {
   static size_t set = 0;
-  size_t sm = sizeof(float2) * ((size_t)D.L.LDR * D.L.LDR + (size_t)D.L.LDR * APPLY_ROWS);
+  const int rows = D.L.LDR <= 64 ? 128 : 64;
+  const size_t sm = sizeof(float2) * ((size_t)D.L.LDR * ((D.L.LDR + 3) & ~3) + (size_t)D.L.LDR * rows);
   if (sm > set) {
     cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;
   }
-  dim3 g((D.maxN + APPLY_ROWS - 1) / APPLY_ROWS, D.nprob);
+  dim3 g((D.maxN + rows - 1) / rows, D.nprob);
   note_launch();
-  k_apply<<<g, 256, sm, s>>>(D, xbuf, xw, outw, m_off, m_double, zbuf, outbuf, norm_only);
+  k_apply<<<g, 256, sm, s>>>(D, xbuf, xw, outw, m_off, m_double, zbuf, outbuf, norm_only, rows);
 }
 
 void launch_argmax(const Dev& D, int buf, cudaStream_t s) {

@@ -624,7 +624,9 @@ long long tc_prob_stride(int kind, int ntbox, int maxnc) { return (long long)max
 
 void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, long long prob_stride, cudaStream_t s) {
   note_launch();
-  dim3 g(std::max(1, std::min(((D.maxN + 31) / 32) * 4, 1024)), D.nprob);
+  // items (chunk, row, 16-byte group) of the largest problem, about four per thread
+  const long long items = (long long)((D.maxN + 31) / 32) * (2 * D.maxR0 + 16) * 16;
+  dim3 g((unsigned)std::max<long long>(1, std::min<long long>(1024, (items + 1023) / 1024)), D.nprob);
   unsigned char* b = (unsigned char*)xb;
   switch (kind) {
     case PRONY_BF16X3: k_xb_prep<PRONY_BF16X3><<<g, 256, 0, s>>>(D, xbuf, wsel, b, prob_stride); break;
