@@ -258,6 +258,27 @@ def solve_c(t: np.ndarray, f: np.ndarray, n: int) -> np.ndarray:
     return c
 
 
+def vandermonde_z(z: np.ndarray, n: int) -> np.ndarray:
+    """A with columns built from the raw eigenvalues z_j(l) instead of exp(-2 pi i t_j(l)):
+    A[j, k] = prod_l z_j(l)^{k_l}, k in I_n (powers by repeated multiplication, no logarithm)."""
+    m, d = z.shape
+    K = index_set(n, d)
+    A = np.ones((m, len(K)), dtype=np.complex128)
+    for l in range(d):
+        powers = np.ones((m, n + 1), dtype=np.complex128)
+        for x in range(1, n + 1):
+            powers[:, x] = powers[:, x - 1] * z[:, l]
+        A *= powers[:, K[:, l]]
+    return A
+
+
+def solve_c_z(z: np.ndarray, f: np.ndarray, n: int) -> np.ndarray:
+    """argmin_c ||A^T c - f||_2 with A from the raw z_j (Section 4 reading: the perturbation
+    analysis builds A from the computed z~, not from unit-modulus exp(-2 pi i t~))."""
+    c, *_ = np.linalg.lstsq(vandermonde_z(z, n).T, f, rcond=None)
+    return c
+
+
 def ls_residual(t, c, f, n) -> float:
     """||A^T c - f||_2 / ||f||_2 (Section 5: operational accuracy estimate)."""
     nf = np.linalg.norm(f)
@@ -279,13 +300,15 @@ def power_start_blocks(seed: int, N: int, r0: int):
 def prony(grid: np.ndarray, d: int, n: int, m: int, *, svd: str = "full", seed: int = 1,
           oversample_p: int | None = None, tol_rank: float | None = None,
           tol_power: float | None = None, max_iter: int = 50, detect_rank: bool = False,
-          return_internals: bool = False):
+          return_internals: bool = False, vandermonde_from: str = "t"):
     """Algorithm 1 (multivariate matrix-pencil Prony), FP64, explicit matrices.
 
     svd = "full": LAPACK gesvd of T, keep the leading m (Section 5 reference variant);
     svd = "power": Algorithm 3 with r0 = m + p (p = m by default: starting width 2m, Section 5).
     Rank: reported with the paper's criterion (tol_rank default N eps_M); with detect_rank the
-    detected rank replaces m.  Output sorted lexicographically by t."""
+    detected rank replaces m.  vandermonde_from = "t" builds A of the least-squares problem from
+    t (unit modulus, Eq. ls_probl); "z" from the raw eigenvalues z~ (Section 4 reading).  Output
+    sorted lexicographically by t."""
     if grid.shape != (2 * n + 2,) * d:
         raise ValueError("grid must have shape (2n+2,)*d")
     N = (n + 1) ** d
@@ -314,8 +337,13 @@ def prony(grid: np.ndarray, d: int, n: int, m: int, *, svd: str = "full", seed: 
     mu = philox.draw_mu(seed, d)
     W, z = joint_diagonalize(S, mu)
     t = t_from_z(z)
-    c = solve_c(t, f, n)
-    info["ls_resid"] = ls_residual(t, c, f, n)
+    if vandermonde_from == "z":
+        c = solve_c_z(z, f, n)
+        nf = np.linalg.norm(f)
+        info["ls_resid"] = float(np.linalg.norm(vandermonde_z(z, n).T @ c - f) / nf) if nf else 0.0
+    else:
+        c = solve_c(t, f, n)
+        info["ls_resid"] = ls_residual(t, c, f, n)
     t, c = sort_by_t(t, c)
     if return_internals:
         info.update(U=U, s=s, V=V, S=S, W=W, z=z, mu=mu, T=T, f=f)

@@ -329,6 +329,30 @@ def test_refine_least_squares_recovers_truth_and_is_stationary():
     assert L < loss(P.t, P.c) and L < loss(t0, c0)
 
 
+def test_raw_z_vandermonde():
+    """Section 4 reading (A from the raw eigenvalues z~): on noise-free data every |z_j(l)| = 1
+    and z_j(l) = exp(-2 pi i t_j(l)), so both least-squares problems coincide and recover c
+    exactly; the raw-z matrix equals the t matrix built from the same nodes; under noise the two
+    variants differ (|z~| != 1), each a least-squares solution of its own A."""
+    P = _problem(2, 9, 4, 151)
+    t_t, c_t, _ = O.prony(P.grid, 2, 9, 4)
+    t_z, c_z, info = O.prony(P.grid, 2, 9, 4, vandermonde_from="z", return_internals=True)
+    assert np.allclose(t_t, t_z, atol=1e-12) and np.allclose(c_t, c_z, atol=1e-10)
+    order = np.lexsort(P.t.T[::-1])
+    assert np.allclose(c_z, P.c[order], atol=1e-9)
+    z = np.exp(-2j * np.pi * P.t)
+    assert np.allclose(O.vandermonde_z(z, 9), O.vandermonde(P.t, 9), atol=1e-12)
+    Pn = _problem(2, 9, 4, 152, snr_db=20.0)
+    _, cz, iz = O.prony(Pn.grid, 2, 9, 4, vandermonde_from="z", return_internals=True)
+    _, ct, _ = O.prony(Pn.grid, 2, 9, 4)
+    assert np.max(np.abs(np.abs(iz["z"]) - 1)) > 1e-6 and not np.allclose(cz, ct, atol=1e-9)
+    f = O.data_vector(Pn.grid, 9, 2)
+    A = O.vandermonde_z(iz["z"], 9)
+    c0, *_ = np.linalg.lstsq(A.T, f, rcond=None)          # normal-equation optimality of c
+    # (cz is sorted by t; compare as sets through the residual norm)
+    assert abs(np.linalg.norm(A.T @ c0 - f) - np.sqrt(iz["ls_resid"] ** 2) * np.linalg.norm(f)) < 1e-9 * np.linalg.norm(f)
+
+
 # --------------------------------------------------------------------- planted mistakes
 @pytest.mark.parametrize("mistake", ["t_sign", "shift_sign", "transpose_T", "drop_sigma"])
 def test_pins_catch_planted_mistakes(monkeypatch, mistake):
