@@ -86,6 +86,12 @@ def roofline(prec, achieved, traffic, launches, stats, total_ms) -> dict:
                 "peak_source": (f"BF16 dense {pk['bf16']:.0f} TFLOP/s {pk['src']} / {SPLIT_PRODUCTS[prec]}"
                                 + (" (3 TF32 products at half the BF16 rate)" if prec == "tf32x3" else " split products")),
                 "tensor_pipe_frac": achieved * SPLIT_PRODUCTS[prec] / pk["bf16"], **common}
+    if prec == "fft32":
+        return {"bound": "alu", "kernel": "k_toeplitz_fft (FP32 FFTs in shared memory)", "peak": FP32_PEAK_TFLOPS,
+                "frac": achieved / FP32_PEAK_TFLOPS, "flops_counted": "5 L log2 L per transformed line (pruned), "
+                "forward + inverse, + 6 per point for the spectral product",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (no measured FP32 peak)",
+                **common}
     return {"bound": "alu", "kernel": "k_toeplitz_simt (FP32 FFMA)", "peak": FP32_PEAK_TFLOPS,
             "frac": achieved / FP32_PEAK_TFLOPS,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (no measured FP32 peak)", **common}
@@ -100,6 +106,8 @@ def parse():
     ap.add_argument("--config", default="C2", choices=["C1", "C2", "C3", "C4", "C5"])
     ap.add_argument("--batch", type=int, default=None, help="problems per GPU (default 152; C4: 4096)")
     ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--svd", default="power", choices=["power", "lanczos"],
+                    help="subspace step: block power method (Algorithm 3) or Lanczos start (Algorithm 2)")
     ap.add_argument("--oracle-sample", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -349,7 +357,7 @@ def main():
     dev = host.cuda()
     t_dev = torch.zeros(total_terms * dmax, dtype=torch.float64, device="cuda")
     c_dev = torch.zeros(total_terms, dtype=torch.complex128, device="cuda")
-    opts = default_opts(precision=args.precision)
+    opts = default_opts(precision=args.precision, svd_method=1 if args.svd == "lanczos" else 0)
     ctx = Context(local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -367,7 +375,7 @@ def main():
     errs = []
     for i, P in enumerate(problems):
         o = int(ooff[i])
-        errs.append(W.match_to_truth(t_all[o * P.d:(o + P.m) * P.d].reshape(P.m, P.d), c_all[o:o + P.m],
+        errs.append(W.match_to_truth(t_all[o * dmax:(o + P.m) * dmax].reshape(P.m, dmax)[:, :P.d], c_all[o:o + P.m],
                                      P.t, P.c))
     # oracle sample: CPU baseline and gate thresholds (rank 0)
     cpu = None
@@ -454,6 +462,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD[args.config], "batch_per_gpu": B, "precision_small_steps": "f64",
+                   "subspace": "Lanczos start (Algorithm 2) + block power" if args.svd == "lanczos"
+                   else "block power (Algorithm 3)",
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "parallelism": f"independent problems, {ws} GPU(s), no collective",
                    "passed_gate": f"{passed}/{B} on rank 0",

@@ -55,8 +55,12 @@ typedef enum {
  *                  products (tcgen05.mma kind::f16), FP32 accumulation.
  *   PRONY_TF32X3 : FP32 operands split into TF32 hi+lo, three tensor-core
  *                  products (tcgen05.mma kind::tf32), FP32 accumulation.
- *   PRONY_BF16X2 : BF16 hi+lo split, three tensor-core products. */
-typedef enum { PRONY_FP32 = 0, PRONY_BF16X3 = 1, PRONY_TF32X3 = 2, PRONY_BF16X2 = 3 } prony_precision;
+ *   PRONY_BF16X2 : BF16 hi+lo split, three tensor-core products.
+ *   PRONY_FFT32  : no dense product: T embedded in a circulant of L^d points (L the power of
+ *                  two >= 2n+2), FP32 FFTs in shared memory, O(L^d log L) per column instead
+ *                  of O(N^2).  Needs L^(d-1) (L+1) <= 128 * 129 for every problem of the call
+ *                  (d = 1: n <= 8191; d = 2: n <= 63; d = 3: n <= 7), else PRONY_EINVAL. */
+typedef enum { PRONY_FP32 = 0, PRONY_BF16X3 = 1, PRONY_TF32X3 = 2, PRONY_BF16X2 = 3, PRONY_FFT32 = 4 } prony_precision;
 
 typedef struct {
   int precision;            /* prony_precision */
@@ -66,6 +70,13 @@ typedef struct {
   int max_iter;             /* cap on power iterations; <= 0: default 30 */
   unsigned long long seed;  /* Philox4x64-10 key for mu, V_0 */
   int rank_mode;            /* 0: use the given m (rank detected and reported); 1: use the detected rank */
+  int vandermonde;          /* matrix of the least-squares problem for c (Eq. ls_probl): 0 from t
+                               (unit modulus, default); 1 from the raw eigenvalues z~ (the matrix
+                               the Section 4 perturbation analysis works with) */
+  int svd_method;           /* subspace of T: 0 block power method (Algorithm 3, default);
+                               1 Lanczos bidiagonalisation with full reorthogonalisation
+                               (Algorithm 2) up to the rank it reveals, then the block power
+                               iteration from its right vectors with the pivoted-QR rank step */
 } prony_opts;
 
 typedef struct {
@@ -77,6 +88,7 @@ typedef struct {
   double ls_resid;          /* ||A^T c - f||_2 / ||f||_2 (Section 5 accuracy estimate) */
   double sigma_ratio;       /* sigma_m / sigma_1 */
   double normT;             /* ||T||_F (closed form from the grid) */
+  int lanczos_steps;        /* left vectors u accepted by Algorithm 2 (svd_method 1), else 0 */
 } prony_info;
 
 /* Fill *opts with defaults: PRONY_BF16X3, p = m, tolerances and cap as documented above. */
@@ -111,9 +123,10 @@ int prony_build_S(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m
 int prony_eval(prony_ctx* ctx, const double* t, const prony_c128* c, int m, int d,
                const int* k, int K, prony_c128* f_out);
 
-/* Many independent problems of uneven (d, n, m) (same d for all in this version).
+/* Many independent problems of uneven (d, n, m).
  * sample_off[p]: offset (in prony_c128) of problem p's grid inside `samples`;
- * out_off[p]: offset (in terms) of its results: t_out[(out_off[p]+j)*d + l],
+ * out_off[p]: offset (in terms) of its results: t_out[(out_off[p]+j)*dmax + l] for
+ * l < d[p] (dmax = the largest d of the call; entries l >= d[p] are left untouched),
  * c_out[out_off[p]+j].  infos[P] nullable.  Returns the worst status. */
 int prony_solve_batched(prony_ctx* ctx, int P, const int* d, const int* n, const int* m,
                         const long long* sample_off, const prony_c128* samples,

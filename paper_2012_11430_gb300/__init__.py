@@ -7,4 +7,4 @@ exponential-sum kernels in a torch.autograd.Function for least-squares refinemen
 """
 from .binding import (Context, PronyError, PronyInfo, PronyOpts, default_opts, load,  # noqa: F401
                       PRONY_OK, PRONY_EINVAL, PRONY_ERANK, PRONY_ENOCONV, PRONY_ENAN, PRONY_ECUDA, PRONY_ENOMEM,
-                      PRONY_FP32, PRONY_BF16X3, PRONY_TF32X3, PRONY_BF16X2, PRECISIONS)
+                      PRONY_FP32, PRONY_BF16X3, PRONY_TF32X3, PRONY_BF16X2, PRONY_FFT32, PRECISIONS)

@@ -16,8 +16,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libprony.so")
 
 PRONY_OK, PRONY_EINVAL, PRONY_ERANK, PRONY_ENOCONV, PRONY_ENAN, PRONY_ECUDA, PRONY_ENOMEM = 0, -1, -2, -3, -4, -5, -6
-PRONY_FP32, PRONY_BF16X3, PRONY_TF32X3, PRONY_BF16X2 = 0, 1, 2, 3
-PRECISIONS = {"fp32": PRONY_FP32, "bf16x3": PRONY_BF16X3, "tf32x3": PRONY_TF32X3, "bf16x2": PRONY_BF16X2}
+PRONY_FP32, PRONY_BF16X3, PRONY_TF32X3, PRONY_BF16X2, PRONY_FFT32 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": PRONY_FP32, "bf16x3": PRONY_BF16X3, "tf32x3": PRONY_TF32X3, "bf16x2": PRONY_BF16X2,
+              "fft32": PRONY_FFT32}
 
 EXPORTS = [
     "prony_default_opts", "prony_status_string", "prony_last_error", "prony_ctx_create", "prony_ctx_destroy",
@@ -39,13 +40,13 @@ class PronyStats(ctypes.Structure):
 class PronyOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("oversample_p", ctypes.c_int), ("tol_rank", ctypes.c_double),
                 ("tol_power", ctypes.c_double), ("max_iter", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-                ("rank_mode", ctypes.c_int)]
+                ("rank_mode", ctypes.c_int), ("vandermonde", ctypes.c_int), ("svd_method", ctypes.c_int)]
 
 
 class PronyInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("rank_detected", ctypes.c_int), ("rank_used", ctypes.c_int),
                 ("power_iters", ctypes.c_int), ("power_resid", ctypes.c_double), ("ls_resid", ctypes.c_double),
-                ("sigma_ratio", ctypes.c_double), ("normT", ctypes.c_double)]
+                ("sigma_ratio", ctypes.c_double), ("normT", ctypes.c_double), ("lanczos_steps", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -243,7 +244,7 @@ class Context:
         out = []
         for i in range(P):
             d, m, o = int(ds[i]), int(ms[i]), int(ooff[i])
-            out.append(SolveResult(t[o * d:(o + m) * d].reshape(m, d).copy(), c[o:o + m].copy(),
+            out.append(SolveResult(t[o * dmax:(o + m) * dmax].reshape(m, dmax)[:, :d].copy(), c[o:o + m].copy(),
                                    infos[i].as_dict()))
         return out, rc
 

@@ -15,6 +15,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// per-problem status codes (the values of prony_status in the public header)
+#define ST_OK 0
+#define ST_ERANK (-2)
+#define ST_ENOCONV (-3)
+#define ST_ENAN (-4)
+
 #define PRONY_RMAX 128        // max columns r0 = m + p
 #define PRONY_LM_PMAX 160     // max real parameters m (d + 2) of the refinement
 #define PRONY_MMAX 64         // max terms m
@@ -30,6 +36,8 @@ struct ProbDesc {
   long long ooff;             // offset (terms) of its results in the packed t / c outputs
   long long toff;             // offset (words) of its split-plane tables in tabF / tabH
   int Gd4;                    // Gd rounded up to a multiple of 4 (length of one table)
+  int fL;                     // FFT products: points per axis of the circulant embedding (0: dense)
+  long long foff;             // FFT products: offset (elements) of the problem's transform in fhat
 };
 
 // Per-problem iteration state, device resident.
@@ -48,6 +56,9 @@ struct ProbState {
   double resid2_prev;
   double ls_num2;             // ||A^T c - f||^2
   double sigma_ratio;
+  int lk;                     // Lanczos (Algorithm 2): vectors u_1..u_lk accepted
+  int lstop;                  // Lanczos: why it stopped (1 alpha, 2 beta below the tolerance, 3 block full)
+  double lalpha, lbeta;       // Lanczos: last alpha, beta
 };
 
 // Small per-problem workspace: byte offsets inside the block at ProbDesc::soff.
@@ -68,6 +79,7 @@ struct SmallLay {
   long long phase;   // LDM double2
   long long argmx;   // LDM u64
   long long work1, work2, work3, work4;   // LDR x LDM double2 scratch of the FP64 steps
+  long long zraw;    // LDM x DMAX double2  eigenvalues z_j(l) of the S_l
   long long bytes;
 };
 
@@ -94,6 +106,7 @@ inline SmallLay make_small_lay(int LDR, int LDM, int dmax) {
   L.work2 = take(16LL * LDR * LDM);
   L.work3 = take(16LL * LDR * LDM);
   L.work4 = take(16LL * LDR * LDM);
+  L.zraw = take(16LL * LDM * PRONY_DMAX);
   L.bytes = (o + 255) / 256 * 256;
   return L;
 }
@@ -119,6 +132,11 @@ struct Dev {
   float2* Y;
   char* small;
   SmallLay L;
+  int vand;          // least-squares matrix from t (0) or from the raw z (1)
+  // FFT products: transforms of the embedded samples (scrambled order) and exp(-2 pi i j / fLT)
+  float2* fhat;
+  float2* ftw;
+  int fLT;
 };
 
 // ----------------------------------------------------------------------------- complex helpers
@@ -228,7 +246,22 @@ void note_launch();
 // Message returned by prony_last_error() on this host thread.
 void set_last_error(const char* msg);
 
-enum WidthSel { W_R0 = 0, W_U = 1, W_V = 2, W_M = 3, W_IN = 4, W_OUT = 5 };
+// Column counts of the tall blocks, selected per problem: r0, the current U / V widths, m, the
+// pending X -> X M product, a single column, and the Lanczos basis sizes k and k + 1.
+enum WidthSel { W_R0 = 0, W_U = 1, W_V = 2, W_M = 3, W_IN = 4, W_OUT = 5, W_ONE = 6, W_LK = 7, W_LK1 = 8 };
+__host__ __device__ inline int sel_width(const ProbState& s, const ProbDesc& p, int sel) {
+  switch (sel) {
+    case W_R0: return p.r0;
+    case W_U: return s.wu;
+    case W_V: return s.wv;
+    case W_M: return p.m;
+    case W_IN: return s.w_in;
+    case W_OUT: return s.w_out;
+    case W_ONE: return 1;
+    case W_LK: return s.lk;
+    default: return s.lk + 1;
+  }
+}
 enum BufSel { BUF_V = 0, BUF_U = 1, BUF_B1 = 2, BUF_B2 = 3, BUF_Y = 4 };
 
 // kernels_tall.cu
@@ -238,7 +271,7 @@ void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_
 // out[a][b] (+)= sum_{r in I_n} conj(X[map(r), a]) Z[map(r), b]; X, Z buffers with row shifts
 void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
                  long long out_off, int out_ld, cudaStream_t s);
-// OUT[r, j] = sum_a X[r, a] M[a][j] - (zbuf >= 0 ? Z[r, j] : 0) for r in I_n; M in the small workspace
+// OUT[r, j] = (zbuf >= 0 ? Z[r, j] : 0) - sum_a X[r, a] M[a][j] for r in I_n (without Z: + the sum); M in the small workspace
 // (float2 at mapm, ld RMAX) or double2 (m_double, at m_off with ld MMAX).  norm_only: accumulate
 // ||OUT||^2 into st.resid2 and do not store.
 void launch_apply(const Dev& D, int xbuf, int xw, int outw, long long m_off, int m_double, int zbuf,
@@ -281,6 +314,21 @@ cudaError_t lm_set_attributes(int m, int d);
 void launch_refine_lm(double* t, double2* c, int m, int d, const int* lo, const int* len, long long K,
                       const float2* y, int iters, double lambda0, double* hist, void* ws, cudaStream_t s);
 constexpr int LM_LAUNCHES_PER_STEP = 4;
+
+// kernels_lanczos.cu (Algorithm 2, batched)
+// kernels_fft.cu (Toeplitz products by circulant embedding and FP32 FFTs)
+int fft_length(int n);
+long long fft_points_host(int n, int d);   // points of one embedded grid in shared memory (padded)
+void launch_fft_tables(const Dev& D, int maxpts, cudaStream_t s);
+void launch_toeplitz_fft(const Dev& D, int maxpts, int maxw, int adjoint, int xbuf, int wsel, int ybuf, int y_ext,
+                         cudaStream_t s);
+
+void launch_lz_start(const Dev& D, cudaStream_t s);
+void launch_lz_load(const Dev& D, int which, cudaStream_t s);
+void launch_lz_axpy(const Dev& D, int which, cudaStream_t s);
+void launch_lz_accept(const Dev& D, int which, double tol_rel, int cap, cudaStream_t s);
+void launch_lz_finish(const Dev& D, cudaStream_t s);
+void launch_lz_all_done(const Dev& D, int* flag, cudaStream_t s);
 
 // kernels_small.cu
 enum QrMode { QR_PLAIN = 0, QR_DROP = 1, QR_RANK = 2 };

@@ -18,9 +18,6 @@
 
 #include <algorithm>
 
-#define ST_OK 0
-#define ST_ENOCONV (-3)
-#define ST_ENAN (-4)
 
 namespace {
 
@@ -615,6 +612,7 @@ __global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
       double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
       for (int a = 0; a < m; ++a) acc[a & 3] = cadd(acc[a & 3], cmul(Xd[j * LM + a], Cd[a * LM + j]));
       double2 z = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+      ((double2*)(sb + D.L.zraw))[j * PRONY_DMAX + l] = z;
       double tj = -atan2(z.y, z.x) / 6.283185307179586;
       tj -= floor(tj);
       if (tj >= 1.0) tj = 0.0;

@@ -1,0 +1,327 @@
+// Toeplitz products by circulant embedding and FFTs (FP32), an alternative to the dense
+// products for grids that fit one CTA's shared memory.
+//
+// T = [f(k - h)] with k in {0..n+1}^d (or I_n) and h in I_n = {0..n}^d only ever meets the
+// differences k - h in {-n..n+1}^d, the sample grid of Section 1.  Embedded periodically in a
+// grid of L >= 2n+2 points per axis (L a power of two), f becomes the kernel of an L^d circular
+// convolution whose outputs at k coincide with (T x)_k: no difference wraps onto another one.
+// So T x = IDFT(DFT(f_emb) * DFT(x_emb)) restricted to the rows, and T^* x uses conj(DFT(f_emb))
+// (the embedding of conj f(-u) has the conjugate transform).
+//
+// The transforms are mixed-radix Cooley-Tukey in shared memory: the forward pass is a
+// decimation in frequency that leaves its output in digit-reversed order, the inverse pass runs
+// the same stages backwards from that order, so no reordering is ever done; DFT(f_emb) is stored
+// in the same scrambled order by the same forward pass.  Each stage gives a thread R = 2..16
+// points, transformed in registers by a radix-2 network with constant twiddles.  Pruning: the
+// forward pass transforms only the lines that can hold nonzeros (x lives on {0..n}^d), and the
+// inverse pass only the lines that reach the output rows.  Layout in shared memory: row-major
+// over the axes with the last axis padded to P = L + 1 points (d >= 2), so that the threads of a
+// warp, which take consecutive lines, hit distinct banks along every axis.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace {
+
+// exp(-2 pi i e / 16) for e = 0..7 (conjugated for the inverse)
+constexpr float kC1 = 0.92387953251128674f;   // cos(pi/8)
+constexpr float kS1 = 0.38268343236508978f;   // sin(pi/8)
+constexpr float kH = 0.70710678118654752f;    // sqrt(1/2)
+
+template <bool INV>
+__device__ __forceinline__ float2 rot16(float2 t, int e) {
+  float c, s;   // w = c - i s (forward)
+  switch (e) {
+    case 0: return t;
+    case 4: return INV ? make_float2(-t.y, t.x) : make_float2(t.y, -t.x);
+    case 1: c = kC1; s = kS1; break;
+    case 2: c = kH; s = kH; break;
+    case 3: c = kS1; s = kC1; break;
+    case 5: c = -kS1; s = kC1; break;
+    case 6: c = -kH; s = kH; break;
+    default: c = -kC1; s = kS1; break;
+  }
+  if (INV) s = -s;
+  return make_float2(t.x * c + t.y * s, t.y * c - t.x * s);
+}
+
+__host__ __device__ constexpr int bitrev(int k, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((k >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+template <int R>
+struct Log2 { static constexpr int v = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4; };
+
+// In-register DFT of R points by a radix-2 decimation-in-frequency network; the result of
+// frequency k lands in x[bitrev(k)].
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
+#pragma unroll
+  for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+    for (int s0 = 0; s0 < R; s0 += 2 * span) {
+#pragma unroll
+      for (int i = 0; i < span; ++i) {
+        const float2 a = x[s0 + i], b = x[s0 + i + span];
+        x[s0 + i] = make_float2(a.x + b.x, a.y + b.y);
+        x[s0 + i + span] = rot16<INV>(make_float2(a.x - b.x, a.y - b.y), i * (8 / span));
+      }
+    }
+  }
+}
+
+// The line set of one axis: nl lines of L points at element stride es.  A line is fixed by its
+// coordinates on the other axes (no = d - 1 of them, slowest first, extents ext, strides str):
+// those before the transformed axis run below E (pruning), those after it over [0, L).
+struct Lines {
+  int nl, es, no;
+  int ext[2], str[2];
+  __device__ int base(int li) const {
+    if (no == 0) return 0;
+    if (no == 1) return li * str[0];
+    const int f = li % ext[1], sl = li / ext[1];
+    return sl * str[0] + f * str[1];
+  }
+};
+
+// stride of axis m in the padded layout
+__device__ inline int axis_stride(int L, int P, int d, int m) {
+  if (m == d - 1) return 1;
+  int s = P;
+  for (int l = m + 1; l < d - 1; ++l) s *= L;
+  return s;
+}
+
+// One stage (sub-blocks of M points, stride S = M / R) over every line of the set.
+template <int R, bool INV>
+__device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2* __restrict__ tw, int LT) {
+  constexpr int B = Log2<R>::v;
+  const int per_line = L / R, S = M / R;
+  const int items = ls.nl * per_line;
+  const bool lines_fast = ls.no > 0;
+  const int tws = LT / M;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    int line, bj;
+    if (lines_fast) {
+      line = it % ls.nl;
+      bj = it / ls.nl;
+    } else {
+      line = it / per_line;
+      bj = it % per_line;
+    }
+    const int b = bj / S, j = bj - b * S;
+    float2* p = a + ls.base(line) + (b * M + j) * ls.es;
+    const int step = S * ls.es;
+    float2 x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = p[q * step];
+    if (!INV) {
+      dft_reg<R, false>(x);
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        float2 y = x[bitrev(k, B)];
+        if (k > 0 && j > 0) y = cmulf(y, __ldg(&tw[((j * k) & (M - 1)) * tws]));
+        p[k * step] = y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 1; k < R; ++k) {
+        if (j > 0) {
+          const float2 w = __ldg(&tw[((j * k) & (M - 1)) * tws]);
+          x[k] = cmulf(x[k], make_float2(w.x, -w.y));
+        }
+      }
+      dft_reg<R, true>(x);
+#pragma unroll
+      for (int q = 0; q < R; ++q) p[q * step] = x[bitrev(q, B)];
+    }
+  }
+}
+
+__device__ inline int stage_radix(int M) { return M >= 16 ? 16 : M; }
+
+template <bool INV>
+__device__ void fft_stage_any(float2* a, const Lines& ls, int L, int M, const float2* tw, int LT) {
+  switch (stage_radix(M)) {
+    case 16: fft_stage<16, INV>(a, ls, L, M, tw, LT); break;
+    case 8: fft_stage<8, INV>(a, ls, L, M, tw, LT); break;
+    case 4: fft_stage<4, INV>(a, ls, L, M, tw, LT); break;
+    default: fft_stage<2, INV>(a, ls, L, M, tw, LT); break;
+  }
+}
+
+__device__ inline Lines axis_lines(int L, int P, int d, int axis, int E) {
+  Lines ls;
+  ls.es = axis_stride(L, P, d, axis);
+  ls.no = 0;
+  ls.nl = 1;
+  for (int m = 0; m < d; ++m) {
+    if (m == axis) continue;
+    const int e = m < axis ? E : L;
+    ls.ext[ls.no] = e;
+    ls.str[ls.no] = axis_stride(L, P, d, m);
+    ls.nl *= e;
+    ++ls.no;
+  }
+  return ls;
+}
+
+// Forward transform along every axis, last axis first; lines whose coordinates on the axes not
+// yet transformed exceed E - 1 are zero and skipped.
+__device__ void fft_forward(float2* a, int L, int P, int d, int E, const float2* tw, int LT) {
+  for (int axis = d - 1; axis >= 0; --axis) {
+    const Lines ls = axis_lines(L, P, d, axis, E);
+    for (int M = L; M > 1; M /= stage_radix(M)) {
+      fft_stage_any<false>(a, ls, L, M, tw, LT);
+      __syncthreads();
+    }
+  }
+}
+
+// Inverse of fft_forward (unscaled), first axis first; only lines whose coordinates on the axes
+// already back in the sample domain are below E are computed.
+__device__ void fft_inverse(float2* a, int L, int P, int d, int E, const float2* tw, int LT) {
+  for (int axis = 0; axis < d; ++axis) {
+    const Lines ls = axis_lines(L, P, d, axis, E);
+    int Ms[16], ns = 0;
+    for (int M = L; M > 1; M /= stage_radix(M)) Ms[ns++] = M;
+    for (int s = ns - 1; s >= 0; --s) {
+      fft_stage_any<true>(a, ls, L, Ms[s], tw, LT);
+      __syncthreads();
+    }
+  }
+}
+
+// position of row r of a box with `base` points per axis (row-major) in the padded layout
+__device__ inline int grid_index(int r, int base, int d, int L, int P) {
+  int g = 0, rem = r;
+  for (int l = d - 1; l >= 0; --l) {
+    const int k = rem % base;
+    rem /= base;
+    g += k * axis_stride(L, P, d, l);
+  }
+  return g;
+}
+
+__device__ inline int fft_pitch(const ProbDesc& p) { return p.d >= 2 ? p.fL + 1 : p.fL; }
+__device__ inline int fft_points(const ProbDesc& p) {
+  int v = fft_pitch(p);
+  for (int l = 1; l < p.d; ++l) v *= p.fL;
+  return v;
+}
+
+__global__ void k_fft_twiddles(float2* tw, int LT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= LT) return;
+  double s, c;
+  sincospi(2.0 * i / LT, &s, &c);
+  tw[i] = make_float2((float)c, (float)-s);
+}
+
+// DFT of the embedded samples of every problem, in the scrambled order of fft_forward.
+__global__ void __launch_bounds__(512) k_fft_table(Dev D) {
+  extern __shared__ float2 a[];
+  const ProbDesc& p = D.P[blockIdx.x];
+  const int L = p.fL, d = p.d, P = fft_pitch(p), npts = fft_points(p);
+  for (int i = threadIdx.x; i < npts; i += blockDim.x) a[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = threadIdx.x; i < p.Gd; i += blockDim.x) {
+    int rem = i, g = 0;
+    for (int l = d - 1; l >= 0; --l) {
+      const int x = rem % p.G - p.n;          // coordinate in {-n..n+1}
+      rem /= p.G;
+      g += ((x + L) & (L - 1)) * axis_stride(L, P, d, l);
+    }
+    a[g] = D.gF[p.grid + i];
+  }
+  __syncthreads();
+  fft_forward(a, L, P, d, L, D.ftw, D.fLT);
+  for (int i = threadIdx.x; i < npts; i += blockDim.x) D.fhat[p.foff + i] = a[i];
+}
+
+__device__ inline float2* fbuf(const Dev& D, int buf, const ProbDesc& p, int& ld) {
+  switch (buf) {
+    case BUF_V: ld = p.N; return D.V + p.xoff;
+    case BUF_U: ld = p.N; return D.U + p.xoff;
+    case BUF_B1: ld = p.N; return D.B1 + p.xoff;
+    case BUF_B2: ld = p.N; return D.B2 + p.xoff;
+    default: ld = p.Next; return D.Y + p.yoff;
+  }
+}
+
+// One column of one problem per CTA: Y[:, col] = T X[:, col] (rows {0..n+1}^d when y_ext, else
+// I_n) or T^* X[:, col] (adjoint, rows I_n).
+__global__ void __launch_bounds__(512) k_toeplitz_fft(Dev D, int adjoint, int xbuf, int wsel, int ybuf, int y_ext) {
+  extern __shared__ float2 a[];
+  const ProbDesc& p = D.P[blockIdx.y];
+  const ProbState& st = D.st[blockIdx.y];
+  if (st.done) return;
+  const int col = blockIdx.x;
+  if (col >= sel_width(st, p, wsel)) return;
+  const int L = p.fL, d = p.d, n = p.n, P = fft_pitch(p), npts = fft_points(p);
+  int Ld = 1;
+  for (int l = 0; l < d; ++l) Ld *= L;
+  int ldx, ldy;
+  const float2* X = fbuf(D, xbuf, p, ldx) + (long long)col * ldx;
+  float2* Y = fbuf(D, ybuf, p, ldy) + (long long)col * ldy;
+  for (int i = threadIdx.x; i < npts; i += blockDim.x) a[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int r = threadIdx.x; r < p.N; r += blockDim.x) a[grid_index(r, n + 1, d, L, P)] = X[r];
+  __syncthreads();
+  fft_forward(a, L, P, d, n + 1, D.ftw, D.fLT);
+  const float2* F = D.fhat + p.foff;
+  for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+    const float2 f = __ldg(&F[i]);
+    a[i] = cmulf(a[i], adjoint ? make_float2(f.x, -f.y) : f);
+  }
+  __syncthreads();
+  const int K = y_ext ? n + 2 : n + 1;
+  fft_inverse(a, L, P, d, K, D.ftw, D.fLT);
+  const float scale = 1.0f / (float)Ld;
+  int rows = 1;
+  for (int l = 0; l < d; ++l) rows *= K;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const float2 v = a[grid_index(r, K, d, L, P)];
+    Y[r] = make_float2(v.x * scale, v.y * scale);
+  }
+}
+
+int fft_threads(int maxpts) { return maxpts >= 8192 ? 512 : maxpts >= 2048 ? 256 : 128; }
+
+}  // namespace
+
+int fft_length(int n) {
+  int L = 2;
+  while (L < 2 * n + 2) L *= 2;
+  return L;
+}
+
+long long fft_points_host(int n, int d) {
+  const int L = fft_length(n);
+  long long v = d >= 2 ? L + 1 : L;
+  for (int l = 1; l < d; ++l) v *= L;
+  return v;
+}
+
+void launch_fft_tables(const Dev& D, int maxpts, cudaStream_t s) {
+  note_launch();
+  k_fft_twiddles<<<(D.fLT + 255) / 256, 256, 0, s>>>(D.ftw, D.fLT);
+  const size_t sm = sizeof(float2) * (size_t)maxpts;
+  cudaFuncSetAttribute(k_fft_table, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  note_launch();
+  k_fft_table<<<D.nprob, fft_threads(maxpts), sm, s>>>(D);
+}
+
+void launch_toeplitz_fft(const Dev& D, int maxpts, int maxw, int adjoint, int xbuf, int wsel, int ybuf, int y_ext,
+                         cudaStream_t s) {
+  const size_t sm = sizeof(float2) * (size_t)maxpts;
+  static size_t set = 0;
+  if (sm > set) {
+    cudaFuncSetAttribute(k_toeplitz_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    set = sm;
+  }
+  note_launch();
+  k_toeplitz_fft<<<dim3(maxw, D.nprob), fft_threads(maxpts), sm, s>>>(D, adjoint, xbuf, wsel, ybuf, y_ext);
+}

@@ -10,23 +10,10 @@
 #include "common.cuh"
 #include <algorithm>
 
-#define ST_OK 0
-#define ST_ERANK (-2)
-#define ST_ENOCONV (-3)
-#define ST_ENAN (-4)
 
 namespace {
 
-__device__ inline int swidth(const ProbState& s, const ProbDesc& p, int sel) {
-  switch (sel) {
-    case W_R0: return p.r0;
-    case W_U: return s.wu;
-    case W_V: return s.wv;
-    case W_M: return p.m;
-    case W_IN: return s.w_in;
-    default: return s.w_out;
-  }
-}
+__device__ inline int swidth(const ProbState& s, const ProbDesc& p, int sel) { return sel_width(s, p, sel); }
 __device__ inline void set_width(ProbState& s, int sel, int w) {
   if (sel == W_U) s.wu = w;
   else if (sel == W_V) s.wv = w;
@@ -231,10 +218,25 @@ __global__ void __launch_bounds__(256) k_solve_c(Dev D) {
   for (int i = threadIdx.x; i < m; i += blockDim.x) bb[i] = b[i];
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
-  // G[i][j] = prod_l sum_{x=0}^{n} exp(2 pi i (t_i(l) - t_j(l)) x)
+  // G[i][j] = prod_l sum_{x=0}^{n} exp(2 pi i (t_i(l) - t_j(l)) x), or with the raw eigenvalues
+  // prod_l sum_x (conj(z_i(l)) z_j(l))^x (summed term by term: |q| need not be 1)
+  const double2* zr = (const double2*)(D.small + p.soff + D.L.zraw);
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     int i = idx / m, j = idx % m;
     double2 g = make_double2(1.0, 0.0);
+    if (D.vand) {
+      for (int l = 0; l < d; ++l) {
+        const double2 q = cmulc(zr[i * PRONY_DMAX + l], zr[j * PRONY_DMAX + l]);
+        double2 sum = make_double2(1.0, 0.0), pw = make_double2(1.0, 0.0);
+        for (int x = 1; x <= p.n; ++x) {
+          pw = cmul(pw, q);
+          sum = cadd(sum, pw);
+        }
+        g = cmul(g, sum);
+      }
+      G[i * LD + j] = g;
+      continue;
+    }
     for (int l = 0; l < d; ++l) {
       double dl = ts[i * PRONY_DMAX + l] - ts[j * PRONY_DMAX + l];
       dl -= rint(dl);
@@ -286,7 +288,11 @@ __global__ void __launch_bounds__(256) k_solve_c(Dev D) {
     if (s_bad) set_status(st, ST_ERANK);
   }
   __syncthreads();
-  // sort (t, c) lexicographically by t
+  // sort (t, c) lexicographically by t (and the raw eigenvalues with them)
+  __shared__ double2 zs[PRONY_MMAX * PRONY_DMAX];
+  double2* zw = (double2*)(D.small + p.soff + D.L.zraw);
+  for (int q = threadIdx.x; q < m * d; q += blockDim.x) zs[(q / d) * PRONY_DMAX + q % d] = zw[(q / d) * PRONY_DMAX + q % d];
+  __syncthreads();
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     int r = 0;
     for (int i = 0; i < m; ++i) {
@@ -298,7 +304,10 @@ __global__ void __launch_bounds__(256) k_solve_c(Dev D) {
       }
       if (less || (eq && i < j)) ++r;
     }
-    for (int l = 0; l < d; ++l) t[r * PRONY_DMAX + l] = ts[j * PRONY_DMAX + l];
+    for (int l = 0; l < d; ++l) {
+      t[r * PRONY_DMAX + l] = ts[j * PRONY_DMAX + l];
+      zw[r * PRONY_DMAX + l] = zs[j * PRONY_DMAX + l];
+    }
     cout[r] = cs_[j];
   }
   if (threadIdx.x == 0) st.ls_num2 = 0.0;

@@ -18,16 +18,7 @@ __device__ inline float2* buf_base(const Dev& D, int buf, const ProbDesc& p, int
   }
 }
 
-__device__ inline int width_of(const ProbState& s, const ProbDesc& p, int sel) {
-  switch (sel) {
-    case W_R0: return p.r0;
-    case W_U: return s.wu;
-    case W_V: return s.wv;
-    case W_M: return p.m;
-    case W_IN: return s.w_in;
-    default: return s.w_out;
-  }
-}
+__device__ inline int width_of(const ProbState& s, const ProbDesc& p, int sel) { return sel_width(s, p, sel); }
 
 // Row of buffer `buf` holding row r of I_n (Y is laid out over the box {0..n+1}^d).
 __device__ inline int buf_row(int buf, const ProbDesc& p, int r, int shift) {
@@ -135,14 +126,25 @@ __global__ void k_zero_small(Dev D, long long off, long long bytes) {
 // ----------------------------------------------------------------------------- tall-skinny Gram
 // out[a][b] += sum_r conj(X[r, a]) Z[r, b] over a block of `chunk` rows (chosen by the launcher
 // so that the batch gives a few blocks per SM: few blocks per problem means few FP64 atomics on
-// the same output entries).  Rows are staged in shared memory GRAM_ROWS at a time, transposed
-// (row-major, padded) so that threads reading neighbouring columns hit different banks.  Each
-// thread owns a 4x4 tile of (a, b); when there are fewer tiles than threads, threads split the
-// staged rows into row groups, whose partial sums are added by a tree in shared memory; when
-// there are more, the tiles are processed in batches of blockDim.x (every batch re-stages the
-// rows).  Each block adds its totals to the FP64 output with one atomic per entry.
-constexpr int GRAM_ROWS = 64;       // rows staged per pass
+// the same output entries).  Rows are staged in shared memory GRAM_ROWS at a time with
+// asynchronous copies into two alternating buffers (the next rows load while the current ones
+// are multiplied), transposed (row-major, padded) so that threads reading neighbouring columns
+// hit different banks.  Each thread owns a 4x4 tile of (a, b); when there are fewer tiles than
+// threads, threads split the staged rows into row groups, whose partial sums are added by a tree
+// in shared memory; when there are more, the tiles are processed in batches of blockDim.x
+// (every batch re-stages the rows).  Each block adds its totals to the FP64 output with one
+// atomic per entry.
+constexpr int GRAM_ROWS = 32;       // rows staged per pass (per buffer)
 constexpr int GRAM_T = 4;           // register tile (GRAM_T x GRAM_T complex accumulators)
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
                                               long long out_off, int out_ld, int chunk) {
@@ -157,9 +159,9 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
   const int r_end = min(p.N, r_begin + chunk);
   const int LR = D.L.LDR;
   const int lda = a + 1, ldb = b + 1;             // padded row strides of the staged rows
-  float2* Xs = smem;                              // [GRAM_ROWS][lda]
-  float2* Zs = smem + GRAM_ROWS * (LR + 1);       // [GRAM_ROWS][ldb]
-  float2* red = Zs + GRAM_ROWS * (LR + 1);        // [RG][per_batch][16] partial sums (aliased per batch)
+  const size_t buf_elems = (size_t)GRAM_ROWS * (LR + 1);
+  float2* stage = smem;                           // [2 buffers][X rows | Z rows]
+  float2* red = smem + 4 * buf_elems;             // [RG-1][per_batch][16] row-group partial sums
   int ldx, ldz;
   const float2* X = buf_base(D, xbuf, p, ldx);
   const float2* Z = buf_base(D, zbuf, p, ldz);
@@ -169,6 +171,25 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
   const int RG = max(1, min(8, nthr / per_batch));     // row groups (1 when tiles >= threads)
   const int nbatch = (ntile + per_batch - 1) / per_batch;
   double2* out = (double2*)(D.small + p.soff + out_off);
+  // asynchronous staging of rows r0 .. r0 + GRAM_ROWS - 1 into buffer k (zeros past r_end)
+  auto stage_rows = [&](int r0, int k) {
+    float2* Xs = stage + (size_t)k * 2 * buf_elems;
+    float2* Zs = Xs + buf_elems;
+    for (int idx = threadIdx.x; idx < (a + b) * GRAM_ROWS; idx += nthr) {
+      const int rr = idx % GRAM_ROWS, col = idx / GRAM_ROWS;
+      const int r = r0 + rr;
+      const bool ok = r < r_end;
+      if (col < a) {
+        const float2* src = X + (long long)col * ldx + (ok ? buf_row(xbuf, p, r, xshift) : 0);
+        cp_async8(Xs + rr * lda + col, src, ok ? 8 : 0);
+      } else {
+        const int cz = col - a;
+        const float2* src = Z + (long long)cz * ldz + (ok ? buf_row(zbuf, p, r, zshift) : 0);
+        cp_async8(Zs + rr * ldb + cz, src, ok ? 8 : 0);
+      }
+    }
+    cp_async_commit();
+  };
   for (int batch = 0; batch < nbatch; ++batch) {
     const int tile = batch * per_batch + threadIdx.x % per_batch, grp = threadIdx.x / per_batch;
     const bool active = grp < RG && tile < ntile;
@@ -178,19 +199,19 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
     for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
       for (int j = 0; j < GRAM_T; ++j) acc[i][j] = make_float2(0.f, 0.f);
-    for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS) {
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < (a + b) * GRAM_ROWS; idx += nthr) {
-        const int rr = idx % GRAM_ROWS, col = idx / GRAM_ROWS;
-        const int r = r0 + rr;
-        if (col < a) {
-          Xs[rr * lda + col] = r < r_end ? X[(long long)col * ldx + buf_row(xbuf, p, r, xshift)] : make_float2(0.f, 0.f);
-        } else {
-          const int cz = col - a;
-          Zs[rr * ldb + cz] = r < r_end ? Z[(long long)cz * ldz + buf_row(zbuf, p, r, zshift)] : make_float2(0.f, 0.f);
-        }
+    __syncthreads();                              // the buffers are free (previous batch done)
+    stage_rows(r_begin, 0);
+    int k = 0;
+    for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS, k ^= 1) {
+      if (r0 + GRAM_ROWS < r_end) {
+        stage_rows(r0 + GRAM_ROWS, k ^ 1);        // next rows load while these are multiplied
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
       __syncthreads();
+      const float2* Xs = stage + (size_t)k * 2 * buf_elems;
+      const float2* Zs = Xs + buf_elems;
       if (active) {
         for (int rr = grp; rr < GRAM_ROWS; rr += RG) {
           float2 xa[GRAM_T], zb[GRAM_T];
@@ -207,10 +228,10 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
             }
         }
       }
+      __syncthreads();                            // buffer k is overwritten two passes later
     }
     // row groups: partial sums meet in shared memory, group 0 adds them (fixed order)
     if (RG > 1) {
-      __syncthreads();
       if (active && grp > 0) {
         float2* dst = red + ((size_t)(grp - 1) * per_batch + (tile - batch * per_batch)) * 16;
 #pragma unroll
@@ -374,11 +395,20 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
   const double* t = (const double*)(D.small + p.soff + D.L.t);
   const double2* c = (const double2*)(D.small + p.soff + D.L.c);
   const double sign = resid ? -1.0 : 1.0;
+  const double2* zr = (const double2*)(D.small + p.soff + D.L.zraw);
   for (int q = threadIdx.x; q < p.d * m; q += blockDim.x) {
     int l = q / m, i = q % m;
-    double sn, cs;
-    sincospi(2.0 * t[i * PRONY_DMAX + l], &sn, &cs);
-    double2 e1 = make_double2(cs, sign * sn), e = make_double2(1.0, 0.0);
+    double2 e1;
+    if (D.vand) {
+      // raw eigenvalue z~ (Section 4 reading): conj(z) for the right-hand side, z for the model
+      const double2 z = zr[i * PRONY_DMAX + l];
+      e1 = make_double2(z.x, -sign * z.y);
+    } else {
+      double sn, cs;
+      sincospi(2.0 * t[i * PRONY_DMAX + l], &sn, &cs);
+      e1 = make_double2(cs, sign * sn);
+    }
+    double2 e = make_double2(1.0, 0.0);
     double2* row = tab + ((size_t)l * m + i) * n1;
     for (int x = 0; x < n1; ++x) {
       row[x] = e;
@@ -449,7 +479,7 @@ __global__ void k_gather_out(Dev D, double* t_out, double2* c_out) {
   const double2* c = (const double2*)(D.small + p.soff + D.L.c);
   for (int q = threadIdx.x; q < p.m * p.d; q += blockDim.x) {
     int j = q / p.d, l = q % p.d;
-    t_out[(p.ooff + j) * p.d + l] = j < s.rank_used ? t[j * PRONY_DMAX + l] : 0.0;
+    t_out[(p.ooff + j) * D.maxD + l] = j < s.rank_used ? t[j * PRONY_DMAX + l] : 0.0;
   }
   for (int j = threadIdx.x; j < p.m; j += blockDim.x)
     c_out[p.ooff + j] = j < s.rank_used ? c[j] : make_double2(0.0, 0.0);
@@ -586,9 +616,9 @@ void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_
 void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
                  int out_ld, cudaStream_t s) {
   static size_t set = 0;
-  // staged rows of X and Z, then the row-group partial sums: (RG - 1) x tiles x 16 entries with
+  // two buffers of staged rows of X and Z, then the row-group partial sums: (RG - 1) x tiles x 16 entries with
   // RG = min(8, 256 / tiles) when tiles <= 128, at most 224 x 16 (32 tiles, 8 groups)
-  const size_t sm = sizeof(float2) * (2 * (size_t)(D.L.LDR + 1) * GRAM_ROWS + (size_t)224 * 16);
+  const size_t sm = sizeof(float2) * (4 * (size_t)(D.L.LDR + 1) * GRAM_ROWS + (size_t)224 * 16);
   if (sm > set) {
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;

@@ -45,16 +45,7 @@ constexpr int TC_APROD = 8;                 // A' warps (two per TMEM lane quadr
 constexpr int TC_THREADS = 32 * (2 + TC_APROD);
 constexpr int TC_MAXCH = 512;               // K chunks per CTA (host splits K to stay below)
 
-__device__ inline int tc_width(const ProbState& s, const ProbDesc& p, int sel) {
-  switch (sel) {
-    case W_R0: return p.r0;
-    case W_U: return s.wu;
-    case W_V: return s.wv;
-    case W_M: return p.m;
-    case W_IN: return s.w_in;
-    default: return s.w_out;
-  }
-}
+__device__ inline int tc_width(const ProbState& s, const ProbDesc& p, int sel) { return sel_width(s, p, sel); }
 
 __device__ inline float2* tc_buf(const Dev& D, int buf, const ProbDesc& p, int& ld) {
   switch (buf) {

@@ -27,16 +27,7 @@ __device__ inline float2* tbuf(const Dev& D, int buf, const ProbDesc& p, int& ld
   }
 }
 
-__device__ inline int twidth(const ProbState& s, const ProbDesc& p, int sel) {
-  switch (sel) {
-    case W_R0: return p.r0;
-    case W_U: return s.wu;
-    case W_V: return s.wv;
-    case W_M: return p.m;
-    case W_IN: return s.w_in;
-    default: return s.w_out;
-  }
-}
+__device__ inline int twidth(const ProbState& s, const ProbDesc& p, int sel) { return sel_width(s, p, sel); }
 
 __global__ void k_zero_buf(Dev D, int buf, int wsel, int y_ext) {
   const ProbDesc& p = D.P[blockIdx.y];

@@ -67,6 +67,7 @@ struct prony_ctx {
   cudaStream_t stream = nullptr;
   DBuf grid64, gF, gH, V, U, B1, B2, Y, small, P, st, jobs, flag, tout, cout, misc, misc2, misc3;
   DBuf xb, tabF, tabH, tcjobs, tcerr;   // tensor-core path: B' planes, split sample tables, jobs, error flag
+  DBuf fhat, ftw;                       // FFT path: sample transforms, twiddles
   int* h_flag = nullptr;            // pinned
   std::vector<ProbState> h_st;
   // profiling of the Toeplitz launches
@@ -137,7 +138,13 @@ struct Batch {
   ToeplitzJob* jobs_in = nullptr;
   int maxw = 0;
   TcConf tc;
+  struct FftConf {
+    bool on = false;
+    int maxpts = 0;   // largest embedded grid of the batch (shared memory of one CTA, in points)
+  } fft;
 };
+
+constexpr int FFT_MAX_POINTS = 128 * 129;   // one embedded grid (L = 128, d = 2, padded): 129 KB of complex64
 
 bool is_tc(int prec) { return prec == PRONY_BF16X3 || prec == PRONY_BF16X2 || prec == PRONY_TF32X3; }
 
@@ -291,7 +298,9 @@ int check_tc_error(prony_ctx* ctx, const Batch& B);
 void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int xbuf, int wsel, int ybuf, int prec,
                       cudaStream_t s, int adjoint = -1) {
   if (adjoint < 0) adjoint = ext ? 0 : 1;
-  if (B.tc.on) {
+  if (B.fft.on) {
+    launch_toeplitz_fft(D, B.fft.maxpts, wsel == W_ONE ? 1 : B.maxw, adjoint, xbuf, wsel, ybuf, ext, s);
+  } else if (B.tc.on) {
     const TcConf& T = B.tc;
     launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.kind, T.prob_stride, s);
     cudaError_t e = launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, T.nks,
@@ -358,6 +367,31 @@ int tc_autotune(prony_ctx* ctx, Batch& B, const Dev& D, int prec, cudaStream_t s
   if ((rc = tc_set_jobs(ctx, B, pick.first, pick.second))) return rc;
   ctx->tc_tuned[T.key] = pick;
   T.tuned = true;
+  return PRONY_OK;
+}
+
+// FFT products: embedding length and transform offset of every problem, device tables.
+int setup_fft(prony_ctx* ctx, Batch& B) {
+  long long foff = 0;
+  int maxpts = 0, LT = 2;
+  for (auto& p : B.P) {
+    p.fL = fft_length(p.n);
+    const long long pts = fft_points_host(p.n, p.d);
+    if (pts > FFT_MAX_POINTS) return PRONY_EINVAL;
+    p.foff = foff;
+    foff += pts;
+    maxpts = std::max(maxpts, (int)pts);
+    LT = std::max(LT, p.fL);
+  }
+  int rc;
+  if ((rc = ensure(ctx->fhat, sizeof(float2) * foff))) return rc;
+  if ((rc = ensure(ctx->ftw, sizeof(float2) * LT))) return rc;
+  CK(cudaMemcpyAsync(ctx->P.p, B.P.data(), sizeof(ProbDesc) * B.P.size(), cudaMemcpyHostToDevice, ctx->stream));
+  B.D.fhat = (float2*)ctx->fhat.p;
+  B.D.ftw = (float2*)ctx->ftw.p;
+  B.D.fLT = LT;
+  B.fft.on = true;
+  B.fft.maxpts = maxpts;
   return PRONY_OK;
 }
 
@@ -456,8 +490,10 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
   D.Y = (float2*)ctx->Y.p;
   D.small = (char*)ctx->small.p;
   D.L = L;
+  D.vand = o.vandermonde ? 1 : 0;
   B.jobs_ext = (ToeplitzJob*)ctx->jobs.p;
   B.jobs_in = B.jobs_ext + B.njobs_ext;
+  if (o.precision == PRONY_FFT32) return setup_fft(ctx, B);
   if (is_tc(o.precision)) return setup_tc(ctx, B, o.precision, maxR0);
   return PRONY_OK;
 }
@@ -489,6 +525,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   const double tol_power = o.tol_power > 0 ? o.tol_power : default_tol_power(prec);
   const int max_iter = o.max_iter > 0 ? o.max_iter : 30;
   const double tol_drop = 1e-3;
+  const double tol_lanczos = tol_rank;   // alpha, beta <= tol ||T||_F stop Algorithm 2 (Section 2.1)
 
   // Toeplitz launch, bracketed by events when profiling
   auto toeplitz = [&](int iter, int ext) -> int {
@@ -515,15 +552,48 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   }
   launch_prep(D, s);
   if (B.tc.on) launch_split_tables(D, B.tc.kind, s);
+  if (B.fft.on) launch_fft_tables(D, B.fft.maxpts, s);
   launch_init_v0(D, o.seed, s);
-  tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+  int* dflag = (int*)ctx->flag.p;
+  if (o.svd_method == 1) {
+    // Algorithm 2: Lanczos bidiagonalisation from the first start column, full
+    // reorthogonalisation (classical Gram-Schmidt twice); its right vectors start the power loop
+    const int cap = std::max(1, D.maxR0);
+    launch_lz_start(D, s);
+    auto reorth = [&](int basis, int wsel) {
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_zero_small(D, D.L.work1, 16LL * D.L.LDR * D.L.LDM, s);
+        launch_gram(D, basis, -1, wsel, BUF_B2, -1, W_ONE, D.L.work1, D.L.LDM, s);
+        launch_apply(D, basis, wsel, W_ONE, D.L.work1, 1, BUF_B2, BUF_B2, 0, s);
+      }
+    };
+    for (int step = 0; step < cap; ++step) {
+      launch_lz_load(D, 0, s);                                       // v_k
+      toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, 0);   // T v_k
+      launch_lz_axpy(D, 0, s);                                       // - beta_k u_{k-1}
+      reorth(BUF_U, W_LK);
+      launch_lz_accept(D, 0, tol_lanczos, cap, s);                   // alpha_k, u_k
+      launch_lz_load(D, 1, s);                                       // u_k
+      toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, 1);   // T^* u_k
+      launch_lz_axpy(D, 1, s);                                       // - alpha_k v_k
+      reorth(BUF_V, W_LK1);
+      launch_lz_accept(D, 1, tol_lanczos, cap, s);                   // beta_{k+1}, v_{k+1}
+      CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
+      launch_lz_all_done(D, dflag, s);
+      CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*ctx->h_flag != 0) break;
+    }
+    launch_lz_finish(D, s);
+  } else {
+    tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+  }
   if (B.tc.on && !B.tc.tuned && (rc = tc_autotune(ctx, B, D, prec, s))) return rc;
   if ((rc = toeplitz(0, 1))) return rc;
   if (ctx->prof) {
     ctx->snaps.emplace_back(D.nprob);
     CK(cudaMemcpyAsync(ctx->snaps.back().data(), D.st, sizeof(ProbState) * D.nprob, cudaMemcpyDeviceToHost, s));
   }
-  int* dflag = (int*)ctx->flag.p;
   for (int it = 1; it <= max_iter; ++it) {
     // U = qr(T V_{k-1})  (rows I_n of Y)
     tall_qr(B, BUF_Y, W_V, W_U, QR_DROP, tol_drop, 0, BUF_U, s);
@@ -562,8 +632,20 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
         const ProbDesc& q = B.P[p];
         int w = r.iter == 0 ? q.r0 : (r.ext ? after[p].wv : after[p].wu);
         double rows = r.ext ? q.Next : q.N;
-        fl += 8.0 * rows * q.N * w;
-        by += 8.0 * q.Gd + 8.0 * q.N * w + 8.0 * rows * w;
+        if (B.fft.on) {
+          // transforms as computed: per axis the pruned lines, 5 L log2 L flops each, forward and
+          // inverse, plus the pointwise product (6 flops per point)
+          const int L = q.fL, K = r.ext ? q.n + 2 : q.n + 1;
+          double lines = 0.0, lg = std::log2((double)L);
+          for (int ax = 0; ax < q.d; ++ax)
+            lines += std::pow((double)(q.n + 1), ax) * std::pow((double)L, q.d - 1 - ax) +
+                     std::pow((double)K, ax) * std::pow((double)L, q.d - 1 - ax);
+          fl += w * (5.0 * L * lg * lines + 6.0 * std::pow((double)L, q.d));
+          by += 8.0 * q.N * w + 8.0 * rows * w + 8.0 * (double)fft_points_host(q.n, q.d);
+        } else {
+          fl += 8.0 * rows * q.N * w;
+          by += 8.0 * q.Gd + 8.0 * q.N * w + 8.0 * rows * w;
+        }
       }
       ctx->stats.tc_cluster = B.tc.on ? B.tc.cs : 0;
       ctx->stats.tc_ksplit = B.tc.on ? B.tc.nks : 0;
@@ -616,6 +698,7 @@ int read_states(prony_ctx* ctx, const Batch& B, prony_info* infos, int* worst) {
       I.power_resid = s.normT2 > 0 ? std::sqrt(std::max(0.0, s.resid2) / s.normT2) : 0.0;
       I.ls_resid = s.normf2 > 0 ? std::sqrt(std::max(0.0, s.ls_num2) / s.normf2) : 0.0;
       I.sigma_ratio = s.sigma_ratio;
+      I.lanczos_steps = s.lk;
     }
     if (s.status != PRONY_OK && (w == PRONY_OK || s.status < w)) w = s.status;
   }
@@ -631,7 +714,7 @@ prony_opts resolve_opts(const prony_opts* o) {
 }
 
 int check_precision(int prec) {
-  return (prec == PRONY_FP32 || is_tc(prec)) ? PRONY_OK : PRONY_EINVAL;
+  return (prec == PRONY_FP32 || prec == PRONY_FFT32 || is_tc(prec)) ? PRONY_OK : PRONY_EINVAL;
 }
 
 // Error flag of the tensor-core kernels (bounded waits that gave up, window overflow).
@@ -677,6 +760,8 @@ void prony_default_opts(prony_opts* o) {
   o->max_iter = 0;
   o->seed = 2012114300ull;
   o->rank_mode = 0;
+  o->vandermonde = 0;
+  o->svd_method = 0;
 }
 
 const char* prony_status_string(int s) {
@@ -787,13 +872,14 @@ static int solve_batched_impl(prony_ctx* ctx, int P, const int* d, const int* n,
   int worst = PRONY_OK;
   if ((rc = read_states(ctx, B, infos, &worst))) return rc;
   if (!dev_out) {
-    // per-problem d may differ: copy each problem's block
+    // rows of maxd entries; a problem writes its first d of each row only
     std::vector<double> th(total_terms * maxd);
     std::vector<double2> ch(total_terms);
     CK(cudaMemcpy(th.data(), tdev, sizeof(double) * total_terms * maxd, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(ch.data(), cdev, sizeof(double2) * total_terms, cudaMemcpyDeviceToHost));
     for (int i = 0; i < P; ++i) {
-      std::memcpy(t_out + out_off[i] * d[i], th.data() + out_off[i] * d[i], sizeof(double) * m[i] * d[i]);
+      for (int j = 0; j < m[i]; ++j)
+        std::memcpy(t_out + (out_off[i] + j) * maxd, th.data() + (out_off[i] + j) * maxd, sizeof(double) * d[i]);
       std::memcpy(c_out + out_off[i], ch.data() + out_off[i], sizeof(double2) * m[i]);
     }
   } else if (user_stream) {
@@ -1014,6 +1100,7 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
   CK(cudaMemcpyAsync(ctx->grid64.p, grid_dev, sizeof(double2) * B.P[0].Gd, cudaMemcpyDeviceToDevice, ctx->stream));
   launch_prep(B.D, ctx->stream);
   if (B.tc.on) launch_split_tables(B.D, B.tc.kind, ctx->stream);
+  if (B.fft.on) launch_fft_tables(B.D, B.fft.maxpts, ctx->stream);
   // operate directly on the caller's buffers: X as V (ld N), Y as Y (ld L^d)
   Dev D = B.D;
   D.V = (float2*)X_dev;

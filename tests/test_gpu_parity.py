@@ -203,6 +203,20 @@ def test_batched_matches_single_and_oracle(ctx):
         assert np.max(W.torus_dist(single.t, r.t)) <= 1e-6
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_batched_mixed_dimensions(ctx, prec):
+    """One call over problems of d = 1, 2, 3: t comes back in rows of the call's largest d."""
+    from paper_2012_11430_gb300 import default_opts
+    probs = [W.make_problem(f"md{i}", d, n, m, 600 + i) for i, (d, n, m) in
+             enumerate([(1, 30, 4), (2, 11, 5), (3, 5, 3), (2, 7, 2), (1, 9, 2)])]
+    outs, rc = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
+                                 [p.m for p in probs], default_opts(precision=prec))
+    for p, r in zip(probs, outs):
+        assert r.info["status"] == 0 and r.t.shape == (p.m, p.d), r.info
+        order = np.lexsort(p.t.T[::-1])
+        _check_solution(r, p.t[order], p.c[order])
+
+
 # ----------------------------------------------------------------------------- tensor-core path
 # Split-BF16 products: three planes represent an FP32 value exactly; the three dropped products
 # (relative 2^-24, 2^-24, 2^-32) add ~3 u32 per term; two planes round each operand to 16 bits
@@ -333,3 +347,187 @@ def test_detect_rank_mode(ctx, prec):
     assert np.all(res.c[P.m:] == 0)
     res0 = ctx.solve(P.grid, P.d, P.n, m_over, default_opts(precision=prec), allow=(PRONY_ERANK,))
     assert res0.info["status"] == PRONY_ERANK and res0.info["rank_detected"] == P.m
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_raw_z_vandermonde(ctx, prec):
+    """Least-squares matrix from the raw eigenvalues z~ (Section 4 reading): noise-free it equals
+    the unit-modulus matrix (exact recovery); under noise the GPU's forward error stays within
+    1.5x the FP64 oracle's with the same reading, and its residual matches the oracle's."""
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C1")
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision=prec, vandermonde=1))
+    order = np.lexsort(P.t.T[::-1])
+    _check_solution(res, P.t[order], P.c[order])
+    Pn = W.make_problem("rawz", 2, 15, 5, 901, snr_db=20.0)
+    res = ctx.solve(Pn.grid, Pn.d, Pn.n, Pn.m, default_opts(precision=prec, vandermonde=1))
+    t_o, c_o, info_o = O.prony(Pn.grid, Pn.d, Pn.n, Pn.m, svd="power", tol_power=1e-13, vandermonde_from="z")
+    te_g, ce_g = W.match_to_truth(res.t, res.c, Pn.t, Pn.c)
+    te_o, ce_o = W.match_to_truth(t_o, c_o, Pn.t, Pn.c)
+    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (te_g, te_o, ce_g, ce_o)
+    assert abs(res.info["ls_resid"] - info_o["ls_resid"]) <= 1e-3 * info_o["ls_resid"]
+
+
+def _lanczos_reference_steps(P, seed=1):
+    """Steps of the oracle's Algorithm 2 on the explicit T from the solver's start vector (the
+    first column of the Philox start block V_0), stopping at tol_rank ||T||_F."""
+    from oracle import philox
+    T = O.build_T(P.grid, P.n, P.d)
+    N = T.shape[1]
+    v0 = philox.complex_normal_block(seed, philox.STREAM_V0, N, min(2 * P.m, N))[:, 0]
+    r, *_ = O.lanczos_bidiag(T, v0, 1e-3 * np.linalg.norm(T))
+    return r
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("name,d,n,m,seed", [
+    ("C1", 2, 15, 5, None), ("d1", 1, 12, 3, 5), ("d2rag", 2, 9, 7, 7), ("d3", 3, 5, 4, 8),
+    ("d2m12", 2, 23, 12, 10),
+])
+def test_lanczos_start_noise_free(ctx, prec, name, d, n, m, seed):
+    """Algorithm 2 (Lanczos bidiagonalisation, full reorthogonalisation) as the subspace step:
+    noise-free, T has rank m and the FP64 oracle's Algorithm 2 from the same start vector stops
+    after m left vectors.  With FP32 products the Krylov recurrence carries rounding into the
+    residual of step m + 1 (an FP32 emulation of the same loop leaves alpha_{m+1} at up to
+    1.7e-3 ||T||_F for these shapes), so the GPU may take one more step, a noise direction that
+    the pivoted-QR rank step drops; the solver recovers t and c either way."""
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C1") if seed is None else W.make_problem(name, d, n, m, seed)
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision=prec, svd_method=1))
+    assert res.info["status"] == 0, res.info
+    assert _lanczos_reference_steps(P) == m
+    assert res.info["lanczos_steps"] in (m, m + 1), res.info
+    order = np.lexsort(P.t.T[::-1])
+    _check_solution(res, P.t[order], P.c[order])
+    assert res.info["rank_detected"] == m
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_lanczos_start_noisy_C2(ctx, prec):
+    """Noisy C2 with the Lanczos start: the number of Lanczos steps is within one of the FP64
+    oracle's Algorithm 2 with the same start vector and tolerance (capped at r0 = 2m columns;
+    FP32 rounding moves the residual near the threshold), and the forward error stays within
+    1.5x the oracle's block power result."""
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C2")
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision=prec, svd_method=1))
+    assert res.info["status"] == 0, res.info
+    assert abs(res.info["lanczos_steps"] - min(_lanczos_reference_steps(P), 2 * P.m)) <= 1, res.info
+    t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
+    te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
+    te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
+    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (te_g, te_o, ce_g, ce_o)
+
+
+def test_lanczos_start_batched_and_rank_detect(ctx):
+    """Batched Lanczos start over problems of different shapes (each stops at its own step),
+    and rank detection from an overestimate m' > m."""
+    from paper_2012_11430_gb300 import default_opts
+    probs = [W.make_problem(f"lzb{i}", d, n, m, 300 + i) for i, (d, n, m) in
+             enumerate([(2, 15, 5), (1, 20, 3), (2, 9, 7), (3, 4, 2)])]
+    res, _ = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
+                            [p.m for p in probs], default_opts(precision="bf16x3", svd_method=1))
+    for P, r in zip(probs, res):
+        assert r.info["status"] == 0 and r.info["lanczos_steps"] in (P.m, P.m + 1), r.info
+        order = np.lexsort(P.t.T[::-1])
+        _check_solution(r, P.t[order], P.c[order])
+    P = W.make_problem("lzrank", 2, 15, 5, 78)
+    r = ctx.solve(P.grid, P.d, P.n, 8, default_opts(precision="bf16x3", svd_method=1, rank_mode=1))
+    assert r.info["rank_used"] == P.m and r.info["lanczos_steps"] in (P.m, P.m + 1), r.info
+    order = np.lexsort(P.t.T[::-1])
+    _check_solution(type(r)(r.t[:P.m], r.c[:P.m], r.info), P.t[order], P.c[order])
+
+
+# ------------------------------------------------------------------ FFT products (PRONY_FFT32)
+def _fft_len(n):
+    L = 2
+    while L < 2 * n + 2:
+        L *= 2
+    return L
+
+
+@pytest.mark.parametrize("d,n,r,L_ext,adjoint", [
+    (1, 7, 3, 1, 0), (1, 40, 5, 0, 1), (1, 300, 4, 1, 0), (2, 15, 10, 1, 0), (2, 15, 10, 0, 1),
+    (2, 9, 5, 1, 0), (2, 9, 17, 0, 1), (3, 4, 7, 1, 0), (3, 4, 7, 0, 1), (3, 7, 3, 1, 0),
+    (2, 31, 40, 1, 0), (2, 63, 20, 1, 0), (2, 63, 40, 0, 1), (2, 5, 1, 1, 0), (2, 1, 2, 0, 0),
+])
+def test_toeplitz_product_fft(ctx, d, n, r, L_ext, adjoint):
+    """Circulant-embedding FFT product against the explicit T (FP64).  FFT rounding is
+    normwise: per column ||y - T x||_2 <= 8 log2(L^d) u32 max|DFT(f_emb)| ||x||_2, with
+    max|DFT(f_emb)| the spectral norm of the embedding circulant (>= ||T||_2), from numpy's FFT of
+    the samples placed at k mod L."""
+    import torch
+    grid = _random_grid(d, n, 300 + d * 10 + n)
+    N = (n + 1) ** d
+    L = n + 2 if L_ext else n + 1
+    rng = np.random.Generator(np.random.PCG64(27 + r))
+    X = (rng.standard_normal((r, N)) + 1j * rng.standard_normal((r, N))).astype(np.complex64)
+    g_dev = torch.from_numpy(grid.reshape(-1).astype(np.complex128)).cuda()
+    X_dev = torch.from_numpy(X).cuda()
+    Y_dev = torch.full((r, L ** d), float("nan"), dtype=torch.complex64, device="cuda")
+    ctx.toeplitz_mm_dev(g_dev, d, n, X_dev, L, adjoint, "fft32", Y_dev)
+    Y = Y_dev.cpu().numpy().astype(np.complex128).T
+    T = _toeplitz_rows(grid, n, d, L, adjoint)
+    Xd = X.astype(np.complex128).T
+    ref = T @ Xd
+    Lf = _fft_len(n)
+    emb = np.zeros((Lf,) * d, dtype=np.complex128)
+    idx = np.arange(-n, n + 2) % Lf
+    emb[np.ix_(*([idx] * d))] = grid
+    cnorm = np.max(np.abs(np.fft.fftn(emb)))
+    err = np.linalg.norm(Y - ref, axis=0)
+    bound = 8 * np.log2(Lf ** d) * U32 * cnorm * np.linalg.norm(Xd, axis=0)
+    assert np.all(np.isfinite(Y))
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+@pytest.mark.parametrize("name,d,n,m,seed", [
+    ("C1", 2, 15, 5, None), ("d1", 1, 40, 3, 5), ("d2rag", 2, 9, 7, 7), ("d3", 3, 5, 4, 8),
+    ("d2m12", 2, 23, 12, 10), ("d1m1", 1, 4, 1, 6),
+])
+def test_solve_fft_matches_oracle(ctx, name, d, n, m, seed):
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C1") if seed is None else W.make_problem(name, d, n, m, seed)
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision="fft32"))
+    t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m)
+    assert res.info["status"] == 0, res.info
+    _check_solution(res, t_o, c_o)
+    assert res.info["rank_detected"] == m
+
+
+def test_solve_noisy_C2_fft(ctx):
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C2")
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision="fft32"))
+    t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
+    te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
+    te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
+    assert res.info["status"] == 0, res.info
+    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (te_g, te_o, ce_g, ce_o)
+
+
+def test_fft_batched_uneven_and_limits(ctx):
+    """Batched FFT products over problems of different n (different L) and d, against the
+    oracle; a problem whose embedding does not fit one CTA (d = 3, n = 19) is refused."""
+    from paper_2012_11430_gb300 import PronyError, default_opts, PRONY_EINVAL
+    probs = [W.make_problem(f"fb{i}", d, n, m, 500 + i) for i, (d, n, m) in
+             enumerate([(2, 7, 2), (2, 31, 12), (2, 12, 5), (1, 50, 4), (3, 6, 3), (2, 63, 20)])]
+    res, _ = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
+                               [p.m for p in probs], default_opts(precision="fft32"))
+    for P, r in zip(probs, res):
+        assert r.info["status"] == 0, r.info
+        order = np.lexsort(P.t.T[::-1])
+        _check_solution(r, P.t[order], P.c[order])
+    P = W.make_problem("big3", 3, 19, 4, 9)
+    with pytest.raises(PronyError) as e:
+        ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision="fft32"))
+    assert e.value.code == PRONY_EINVAL
+
+
+def test_lanczos_with_fft_products(ctx):
+    from paper_2012_11430_gb300 import default_opts
+    P = W.config_problem("C1")
+    res = ctx.solve(P.grid, P.d, P.n, P.m, default_opts(precision="fft32", svd_method=1))
+    assert res.info["status"] == 0 and res.info["lanczos_steps"] in (P.m, P.m + 1), res.info
+    order = np.lexsort(P.t.T[::-1])
+    _check_solution(res, P.t[order], P.c[order])
