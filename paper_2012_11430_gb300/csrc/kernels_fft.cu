@@ -94,13 +94,34 @@ __device__ inline int axis_stride(int L, int P, int d, int m) {
   return s;
 }
 
+// Where a stage reads its points and where it writes its results.  The first stage of an axis
+// (M = L) may take its points from the column in HBM (the last axis of the first forward pass)
+// or treat the positions at and beyond `ein` along the axis as zero (they were never written:
+// no zero fill is needed); the last forward stage may multiply by the spectrum of the samples
+// (stored in the same scrambled order); the last inverse stage (M = L) may keep only the
+// positions below `eout`, in shared memory or scaled into the output column in HBM.
+enum { IN_SMEM = 0, IN_PRUNED = 1, IN_GLOBAL = 2 };
+enum { OUT_SMEM = 0, OUT_SPECTRUM = 1, OUT_PRUNED = 2, OUT_GLOBAL = 3 };
+struct StageIO {
+  int in_mode, ein;
+  const float2* X;      // column base, rows I_n (line li of the last axis starts at row li * ein)
+  int out_mode, eout;
+  const float2* F;      // spectrum (same layout as the shared array)
+  int conjF;
+  float2* Y;            // output column base (line li of the last axis starts at row li * eout)
+  float scale;
+};
+
 // One stage (sub-blocks of M points, stride S = M / R) over every line of the set.
 template <int R, bool INV>
-__device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2* __restrict__ tw, int LT) {
+__device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2* __restrict__ tw, int LT,
+                          const StageIO& io) {
   constexpr int B = Log2<R>::v;
   const int per_line = L / R, S = M / R;
   const int items = ls.nl * per_line;
-  const bool lines_fast = ls.no > 0;
+  // consecutive threads take consecutive lines (distinct banks, see the layout) unless the stage
+  // touches HBM, where consecutive points of a line keep the accesses coalesced
+  const bool lines_fast = ls.no > 0 && io.in_mode != IN_GLOBAL && io.out_mode != OUT_GLOBAL;
   const int tws = LT / M;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     int line, bj;
@@ -115,14 +136,27 @@ __device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2
     float2* p = a + ls.base(line) + (b * M + j) * ls.es;
     const int step = S * ls.es;
     float2 x[R];
+    if (io.in_mode == IN_GLOBAL) {              // M = L: the point of index q sits at position j + S q
+      const float2* xl = io.X + (long long)line * io.ein;
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = p[q * step];
+      for (int q = 0; q < R; ++q) x[q] = j + S * q < io.ein ? xl[j + S * q] : make_float2(0.f, 0.f);
+    } else if (io.in_mode == IN_PRUNED) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = j + S * q < io.ein ? p[q * step] : make_float2(0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) x[q] = p[q * step];
+    }
     if (!INV) {
       dft_reg<R, false>(x);
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         float2 y = x[bitrev(k, B)];
         if (k > 0 && j > 0) y = cmulf(y, __ldg(&tw[((j * k) & (M - 1)) * tws]));
+        if (io.out_mode == OUT_SPECTRUM) {
+          const float2 f = __ldg(&io.F[(p - a) + k * step]);
+          y = cmulf(y, io.conjF ? make_float2(f.x, -f.y) : f);
+        }
         p[k * step] = y;
       }
     } else {
@@ -134,8 +168,21 @@ __device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2
         }
       }
       dft_reg<R, true>(x);
+      if (io.out_mode == OUT_GLOBAL) {          // M = L: output index q is position j + S q
+        float2* yl = io.Y + (long long)line * io.eout;
 #pragma unroll
-      for (int q = 0; q < R; ++q) p[q * step] = x[bitrev(q, B)];
+        for (int q = 0; q < R; ++q) {
+          const float2 v = x[bitrev(q, B)];
+          if (j + S * q < io.eout) yl[j + S * q] = make_float2(v.x * io.scale, v.y * io.scale);
+        }
+      } else if (io.out_mode == OUT_PRUNED) {
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          if (j + S * q < io.eout) p[q * step] = x[bitrev(q, B)];
+      } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) p[q * step] = x[bitrev(q, B)];
+      }
     }
   }
 }
@@ -143,12 +190,12 @@ __device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2
 __device__ inline int stage_radix(int M) { return M >= 16 ? 16 : M; }
 
 template <bool INV>
-__device__ void fft_stage_any(float2* a, const Lines& ls, int L, int M, const float2* tw, int LT) {
+__device__ void fft_stage_any(float2* a, const Lines& ls, int L, int M, const float2* tw, int LT, const StageIO& io) {
   switch (stage_radix(M)) {
-    case 16: fft_stage<16, INV>(a, ls, L, M, tw, LT); break;
-    case 8: fft_stage<8, INV>(a, ls, L, M, tw, LT); break;
-    case 4: fft_stage<4, INV>(a, ls, L, M, tw, LT); break;
-    default: fft_stage<2, INV>(a, ls, L, M, tw, LT); break;
+    case 16: fft_stage<16, INV>(a, ls, L, M, tw, LT, io); break;
+    case 8: fft_stage<8, INV>(a, ls, L, M, tw, LT, io); break;
+    case 4: fft_stage<4, INV>(a, ls, L, M, tw, LT, io); break;
+    default: fft_stage<2, INV>(a, ls, L, M, tw, LT, io); break;
   }
 }
 
@@ -168,41 +215,64 @@ __device__ inline Lines axis_lines(int L, int P, int d, int axis, int E) {
   return ls;
 }
 
-// Forward transform along every axis, last axis first; lines whose coordinates on the axes not
-// yet transformed exceed E - 1 are zero and skipped.
-__device__ void fft_forward(float2* a, int L, int P, int d, int E, const float2* tw, int LT) {
+// Forward transform of a fully populated grid (the samples' table), every line, last axis first.
+__device__ void fft_forward_full(float2* a, int L, int P, int d, const float2* tw, int LT) {
+  StageIO io{};
   for (int axis = d - 1; axis >= 0; --axis) {
-    const Lines ls = axis_lines(L, P, d, axis, E);
+    const Lines ls = axis_lines(L, P, d, axis, L);
     for (int M = L; M > 1; M /= stage_radix(M)) {
-      fft_stage_any<false>(a, ls, L, M, tw, LT);
+      fft_stage_any<false>(a, ls, L, M, tw, LT, io);
       __syncthreads();
     }
   }
 }
 
-// Inverse of fft_forward (unscaled), first axis first; only lines whose coordinates on the axes
-// already back in the sample domain are below E are computed.
-__device__ void fft_inverse(float2* a, int L, int P, int d, int E, const float2* tw, int LT) {
+// Forward transform of the column x (nonzero on {0..n}^d, read from HBM), last axis first,
+// ending with the product by the spectrum F (or its conjugate).  Lines whose coordinates on the
+// axes not yet transformed exceed n are zero and skipped.
+__device__ void fft_forward_column(float2* a, int L, int P, int d, int n, const float2* X, const float2* F,
+                                   int conjF, const float2* tw, int LT) {
+  for (int axis = d - 1; axis >= 0; --axis) {
+    const Lines ls = axis_lines(L, P, d, axis, n + 1);
+    for (int M = L; M > 1; M /= stage_radix(M)) {
+      StageIO io{};
+      if (M == L) {
+        io.in_mode = axis == d - 1 ? IN_GLOBAL : IN_PRUNED;
+        io.ein = n + 1;
+        io.X = X;
+      }
+      if (axis == 0 && M == stage_radix(M)) {
+        io.out_mode = OUT_SPECTRUM;
+        io.F = F;
+        io.conjF = conjF;
+      }
+      fft_stage_any<false>(a, ls, L, M, tw, LT, io);
+      __syncthreads();
+    }
+  }
+}
+
+// Inverse of the forward pass (scaled by 1/L^d), first axis first; only lines whose coordinates
+// on the axes already back in the sample domain are below K are computed, and the last axis
+// writes the rows of the box {0..K-1}^d straight into the output column Y.
+__device__ void fft_inverse_column(float2* a, int L, int P, int d, int K, float2* Y, float scale, const float2* tw,
+                                   int LT) {
   for (int axis = 0; axis < d; ++axis) {
-    const Lines ls = axis_lines(L, P, d, axis, E);
+    const Lines ls = axis_lines(L, P, d, axis, K);
     int Ms[16], ns = 0;
     for (int M = L; M > 1; M /= stage_radix(M)) Ms[ns++] = M;
     for (int s = ns - 1; s >= 0; --s) {
-      fft_stage_any<true>(a, ls, L, Ms[s], tw, LT);
+      StageIO io{};
+      if (s == 0) {
+        io.out_mode = axis == d - 1 ? OUT_GLOBAL : OUT_PRUNED;
+        io.eout = K;
+        io.Y = Y;
+        io.scale = scale;
+      }
+      fft_stage_any<true>(a, ls, L, Ms[s], tw, LT, io);
       __syncthreads();
     }
   }
-}
-
-// position of row r of a box with `base` points per axis (row-major) in the padded layout
-__device__ inline int grid_index(int r, int base, int d, int L, int P) {
-  int g = 0, rem = r;
-  for (int l = d - 1; l >= 0; --l) {
-    const int k = rem % base;
-    rem /= base;
-    g += k * axis_stride(L, P, d, l);
-  }
-  return g;
 }
 
 __device__ inline int fft_pitch(const ProbDesc& p) { return p.d >= 2 ? p.fL + 1 : p.fL; }
@@ -237,7 +307,7 @@ __global__ void __launch_bounds__(512) k_fft_table(Dev D) {
     a[g] = D.gF[p.grid + i];
   }
   __syncthreads();
-  fft_forward(a, L, P, d, L, D.ftw, D.fLT);
+  fft_forward_full(a, L, P, d, D.ftw, D.fLT);
   for (int i = threadIdx.x; i < npts; i += blockDim.x) D.fhat[p.foff + i] = a[i];
 }
 
@@ -260,32 +330,14 @@ __global__ void __launch_bounds__(512) k_toeplitz_fft(Dev D, int adjoint, int xb
   if (st.done) return;
   const int col = blockIdx.x;
   if (col >= sel_width(st, p, wsel)) return;
-  const int L = p.fL, d = p.d, n = p.n, P = fft_pitch(p), npts = fft_points(p);
+  const int L = p.fL, d = p.d, n = p.n, P = fft_pitch(p);
   int Ld = 1;
   for (int l = 0; l < d; ++l) Ld *= L;
   int ldx, ldy;
   const float2* X = fbuf(D, xbuf, p, ldx) + (long long)col * ldx;
   float2* Y = fbuf(D, ybuf, p, ldy) + (long long)col * ldy;
-  for (int i = threadIdx.x; i < npts; i += blockDim.x) a[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int r = threadIdx.x; r < p.N; r += blockDim.x) a[grid_index(r, n + 1, d, L, P)] = X[r];
-  __syncthreads();
-  fft_forward(a, L, P, d, n + 1, D.ftw, D.fLT);
-  const float2* F = D.fhat + p.foff;
-  for (int i = threadIdx.x; i < npts; i += blockDim.x) {
-    const float2 f = __ldg(&F[i]);
-    a[i] = cmulf(a[i], adjoint ? make_float2(f.x, -f.y) : f);
-  }
-  __syncthreads();
-  const int K = y_ext ? n + 2 : n + 1;
-  fft_inverse(a, L, P, d, K, D.ftw, D.fLT);
-  const float scale = 1.0f / (float)Ld;
-  int rows = 1;
-  for (int l = 0; l < d; ++l) rows *= K;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-    const float2 v = a[grid_index(r, K, d, L, P)];
-    Y[r] = make_float2(v.x * scale, v.y * scale);
-  }
+  fft_forward_column(a, L, P, d, n, X, D.fhat + p.foff, adjoint, D.ftw, D.fLT);
+  fft_inverse_column(a, L, P, d, y_ext ? n + 2 : n + 1, Y, 1.0f / (float)Ld, D.ftw, D.fLT);
 }
 
 int fft_threads(int maxpts) { return maxpts >= 8192 ? 512 : maxpts >= 2048 ? 256 : 128; }

@@ -4,6 +4,9 @@
 // (Eq. ls_probl), and the exponential sum of Eq. 1 with its vector-Jacobian product.
 #include "common.cuh"
 
+#include <algorithm>
+#include <map>
+
 namespace {
 
 __device__ inline const ProbDesc& prob(const Dev& D, int p) { return D.P[p]; }
@@ -126,29 +129,42 @@ __global__ void k_zero_small(Dev D, long long off, long long bytes) {
 // ----------------------------------------------------------------------------- tall-skinny Gram
 // out[a][b] += sum_r conj(X[r, a]) Z[r, b] over a block of `chunk` rows (chosen by the launcher
 // so that the batch gives a few blocks per SM: few blocks per problem means few FP64 atomics on
-// the same output entries).  Rows are staged in shared memory GRAM_ROWS at a time with
-// asynchronous copies into two alternating buffers (the next rows load while the current ones
-// are multiplied), transposed (row-major, padded) so that threads reading neighbouring columns
-// hit different banks.  Each thread owns a 4x4 tile of (a, b); when there are fewer tiles than
-// threads, threads split the staged rows into row groups, whose partial sums are added by a tree
-// in shared memory; when there are more, the tiles are processed in batches of blockDim.x
-// (every batch re-stages the rows).  Each block adds its totals to the FP64 output with one
-// atomic per entry.
-constexpr int GRAM_ROWS = 32;       // rows staged per pass (per buffer)
+// the same output entries).
+//
+// Rows are staged RS at a time (32, or 16 / 8 for wide blocks) in two alternating shared-memory
+// buffers: each thread loads the next rows' values into registers while the current ones are
+// multiplied, then stores them.  A thread stages one row (its row index is computed once per
+// pass) and several columns; the values are stored column-major with a row pitch of RS + 1 and
+// pre-arranged for paired FP32 FMAs (fma.rn.f32x2): x as (Re x, Re x, Im x, Im x) and z as
+// (Re z, Im z, Im z, -Re z), so that conj(x) z is two paired FMAs on (re, im) accumulators.
+// Output ownership is interleaved: thread (ti, tj) owns the entries (ti + NA i, tj + NB j),
+// i, j < 4, so the threads of a warp read consecutive columns (different banks) or the same one
+// (broadcast).  When there are fewer 4x4 tiles than threads, threads split the staged rows into
+// row groups whose partial sums are added in shared memory; when there are more, the tiles are
+// processed in batches (every batch re-stages the rows).  Each block adds its totals to the FP64
+// output with one atomic per entry.
 constexpr int GRAM_T = 4;           // register tile (GRAM_T x GRAM_T complex accumulators)
+constexpr int GRAM_KMAX = 10;       // staged values per thread and pass: (a + b) RS <= 256 GRAM_KMAX
 
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, int bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
-               "l"(gsrc), "r"(bytes)
-               : "memory");
+__host__ __device__ inline int gram_rows(int LR) { return LR <= 40 ? 32 : LR <= 80 ? 16 : 8; }
+
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return make_float2(lo, hi);
+}
+__device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
 
 __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
                                               long long out_off, int out_ld, int chunk) {
-  extern __shared__ float2 smem[];
+  extern __shared__ float4 smem4[];
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
   const ProbState& s = D.st[pi];
@@ -158,82 +174,97 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
   if (r_begin >= p.N || a <= 0 || b <= 0) return;
   const int r_end = min(p.N, r_begin + chunk);
   const int LR = D.L.LDR;
-  const int lda = a + 1, ldb = b + 1;             // padded row strides of the staged rows
-  const size_t buf_elems = (size_t)GRAM_ROWS * (LR + 1);
-  float2* stage = smem;                           // [2 buffers][X rows | Z rows]
-  float2* red = smem + 4 * buf_elems;             // [RG-1][per_batch][16] row-group partial sums
+  const int RS = gram_rows(LR), PR = RS + 1;
+  const size_t buf_elems = (size_t)2 * LR * PR;   // X then Z, column-major with row pitch PR
+  // [RG-1][per_batch][16] packed partial sums, over the staging buffers once the rows are done
+  unsigned long long* red = (unsigned long long*)smem4;
   int ldx, ldz;
   const float2* X = buf_base(D, xbuf, p, ldx);
   const float2* Z = buf_base(D, zbuf, p, ldz);
-  const int na = (a + GRAM_T - 1) / GRAM_T, nb = (b + GRAM_T - 1) / GRAM_T, ntile = na * nb;
+  const int NA = (a + GRAM_T - 1) / GRAM_T, NB = (b + GRAM_T - 1) / GRAM_T, ntile = NA * NB;
   const int nthr = blockDim.x;
   const int per_batch = min(ntile, nthr);
   const int RG = max(1, min(8, nthr / per_batch));     // row groups (1 when tiles >= threads)
   const int nbatch = (ntile + per_batch - 1) / per_batch;
   double2* out = (double2*)(D.small + p.soff + out_off);
-  // asynchronous staging of rows r0 .. r0 + GRAM_ROWS - 1 into buffer k (zeros past r_end)
-  auto stage_rows = [&](int r0, int k) {
-    float2* Xs = stage + (size_t)k * 2 * buf_elems;
-    float2* Zs = Xs + buf_elems;
-    for (int idx = threadIdx.x; idx < (a + b) * GRAM_ROWS; idx += nthr) {
-      const int rr = idx % GRAM_ROWS, col = idx / GRAM_ROWS;
-      const int r = r0 + rr;
-      const bool ok = r < r_end;
-      if (col < a) {
-        const float2* src = X + (long long)col * ldx + (ok ? buf_row(xbuf, p, r, xshift) : 0);
-        cp_async8(Xs + rr * lda + col, src, ok ? 8 : 0);
-      } else {
-        const int cz = col - a;
-        const float2* src = Z + (long long)cz * ldz + (ok ? buf_row(zbuf, p, r, zshift) : 0);
-        cp_async8(Zs + rr * ldb + cz, src, ok ? 8 : 0);
-      }
+  // staging role: one row, columns c0, c0 + cstep, ...
+  const int my_rr = threadIdx.x % RS, c0 = threadIdx.x / RS, cstep = nthr / RS;
+  float2 held[GRAM_KMAX];
+  auto load_rows = [&](int r0) {
+    const int r = r0 + my_rr;
+    const bool ok = r < r_end;
+    const int gx = ok ? buf_row(xbuf, p, r, xshift) : 0, gz = ok ? buf_row(zbuf, p, r, zshift) : 0;
+#pragma unroll
+    for (int k = 0; k < GRAM_KMAX; ++k) {
+      const int col = c0 + k * cstep;
+      float2 v = make_float2(0.f, 0.f);
+      if (ok && col < a) v = X[(long long)col * ldx + gx];
+      else if (ok && col < a + b) v = Z[(long long)(col - a) * ldz + gz];
+      held[k] = v;
     }
-    cp_async_commit();
+  };
+  auto store_rows = [&](int buf) {
+    float4* Xs = smem4 + (size_t)buf * buf_elems;
+    float4* Zs = Xs + (size_t)LR * PR;
+#pragma unroll
+    for (int k = 0; k < GRAM_KMAX; ++k) {
+      const int col = c0 + k * cstep;
+      const float2 v = held[k];
+      if (col < a) Xs[col * PR + my_rr] = make_float4(v.x, v.x, v.y, v.y);
+      else if (col < a + b) Zs[(col - a) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
+    }
   };
   for (int batch = 0; batch < nbatch; ++batch) {
     const int tile = batch * per_batch + threadIdx.x % per_batch, grp = threadIdx.x / per_batch;
     const bool active = grp < RG && tile < ntile;
-    const int ia0 = GRAM_T * (tile / nb), jb0 = GRAM_T * (tile % nb);
-    float2 acc[GRAM_T][GRAM_T];
+    const int ti = tile / NB, tj = tile % NB;
+    unsigned long long acc[GRAM_T][GRAM_T];
 #pragma unroll
     for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
-      for (int j = 0; j < GRAM_T; ++j) acc[i][j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < GRAM_T; ++j) acc[i][j] = 0ull;
     __syncthreads();                              // the buffers are free (previous batch done)
-    stage_rows(r_begin, 0);
+    load_rows(r_begin);
+    store_rows(0);
     int k = 0;
-    for (int r0 = r_begin; r0 < r_end; r0 += GRAM_ROWS, k ^= 1) {
-      if (r0 + GRAM_ROWS < r_end) {
-        stage_rows(r0 + GRAM_ROWS, k ^ 1);        // next rows load while these are multiplied
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
+    for (int r0 = r_begin; r0 < r_end; r0 += RS, k ^= 1) {
+      const bool more = r0 + RS < r_end;
+      if (more) load_rows(r0 + RS);               // in flight while these rows are multiplied
       __syncthreads();
-      const float2* Xs = stage + (size_t)k * 2 * buf_elems;
-      const float2* Zs = Xs + buf_elems;
+      const float4* Xs = smem4 + (size_t)k * buf_elems;
+      const float4* Zs = Xs + (size_t)LR * PR;
       if (active) {
-        for (int rr = grp; rr < GRAM_ROWS; rr += RG) {
-          float2 xa[GRAM_T], zb[GRAM_T];
+        const int nrows = min(RS, r_end - r0);
+        for (int rr = grp; rr < nrows; rr += RG) {
+          float4 xa[GRAM_T], zb[GRAM_T];
 #pragma unroll
-          for (int i = 0; i < GRAM_T; ++i) xa[i] = ia0 + i < a ? Xs[rr * lda + ia0 + i] : make_float2(0.f, 0.f);
+          for (int i = 0; i < GRAM_T; ++i) {
+            const int ia = ti + NA * i;
+            xa[i] = ia < a ? Xs[ia * PR + rr] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
 #pragma unroll
-          for (int j = 0; j < GRAM_T; ++j) zb[j] = jb0 + j < b ? Zs[rr * ldb + jb0 + j] : make_float2(0.f, 0.f);
+          for (int j = 0; j < GRAM_T; ++j) {
+            const int jb = tj + NB * j;
+            zb[j] = jb < b ? Zs[jb * PR + rr] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
 #pragma unroll
-          for (int i = 0; i < GRAM_T; ++i)
+          for (int i = 0; i < GRAM_T; ++i) {
+            const unsigned long long x0 = pk2(xa[i].x, xa[i].y), x1 = pk2(xa[i].z, xa[i].w);
 #pragma unroll
             for (int j = 0; j < GRAM_T; ++j) {
-              acc[i][j].x += xa[i].x * zb[j].x + xa[i].y * zb[j].y;   // conj(x) z
-              acc[i][j].y += xa[i].x * zb[j].y - xa[i].y * zb[j].x;
+              ffma2(acc[i][j], x0, pk2(zb[j].x, zb[j].y));   // (Re x Re z, Re x Im z)
+              ffma2(acc[i][j], x1, pk2(zb[j].z, zb[j].w));   // + (Im x Im z, -Im x Re z)
             }
+          }
         }
       }
-      __syncthreads();                            // buffer k is overwritten two passes later
+      if (more) store_rows(k ^ 1);                // the other buffer was released by the sync above
     }
     // row groups: partial sums meet in shared memory, group 0 adds them (fixed order)
     if (RG > 1) {
+      __syncthreads();                            // every group is done with the staged rows
       if (active && grp > 0) {
-        float2* dst = red + ((size_t)(grp - 1) * per_batch + (tile - batch * per_batch)) * 16;
+        unsigned long long* dst = red + ((size_t)(grp - 1) * per_batch + (tile - batch * per_batch)) * 16;
 #pragma unroll
         for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
@@ -242,13 +273,13 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
       __syncthreads();
       if (active && grp == 0) {
         for (int g = 1; g < RG; ++g) {
-          const float2* src = red + ((size_t)(g - 1) * per_batch + (tile - batch * per_batch)) * 16;
+          const unsigned long long* src = red + ((size_t)(g - 1) * per_batch + (tile - batch * per_batch)) * 16;
 #pragma unroll
           for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
             for (int j = 0; j < GRAM_T; ++j) {
-              acc[i][j].x += src[i * GRAM_T + j].x;
-              acc[i][j].y += src[i * GRAM_T + j].y;
+              const float2 u = upk2(acc[i][j]), v = upk2(src[i * GRAM_T + j]);
+              acc[i][j] = pk2(u.x + v.x, u.y + v.y);
             }
         }
       }
@@ -258,10 +289,11 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
       for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
         for (int j = 0; j < GRAM_T; ++j) {
-          const int ia = ia0 + i, jb = jb0 + j;
+          const int ia = ti + NA * i, jb = tj + NB * j;
           if (ia < a && jb < b) {
-            atomicAdd(&out[ia * out_ld + jb].x, (double)acc[i][j].x);
-            atomicAdd(&out[ia * out_ld + jb].y, (double)acc[i][j].y);
+            const float2 v = upk2(acc[i][j]);
+            atomicAdd(&out[ia * out_ld + jb].x, (double)v.x);
+            atomicAdd(&out[ia * out_ld + jb].y, (double)v.y);
           }
         }
     }
@@ -303,21 +335,41 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
   }
   int ldx;
   const float2* X = buf_base(D, xbuf, p, ldx);
-  for (int idx = threadIdx.x; idx < a * rows; idx += blockDim.x) {
-    const int rr = idx % rows, col = idx / rows;
-    const int r = r0 + rr;
-    Xs[idx] = (r < p.N) ? X[(long long)col * ldx + buf_row(xbuf, p, r, -1)] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
+  // a thread stages one row (blockDim.x is a multiple of rows) and every cstep-th column, eight
+  // loads in flight at a time
   const int rr = threadIdx.x % rows, cg = threadIdx.x / rows;
   const int ngrp = blockDim.x / rows;
   const int r = r0 + rr;
+  {
+    const bool ok = r < p.N;
+    const int gx = ok ? buf_row(xbuf, p, r, -1) : 0;
+    for (int cb = cg; cb < a; cb += 8 * ngrp) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int col = cb + u * ngrp;
+        v[u] = (ok && col < a) ? X[(long long)col * ldx + gx] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int col = cb + u * ngrp;
+        if (col < a) Xs[col * rows + rr] = v[u];
+      }
+    }
+  }
+  __syncthreads();
   int ldz = 0, ldo = 0;
   const float2* Z = zbuf >= 0 ? buf_base(D, zbuf, p, ldz) : nullptr;
   float2* O = norm_only ? nullptr : buf_base(D, outbuf, p, ldo);
   double nrm = 0.0;
   if (r < p.N) {
+    const int gz = Z ? buf_row(zbuf, p, r, -1) : 0;
+    const int go = O ? buf_row(outbuf, p, r, -1) : 0;
     for (int j0 = 4 * cg; j0 < b; j0 += 4 * ngrp) {
+      float2 zv[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)      // issued before the products so that their latency overlaps them
+        zv[e] = (Z && j0 + e < b) ? Z[(long long)(j0 + e) * ldz + gz] : make_float2(0.f, 0.f);
       float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       for (int i = 0; i < a; ++i) {
         const float2 x = Xs[i * rows + rr];
@@ -335,12 +387,11 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
         if (j >= b) break;
         float2 v = acc[e];
         if (Z) {
-          const float2 z = Z[(long long)j * ldz + buf_row(zbuf, p, r, -1)];
-          v.x = z.x - v.x;
-          v.y = z.y - v.y;
+          v.x = zv[e].x - v.x;
+          v.y = zv[e].y - v.y;
         }
         if (norm_only) nrm += (double)v.x * v.x + (double)v.y * v.y;
-        else O[(long long)j * ldo + buf_row(outbuf, p, r, -1)] = v;
+        else O[(long long)j * ldo + go] = v;
       }
     }
   }
@@ -378,20 +429,31 @@ __global__ void k_argmax(Dev D, int buf) {
 
 // ----------------------------------------------------------------------------- Vandermonde RHS / residual
 // rhs: b_i = sum_{k in I_n} conj(z_i^k) f(k);  resid: ||sum_j c_j z_j^k - f(k)||^2.
-// z_i^k = prod_l E_l[i][k_l] with E_l[i][x] = exp(-+2 pi i t_i(l) x) built by FP64 recurrence.
-constexpr int RHS_ROWS = 256;
-constexpr int RHS_TABLE_MAX = 6144;
+// z_i^k = prod_l E_l[i][k_l] with E_l[i][x] = exp(-+2 pi i t_i(l) x) built by an FP64 recurrence
+// once per block and kept in shared memory rounded to FP32; each term is formed in FP32 and
+// summed in FP64.  A term carries a relative error of a few u32 and the errors of the N terms
+// add up like a random walk, so b is accurate to ~u32 / sqrt(N) of its size; the residual to
+// ~u32 |f|.  Blocks take RHS_ROWS rows of one problem; for b, the threads split into m groups
+// (one term each) that share the block's rows, for the residual each thread takes rows.
+constexpr int RHS_ROWS = 1024;
+constexpr int RHS_TABLE_MAX = 6144;          // d m (n + 1) (checked when a problem is accepted)
 
 __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
-  extern __shared__ double2 tab[];   // [d][m][n+1]
-  __shared__ double2 accb[PRONY_MMAX];
+  extern __shared__ float2 tabf[];   // [d][m][n+1] powers, then RHS_ROWS samples f, then [d][RHS_ROWS] digits
+  __shared__ double2 part[256];
   __shared__ double shr[32];
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
   ProbState& s = D.st[pi];
   const int m = s.rank_used;
   if (s.done || m <= 0 || m > p.m) return;
+  const int r0 = blockIdx.x * RHS_ROWS;
+  if (r0 >= p.N) return;
+  const int nrows = min(RHS_ROWS, p.N - r0);
   const int n1 = p.n + 1;
+  const int tsize = p.d * m * n1;
+  float2* fs = tabf + tsize;
+  int* kd = (int*)(fs + RHS_ROWS);                 // kd[l * RHS_ROWS + rr]: digit l of row rr
   const double* t = (const double*)(D.small + p.soff + D.L.t);
   const double2* c = (const double2*)(D.small + p.soff + D.L.c);
   const double sign = resid ? -1.0 : 1.0;
@@ -409,61 +471,61 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
       e1 = make_double2(cs, sign * sn);
     }
     double2 e = make_double2(1.0, 0.0);
-    double2* row = tab + ((size_t)l * m + i) * n1;
+    float2* row = tabf + ((size_t)l * m + i) * n1;
     for (int x = 0; x < n1; ++x) {
-      row[x] = e;
+      row[x] = make_float2((float)e.x, (float)e.y);
       e = cmul(e, e1);
     }
   }
-  for (int i = threadIdx.x; i < PRONY_MMAX; i += blockDim.x) accb[i] = make_double2(0.0, 0.0);
-  __syncthreads();
-  const int r = blockIdx.x * RHS_ROWS + threadIdx.x;
-  int kk[PRONY_DMAX];
-  double2 f = make_double2(0.0, 0.0);
-  bool valid = r < p.N;
-  if (valid) {
-    int rem = r, gi = 0, mul = 1;
+  for (int rr = threadIdx.x; rr < nrows; rr += blockDim.x) {
+    int rem = r0 + rr, gi = 0, mul = 1;
     for (int l = p.d - 1; l >= 0; --l) {
-      kk[l] = rem % n1;
+      const int k = rem % n1;
       rem /= n1;
-      gi += (kk[l] + p.n) * mul;
+      gi += (k + p.n) * mul;
       mul *= p.G;
+      kd[l * RHS_ROWS + rr] = k;
     }
-    f = D.grid64[p.grid + gi];
+    const double2 f = D.grid64[p.grid + gi];
+    fs[rr] = make_float2((float)f.x, (float)f.y);
   }
+  __syncthreads();
+  auto power = [&](int i, int rr) {
+    float2 e = tabf[(size_t)i * n1 + kd[rr]];
+    for (int l = 1; l < p.d; ++l) e = cmulf(e, tabf[((size_t)l * m + i) * n1 + kd[l * RHS_ROWS + rr]]);
+    return e;
+  };
   if (!resid) {
-    for (int i = 0; i < m; ++i) {
-      double2 term = make_double2(0.0, 0.0);
-      if (valid) {
-        double2 e = tab[(size_t)i * n1 + kk[0]];
-        for (int l = 1; l < p.d; ++l) e = cmul(e, tab[((size_t)l * m + i) * n1 + kk[l]]);
-        term = cmul(e, f);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        term.x += __shfl_xor_sync(0xffffffffu, term.x, o);
-        term.y += __shfl_xor_sync(0xffffffffu, term.y, o);
-      }
-      if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&accb[i].x, term.x);
-        atomicAdd(&accb[i].y, term.y);
+    const int tpi = blockDim.x / m;                 // threads per term (m <= 64: at least 4)
+    const int i = threadIdx.x / tpi, q = threadIdx.x % tpi;
+    double2 acc = make_double2(0.0, 0.0);
+    if (i < m) {
+      for (int rr = q; rr < nrows; rr += tpi) {
+        const float2 v = cmulf(power(i, rr), fs[rr]);
+        acc.x += (double)v.x;
+        acc.y += (double)v.y;
       }
     }
+    part[threadIdx.x] = acc;
     __syncthreads();
     double2* b = (double2*)(D.small + p.soff + D.L.rhs);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      atomicAdd(&b[i].x, accb[i].x);
-      atomicAdd(&b[i].y, accb[i].y);
+    if (i < m && q == 0) {
+      double2 sum = make_double2(0.0, 0.0);
+      for (int u = 0; u < tpi; ++u) sum = cadd(sum, part[threadIdx.x + u]);
+      atomicAdd(&b[i].x, sum.x);
+      atomicAdd(&b[i].y, sum.y);
     }
   } else {
     double r2 = 0.0;
-    if (valid) {
-      double2 v = make_double2(-f.x, -f.y);
+    for (int rr = threadIdx.x; rr < nrows; rr += blockDim.x) {
+      float2 v = make_float2(-fs[rr].x, -fs[rr].y);
       for (int i = 0; i < m; ++i) {
-        double2 e = tab[(size_t)i * n1 + kk[0]];
-        for (int l = 1; l < p.d; ++l) e = cmul(e, tab[((size_t)l * m + i) * n1 + kk[l]]);
-        v = cadd(v, cmul(c[i], e));
+        const float2 ci = make_float2((float)c[i].x, (float)c[i].y);
+        const float2 e = cmulf(ci, power(i, rr));
+        v.x += e.x;
+        v.y += e.y;
       }
-      r2 = cabs2(v);
+      r2 += (double)v.x * v.x + (double)v.y * v.y;
     }
     double tot = block_sum(r2, shr);
     if (threadIdx.x == 0) atomicAdd(&s.ls_num2, tot);
@@ -616,17 +678,28 @@ void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_
 void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
                  int out_ld, cudaStream_t s) {
   static size_t set = 0;
-  // two buffers of staged rows of X and Z, then the row-group partial sums: (RG - 1) x tiles x 16 entries with
-  // RG = min(8, 256 / tiles) when tiles <= 128, at most 224 x 16 (32 tiles, 8 groups)
-  const size_t sm = sizeof(float2) * (4 * (size_t)(D.L.LDR + 1) * GRAM_ROWS + (size_t)224 * 16);
+  static std::map<size_t, int> slots_for;      // shared memory size -> resident blocks on the GPU
+  // two buffers of staged rows of X and Z (float4 per value); afterwards the same space holds the
+  // row-group partial sums, (RG - 1) x tiles x 16 packed entries with RG = min(8, 256 / tiles):
+  // at most 224 x 16
+  const int RS = gram_rows(D.L.LDR);
+  const size_t sm = std::max(sizeof(float4) * (4 * (size_t)D.L.LDR * (RS + 1)), sizeof(unsigned long long) * 224 * 16);
   if (sm > set) {
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;
   }
-  // rows per block: enough blocks for ~3 per SM over the batch, at least GRAM_ROWS, at most N
-  long long rows_total = (long long)D.maxN * D.nprob;
-  int chunk = (int)std::min<long long>(D.maxN, std::max<long long>(GRAM_ROWS, rows_total / (152 * 3)));
-  chunk = (chunk + GRAM_ROWS - 1) / GRAM_ROWS * GRAM_ROWS;
+  auto it = slots_for.find(sm);
+  if (it == slots_for.end()) {
+    int occ = 1, dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram, 256, sm);
+    it = slots_for.emplace(sm, std::max(1, occ) * sms).first;
+  }
+  // rows per block: the batch fills the resident blocks once (one wave), at least RS rows
+  const int per_prob = std::max(1, it->second / std::max(1, D.nprob));
+  int chunk = std::max(RS, (D.maxN + per_prob - 1) / per_prob);
+  chunk = (chunk + RS - 1) / RS * RS;
   dim3 g((D.maxN + chunk - 1) / chunk, D.nprob);
   note_launch();
   k_gram<<<g, 256, sm, s>>>(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld, chunk);
@@ -654,14 +727,14 @@ void launch_argmax(const Dev& D, int buf, cudaStream_t s) {
 
 void launch_rhs(const Dev& D, int resid, cudaStream_t s) {
   static bool attr = false;
-  size_t sm = sizeof(double2) * RHS_TABLE_MAX;
+  const size_t sm = sizeof(float2) * (RHS_TABLE_MAX + RHS_ROWS) + sizeof(int) * PRONY_DMAX * RHS_ROWS;
   if (!attr) {
     cudaFuncSetAttribute(k_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
   dim3 g((D.maxN + RHS_ROWS - 1) / RHS_ROWS, D.nprob);
   note_launch();
-  k_rhs<<<g, RHS_ROWS, sm, s>>>(D, resid);
+  k_rhs<<<g, 256, sm, s>>>(D, resid);
 }
 
 void launch_gather_out(const Dev& D, double* t_out, double2* c_out, cudaStream_t s) {
