@@ -162,7 +162,7 @@ __device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long lon
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
 
-__global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
+__global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
                                               long long out_off, int out_ld, int chunk) {
   extern __shared__ float4 smem4[];
   const int pi = blockIdx.y;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
   const int RG = max(1, min(8, nthr / per_batch));     // row groups (1 when tiles >= threads)
   const int nbatch = (ntile + per_batch - 1) / per_batch;
   double2* out = (double2*)(D.small + p.soff + out_off);
-  // staging role: one row, columns c0, c0 + cstep, ...
+  // staging role: one row, columns c0, c0 + cstep, ... (k-th: X column if below a, else Z)
   const int my_rr = threadIdx.x % RS, c0 = threadIdx.x / RS, cstep = nthr / RS;
   float2 held[GRAM_KMAX];
   auto load_rows = [&](int r0) {
@@ -198,26 +198,33 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
     for (int k = 0; k < GRAM_KMAX; ++k) {
       const int col = c0 + k * cstep;
       float2 v = make_float2(0.f, 0.f);
-      if (ok && col < a) v = X[(long long)col * ldx + gx];
-      else if (ok && col < a + b) v = Z[(long long)(col - a) * ldz + gz];
+      if (ok && col < a + b) v = col < a ? X[(long long)col * ldx + gx] : Z[(long long)(col - a) * ldz + gz];
       held[k] = v;
     }
   };
   auto store_rows = [&](int buf) {
     float4* Xs = smem4 + (size_t)buf * buf_elems;
-    float4* Zs = Xs + (size_t)LR * PR;
 #pragma unroll
     for (int k = 0; k < GRAM_KMAX; ++k) {
       const int col = c0 + k * cstep;
       const float2 v = held[k];
+      // X and Z regions are contiguous: Z column c sits at column LR + c of the buffer
       if (col < a) Xs[col * PR + my_rr] = make_float4(v.x, v.x, v.y, v.y);
-      else if (col < a + b) Zs[(col - a) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
+      else if (col < a + b) Xs[(col - a + LR) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
     }
   };
   for (int batch = 0; batch < nbatch; ++batch) {
     const int tile = batch * per_batch + threadIdx.x % per_batch, grp = threadIdx.x / per_batch;
     const bool active = grp < RG && tile < ntile;
     const int ti = tile / NB, tj = tile % NB;
+    // offsets of the owned columns in a buffer (entries past a or b read a valid column; their
+    // sums are never stored)
+    int xo[GRAM_T], zo[GRAM_T];
+#pragma unroll
+    for (int i = 0; i < GRAM_T; ++i) {
+      xo[i] = min(ti + NA * i, a - 1) * PR;
+      zo[i] = (min(tj + NB * i, b - 1) + LR) * PR;
+    }
     unsigned long long acc[GRAM_T][GRAM_T];
 #pragma unroll
     for (int i = 0; i < GRAM_T; ++i)
@@ -231,31 +238,24 @@ __global__ void __launch_bounds__(256) k_gram(Dev D, int xbuf, int xshift, int x
       const bool more = r0 + RS < r_end;
       if (more) load_rows(r0 + RS);               // in flight while these rows are multiplied
       __syncthreads();
-      const float4* Xs = smem4 + (size_t)k * buf_elems;
-      const float4* Zs = Xs + (size_t)LR * PR;
+      // each staged value is 16 bytes read as two packed pairs: x = ((Re x, Re x), (Im x, Im x)),
+      // z = ((Re z, Im z), (Im z, -Re z))
+      const ulonglong2* Bs = (const ulonglong2*)(smem4 + (size_t)k * buf_elems);
       if (active) {
         const int nrows = min(RS, r_end - r0);
         for (int rr = grp; rr < nrows; rr += RG) {
-          float4 xa[GRAM_T], zb[GRAM_T];
+          ulonglong2 xa[GRAM_T], zb[GRAM_T];
 #pragma unroll
-          for (int i = 0; i < GRAM_T; ++i) {
-            const int ia = ti + NA * i;
-            xa[i] = ia < a ? Xs[ia * PR + rr] : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+          for (int i = 0; i < GRAM_T; ++i) xa[i] = Bs[xo[i] + rr];
 #pragma unroll
-          for (int j = 0; j < GRAM_T; ++j) {
-            const int jb = tj + NB * j;
-            zb[j] = jb < b ? Zs[jb * PR + rr] : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+          for (int j = 0; j < GRAM_T; ++j) zb[j] = Bs[zo[j] + rr];
 #pragma unroll
-          for (int i = 0; i < GRAM_T; ++i) {
-            const unsigned long long x0 = pk2(xa[i].x, xa[i].y), x1 = pk2(xa[i].z, xa[i].w);
+          for (int i = 0; i < GRAM_T; ++i)
 #pragma unroll
             for (int j = 0; j < GRAM_T; ++j) {
-              ffma2(acc[i][j], x0, pk2(zb[j].x, zb[j].y));   // (Re x Re z, Re x Im z)
-              ffma2(acc[i][j], x1, pk2(zb[j].z, zb[j].w));   // + (Im x Im z, -Im x Re z)
+              ffma2(acc[i][j], xa[i].x, zb[j].x);   // (Re x Re z, Re x Im z)
+              ffma2(acc[i][j], xa[i].y, zb[j].y);   // + (Im x Im z, -Im x Re z)
             }
-          }
         }
       }
       if (more) store_rows(k ^ 1);                // the other buffer was released by the sync above
