@@ -181,7 +181,11 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
   int ldx, ldz;
   const float2* X = buf_base(D, xbuf, p, ldx);
   const float2* Z = buf_base(D, zbuf, p, ldz);
-  const int NA = (a + GRAM_T - 1) / GRAM_T, NB = (b + GRAM_T - 1) / GRAM_T, ntile = NA * NB;
+  // X^* X (same buffer, shift and width): the rows are loaded once and only the tiles on and
+  // above the diagonal are computed, the others written as their conjugate mirrors
+  const bool sym = xbuf == zbuf && xshift == zshift && a == b;
+  const int NA = (a + GRAM_T - 1) / GRAM_T, NB = (b + GRAM_T - 1) / GRAM_T;
+  const int ntile = sym ? NA * (NA + 1) / 2 : NA * NB;
   const int nthr = blockDim.x;
   const int per_batch = min(ntile, nthr);
   const int RG = max(1, min(8, nthr / per_batch));     // row groups (1 when tiles >= threads)
@@ -194,11 +198,12 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
     const int r = r0 + my_rr;
     const bool ok = r < r_end;
     const int gx = ok ? buf_row(xbuf, p, r, xshift) : 0, gz = ok ? buf_row(zbuf, p, r, zshift) : 0;
+    const int ncols = sym ? a : a + b;
 #pragma unroll
     for (int k = 0; k < GRAM_KMAX; ++k) {
       const int col = c0 + k * cstep;
       float2 v = make_float2(0.f, 0.f);
-      if (ok && col < a + b) v = col < a ? X[(long long)col * ldx + gx] : Z[(long long)(col - a) * ldz + gz];
+      if (ok && col < ncols) v = col < a ? X[(long long)col * ldx + gx] : Z[(long long)(col - a) * ldz + gz];
       held[k] = v;
     }
   };
@@ -209,14 +214,27 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
       const int col = c0 + k * cstep;
       const float2 v = held[k];
       // X and Z regions are contiguous: Z column c sits at column LR + c of the buffer
-      if (col < a) Xs[col * PR + my_rr] = make_float4(v.x, v.x, v.y, v.y);
-      else if (col < a + b) Xs[(col - a + LR) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
+      if (col < a) {
+        Xs[col * PR + my_rr] = make_float4(v.x, v.x, v.y, v.y);
+        if (sym) Xs[(col + LR) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
+      } else if (!sym && col < a + b) {
+        Xs[(col - a + LR) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
+      }
     }
   };
   for (int batch = 0; batch < nbatch; ++batch) {
     const int tile = batch * per_batch + threadIdx.x % per_batch, grp = threadIdx.x / per_batch;
     const bool active = grp < RG && tile < ntile;
-    const int ti = tile / NB, tj = tile % NB;
+    int ti = tile / NB, tj = tile % NB;
+    if (sym) {                                    // tile -> (ti, tj), ti <= tj, row by row
+      ti = 0;
+      int rest = min(tile, ntile - 1);
+      while (rest >= NA - ti) {
+        rest -= NA - ti;
+        ++ti;
+      }
+      tj = ti + rest;
+    }
     // offsets of the owned columns in a buffer (entries past a or b read a valid column; their
     // sums are never stored)
     int xo[GRAM_T], zo[GRAM_T];
@@ -294,6 +312,10 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
             const float2 v = upk2(acc[i][j]);
             atomicAdd(&out[ia * out_ld + jb].x, (double)v.x);
             atomicAdd(&out[ia * out_ld + jb].y, (double)v.y);
+            if (sym && ti != tj) {                // mirror entry of a tile above the diagonal
+              atomicAdd(&out[jb * out_ld + ia].x, (double)v.x);
+              atomicAdd(&out[jb * out_ld + ia].y, -(double)v.y);
+            }
           }
         }
     }

@@ -737,11 +737,18 @@ int check_tc_error(prony_ctx* ctx, const Batch& B) {
 }
 
 // Copy problem grids to the packed device buffer (host or device source).
+// Samples into the packed grid buffer: one copy per run of problems whose grids are adjacent
+// both in the caller's array and in the buffer (the usual packed layout is a single copy).
 int load_grids(prony_ctx* ctx, const Batch& B, const std::vector<HostProb>& hp, const prony_c128* src, bool device) {
-  for (size_t i = 0; i < hp.size(); ++i) {
-    const ProbDesc& p = B.P[i];
-    CK(cudaMemcpyAsync((double2*)ctx->grid64.p + p.grid, src + hp[i].sample_off, sizeof(double2) * p.Gd,
+  size_t i = 0;
+  while (i < hp.size()) {
+    const long long s0 = hp[i].sample_off, d0 = B.P[i].grid;
+    long long len = B.P[i].Gd;
+    size_t j = i + 1;
+    while (j < hp.size() && hp[j].sample_off == s0 + len && B.P[j].grid == d0 + len) len += B.P[j++].Gd;
+    CK(cudaMemcpyAsync((double2*)ctx->grid64.p + d0, src + s0, sizeof(double2) * len,
                        device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    i = j;
   }
   return PRONY_OK;
 }
