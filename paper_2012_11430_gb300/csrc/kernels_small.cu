@@ -23,11 +23,15 @@ __device__ inline void set_status(ProbState& s, int st) {
 }
 
 // ----------------------------------------------------------------------------- pivoted Cholesky (FP32)
+// Step i: warp 0 finds the pivot (largest remaining diagonal entry, lowest index on ties) and the
+// trailing trace and decides whether to stop; rows and columns i, pv are swapped; the scaled
+// column l = A[:, i] / sqrt(A[i][i]) goes to shared memory and the trailing block takes the rank-1
+// update A[j][k] -= l_j conj(l_k).  R^{-1} (R = L^H) is formed by one warp per column with the
+// partial sums of the back substitution spread over the lanes.
 __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int mode, double tol, int rank_mode) {
   extern __shared__ float2 A[];                 // [w][LDR]
   __shared__ int perm[PRONY_RMAX];
-  __shared__ float red_v[256];
-  __shared__ int red_i[256];
+  __shared__ float2 lcol[PRONY_RMAX];
   __shared__ int s_piv, s_stop, s_rho, s_rank;
   __shared__ float s_trace0, s_maxd0;
   const ProbDesc& p = D.P[blockIdx.x];
@@ -35,6 +39,7 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   if (st.done) return;
   const int w = swidth(st, p, wsel);
   const int LR = D.L.LDR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double2* G = (const double2*)(D.small + p.soff + D.L.gram);
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     int i = idx / w, j = idx % w;
@@ -43,26 +48,33 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   }
   for (int i = threadIdx.x; i < w; i += blockDim.x) perm[i] = i;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     float tr = 0.f, mx = 0.f;
     bool finite = true;
-    for (int i = 0; i < w; ++i) {
-      float dd = A[i * LR + i].x;
+    for (int i = lane; i < w; i += 32) {
+      const float dd = A[i * LR + i].x;
       finite = finite && isfinite(dd);
       tr += fmaxf(dd, 0.f);
       mx = fmaxf(mx, dd);
     }
-    s_trace0 = tr;
-    s_maxd0 = mx;
-    s_rho = w;
-    s_rank = -1;
-    s_stop = finite && isfinite(tr) ? 0 : 2;
-    if (s_stop) {                       // non-finite block: the problem stops with ENAN
-      st.status = ST_ENAN;
-      st.done = 1;
-      st.w_in = w;
-      st.w_out = 0;
-      set_width(st, target, 0);
+    for (int o = 16; o > 0; o >>= 1) {
+      tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) {
+      s_trace0 = tr;
+      s_maxd0 = mx;
+      s_rho = w;
+      s_rank = -1;
+      s_stop = finite && isfinite(tr) ? 0 : 2;
+      if (s_stop) {                     // non-finite block: the problem stops with ENAN
+        st.status = ST_ENAN;
+        st.done = 1;
+        st.w_in = w;
+        st.w_out = 0;
+        set_width(st, target, 0);
+      }
     }
   }
   __syncthreads();
@@ -71,89 +83,75 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   int limit = w;  // columns that may be accepted (never more than m after the rank step)
   if (mode == QR_RANK) limit = min(w, p.m);
   for (int i = 0; i < w; ++i) {
-    // pivot search and trailing trace
-    float best = -1.f;
-    int bi = i;
-    float tr = 0.f;
-    for (int j = i + threadIdx.x; j < w; j += blockDim.x) {
-      float dd = A[j * LR + j].x;
-      tr += fmaxf(dd, 0.f);
-      if (dd > best) { best = dd; bi = j; }
-    }
-    red_v[threadIdx.x] = best;
-    red_i[threadIdx.x] = bi;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
-        float v2 = red_v[threadIdx.x + o];
-        int i2 = red_i[threadIdx.x + o];
-        if (v2 > red_v[threadIdx.x] || (v2 == red_v[threadIdx.x] && i2 < red_i[threadIdx.x])) {
-          red_v[threadIdx.x] = v2;
-          red_i[threadIdx.x] = i2;
+    if (warp == 0) {                    // pivot search and trailing trace
+      float best = -1.f, tr = 0.f;
+      int bi = i;
+      for (int j = i + lane; j < w; j += 32) {
+        const float dd = A[j * LR + j].x;
+        tr += fmaxf(dd, 0.f);
+        if (dd > best) {
+          best = dd;
+          bi = j;
         }
       }
-      __syncthreads();
-    }
-    // trailing trace
-    float trs = tr;
-    for (int o = 16; o > 0; o >>= 1) trs += __shfl_xor_sync(0xffffffffu, trs, o);
-    __shared__ float tr_w[8];
-    if ((threadIdx.x & 31) == 0) tr_w[threadIdx.x >> 5] = trs;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float trail = 0.f;
-      for (int q = 0; q < 8; ++q) trail += tr_w[q];
-      int pv = (mode == QR_PLAIN) ? i : red_i[0];
-      float dp = A[pv * LR + pv].x;
-      if (mode == QR_RANK && s_rank < 0 && trail <= tol2 * s_trace0) s_rank = i;
-      bool stop = false;
-      if (!(dp > 1e-30f * s_maxd0) || !(dp > 0.f)) stop = true;                    // exhausted / not PD
-      if (mode == QR_DROP && dp <= tol2 * s_maxd0) stop = true;
-      if (i >= limit && (mode != QR_RANK || s_rank >= 0)) stop = true;
-      if (mode == QR_RANK && rank_mode == 1 && s_rank >= 0) stop = true;
-      if (stop) {
-        s_stop = 1;
-        s_rho = min(i, limit);
+      for (int o = 16; o > 0; o >>= 1) {
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (b2 > best || (b2 == best && i2 < bi)) {
+          best = b2;
+          bi = i2;
+        }
       }
-      s_piv = pv;
+      if (lane == 0) {
+        const int pv = (mode == QR_PLAIN) ? i : bi;
+        const float dp = A[pv * LR + pv].x;
+        if (mode == QR_RANK && s_rank < 0 && tr <= tol2 * s_trace0) s_rank = i;
+        bool stop = false;
+        if (!(dp > 1e-30f * s_maxd0) || !(dp > 0.f)) stop = true;                  // exhausted / not PD
+        if (mode == QR_DROP && dp <= tol2 * s_maxd0) stop = true;
+        if (i >= limit && (mode != QR_RANK || s_rank >= 0)) stop = true;
+        if (mode == QR_RANK && rank_mode == 1 && s_rank >= 0) stop = true;
+        if (stop) {
+          s_stop = 1;
+          s_rho = min(i, limit);
+        }
+        s_piv = pv;
+      }
     }
     __syncthreads();
     if (s_stop) break;
     const int pv = s_piv;
-    if (i >= limit) {
-      // beyond the accepted columns: only continue the factorisation to locate the rank
-    }
     if (pv != i) {
       for (int j = threadIdx.x; j < w; j += blockDim.x) {  // swap rows i, pv
-        float2 t = A[i * LR + j];
+        const float2 t = A[i * LR + j];
         A[i * LR + j] = A[pv * LR + j];
         A[pv * LR + j] = t;
       }
       __syncthreads();
       for (int j = threadIdx.x; j < w; j += blockDim.x) {  // swap cols i, pv
-        float2 t = A[j * LR + i];
+        const float2 t = A[j * LR + i];
         A[j * LR + i] = A[j * LR + pv];
         A[j * LR + pv] = t;
       }
       if (threadIdx.x == 0) {
-        int t = perm[i];
+        const int t = perm[i];
         perm[i] = perm[pv];
         perm[pv] = t;
       }
       __syncthreads();
     }
-    const float lii = sqrtf(A[i * LR + i].x);
-    __syncthreads();
-    for (int j = i + 1 + threadIdx.x; j < w; j += blockDim.x) {
-      float2 v = A[j * LR + i];
-      A[j * LR + i] = make_float2(v.x / lii, v.y / lii);
+    const float inv = rsqrtf(A[i * LR + i].x);
+    for (int j = i + threadIdx.x; j < w; j += blockDim.x) {
+      const float2 v = A[j * LR + i];
+      lcol[j] = make_float2(v.x * inv, v.y * inv);
     }
-    if (threadIdx.x == 0) A[i * LR + i] = make_float2(lii, 0.f);
     __syncthreads();
+    for (int j = i + threadIdx.x; j < w; j += blockDim.x) A[j * LR + i] = lcol[j];   // column i of L
     const int rem = w - i - 1;
     for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-      int j = i + 1 + idx / rem, k = i + 1 + idx % rem;
-      float2 lj = A[j * LR + i], lk = A[k * LR + i];
+      const int j = i + 1 + idx / rem, k = i + 1 + idx % rem;
+      const float2 lj = lcol[j], lk = lcol[k];
       float2 a = A[j * LR + k];
       a.x -= lj.x * lk.x + lj.y * lk.y;            // lj * conj(lk)
       a.y -= lj.y * lk.x - lj.x * lk.y;
@@ -163,27 +161,39 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   }
   __syncthreads();
   const int rho = min(s_rho, limit);
-  // R = L^H (rho x rho); M[perm[a]][b] = Rinv[a][b]; Rinv by column back substitution.
+  // R = L^H (rho x rho); M[perm[a]][b] = Rinv[a][b], column b by back substitution: x_b =
+  // 1 / r_bb, then for k = b .. 0: x_k = s_k / r_kk and s_a -= R[a][k] x_k for a < k, the s_a
+  // spread over the lanes of one warp (a = lane + 32 q).
   float2* M = (float2*)(D.small + p.soff + D.L.mapm);
-  for (int idx = threadIdx.x; idx < w * max(rho, 1); idx += blockDim.x) {
-    int i = idx / max(rho, 1), j = idx % max(rho, 1);
-    M[i * LR + j] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < rho; b += blockDim.x) {
-    float2 x[PRONY_RMAX];
-    for (int a = b; a >= 0; --a) {
-      float2 s = (a == b) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-      for (int k = a + 1; k <= b; ++k) {
-        float2 l = A[k * LR + a];            // R[a][k] = conj(L[k][a])
-        float2 xk = x[k];
-        s.x -= l.x * xk.x + l.y * xk.y;
-        s.y -= l.x * xk.y - l.y * xk.x;
+  const int nwarp = blockDim.x >> 5;
+  for (int b = warp; b < rho; b += nwarp) {
+    float2 sv[PRONY_RMAX / 32];
+#pragma unroll
+    for (int q = 0; q < PRONY_RMAX / 32; ++q) sv[q] = make_float2(lane + 32 * q == b ? 1.f : 0.f, 0.f);
+    for (int k = b; k >= 0; --k) {
+      const int ko = k & 31, kq = k >> 5;
+      float2 mine = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < PRONY_RMAX / 32; ++q)
+        if (q == kq) mine = sv[q];
+      const float rkk = A[k * LR + k].x;
+      float2 xk = make_float2(__shfl_sync(0xffffffffu, mine.x, ko) / rkk, __shfl_sync(0xffffffffu, mine.y, ko) / rkk);
+#pragma unroll
+      for (int q = 0; q < PRONY_RMAX / 32; ++q) {
+        const int a = lane + 32 * q;
+        if (a == k) sv[q] = xk;
+        else if (a < k) {
+          const float2 l = A[k * LR + a];            // R[a][k] = conj(L[k][a])
+          sv[q].x -= l.x * xk.x + l.y * xk.y;
+          sv[q].y -= l.x * xk.y - l.y * xk.x;
+        }
       }
-      float r = A[a * LR + a].x;
-      x[a] = make_float2(s.x / r, s.y / r);
     }
-    for (int a = 0; a <= b; ++a) M[perm[a] * LR + b] = x[a];
+#pragma unroll
+    for (int q = 0; q < PRONY_RMAX / 32; ++q) {
+      const int a = lane + 32 * q;
+      if (a < w) M[perm[a] * LR + b] = a <= b ? sv[q] : make_float2(0.f, 0.f);
+    }
   }
   if (threadIdx.x == 0) {
     st.w_in = w;

@@ -104,10 +104,11 @@ __global__ void k_prep(Dev D) {
 __global__ void k_init_v0(Dev D, unsigned long long seed) {
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
-  long long total = (long long)p.N * p.r0;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    int row = (int)(q / p.r0), col = (int)(q % p.r0);
+  // a thread takes rows, the threads of a warp neighbouring rows of one column at a time
+  // (coalesced stores); the counter of entry (row, col) is row * r0 + col
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < p.N; row += gridDim.x * blockDim.x)
+  for (int col = 0; col < p.r0; ++col) {
+    const long long q = (long long)row * p.r0 + col;
     uint64_t c[4] = {(uint64_t)q, 0, 0, 0};
     philox4x64(c, seed, PRONY_STREAM_V0);
     float u0 = (float)philox_u01(c[0]), u1 = (float)philox_u01(c[1]);
@@ -686,7 +687,7 @@ void launch_prep(const Dev& D, cudaStream_t s) {
 }
 
 void launch_init_v0(const Dev& D, unsigned long long seed, cudaStream_t s) {
-  dim3 g(std::max(1, std::min((D.maxN * D.maxR0 + 255) / 256, 256)), D.nprob);
+  dim3 g(std::max(1, std::min((D.maxN + 255) / 256, 256)), D.nprob);
   note_launch();
   k_init_v0<<<g, 256, 0, s>>>(D, seed);
 }
