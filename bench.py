@@ -434,15 +434,20 @@ def main():
     value = passed_all * args.steps / (total_ms / 1e3)
 
     # ---------------------------------------------------------------- e2e through host pointers
-    grids = [P.grid for P in problems]
+    # the C-ABI call on pinned host buffers: samples in, (t, c) out, copies inside the call
+    t_host = torch.zeros(total_terms * dmax, dtype=torch.float64).pin_memory()
+    c_host = torch.zeros(total_terms, dtype=torch.complex128).pin_memory()
     e2e_ms = []
     for _ in range(max(1, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        outs, _ = ctx.solve_batched(grids, ds, ns, ms, opts)
+        ctx.solve_batched_host(host, ds, ns, ms, soff, ooff, t_host, c_host, opts)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = passed_all / (statistics.mean(e2e_ms) / 1e3) if ws == 1 else None
+    # the host-pointer results are the device-pointer results (up to the order of FP64 atomics)
+    dt = np.abs(t_host.numpy() - t_all)
+    e2e_same = bool(np.max(np.minimum(dt, 1.0 - dt)) <= 1e-6)          # distance on the torus
+    e2e_value = passed_all / (statistics.mean(e2e_ms) / 1e3) if ws == 1 and e2e_same else None
     h2d = int(sum(16 * s for s in sizes))
     d2h = int(total_terms * (8 * dmax + 16) + 48 * B)
 

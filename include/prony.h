@@ -58,8 +58,8 @@ typedef enum {
  *   PRONY_BF16X2 : BF16 hi+lo split, three tensor-core products.
  *   PRONY_FFT32  : no dense product: T embedded in a circulant of L^d points (L the power of
  *                  two >= 2n+2), FP32 FFTs in shared memory, O(L^d log L) per column instead
- *                  of O(N^2).  Needs L^(d-1) (L+1) <= 128 * 129 for every problem of the call
- *                  (d = 1: n <= 8191; d = 2: n <= 63; d = 3: n <= 7), else PRONY_EINVAL. */
+ *                  of O(N^2).  Needs L^(d-1) (L+1) + L <= 128 * 130 for every problem of the
+ *                  call (d = 1: n <= 4095; d = 2: n <= 63; d = 3: n <= 7), else PRONY_EINVAL. */
 typedef enum { PRONY_FP32 = 0, PRONY_BF16X3 = 1, PRONY_TF32X3 = 2, PRONY_BF16X2 = 3, PRONY_FFT32 = 4 } prony_precision;
 
 typedef struct {

@@ -249,6 +249,26 @@ class Context:
         return out, rc
 
     # ---------------------------------------------------------------- device-pointer calls (torch tensors)
+    def solve_batched_host(self, samples, ds, ns, ms, soff, ooff, t_out, c_out, opts: PronyOpts | None = None):
+        """prony_solve_batched on caller-owned host buffers (numpy arrays or CPU torch tensors, pinned
+        or not): packed complex128 samples at soff, t_out (float64) and c_out (complex128) at ooff
+        (t rows of the call's largest d).  Returns (infos, worst status)."""
+        def ptr(a):
+            return ctypes.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else _ptr(a)
+        P = len(ds)
+        ds = np.asarray(ds, dtype=np.int32)
+        ns = np.asarray(ns, dtype=np.int32)
+        ms = np.asarray(ms, dtype=np.int32)
+        soff = np.asarray(soff, dtype=np.int64)
+        ooff = np.asarray(ooff, dtype=np.int64)
+        infos = (PronyInfo * P)()
+        rc = self._lib.prony_solve_batched(self._h, P, _ptr(ds), _ptr(ns), _ptr(ms), _ptr(soff), ptr(samples),
+                                           _ptr(ooff), ptr(t_out), ptr(c_out), infos,
+                                           ctypes.byref(opts) if opts else None)
+        if rc in (PRONY_EINVAL, PRONY_ECUDA, PRONY_ENOMEM):
+            raise PronyError(rc, "prony_solve_batched")
+        return [i.as_dict() for i in infos], rc
+
     def solve_batched_dev(self, samples_dev, ds, ns, ms, soff, ooff, t_out_dev, c_out_dev,
                           opts: PronyOpts | None = None, stream: int = 0):
         ds = np.asarray(ds, dtype=np.int32)

@@ -113,26 +113,29 @@ struct StageIO {
 };
 
 // One stage (sub-blocks of M points, stride S = M / R) over every line of the set.
+// L and M are powers of two (lgL, lgM their logarithms); tw holds exp(-2 pi i q / L), q < L, in
+// shared memory.
 template <int R, bool INV>
-__device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2* __restrict__ tw, int LT,
-                          const StageIO& io) {
+__device__ void fft_stage(float2* a, const Lines& ls, int lgL, int lgM, const float2* tw, const StageIO& io) {
   constexpr int B = Log2<R>::v;
-  const int per_line = L / R, S = M / R;
-  const int items = ls.nl * per_line;
+  const int L = 1 << lgL, M = 1 << lgM;
+  const int lgS = lgM - B, lgPL = lgL - B;
+  const int items = ls.nl << lgPL;
   // consecutive threads take consecutive lines (distinct banks, see the layout) unless the stage
   // touches HBM, where consecutive points of a line keep the accesses coalesced
   const bool lines_fast = ls.no > 0 && io.in_mode != IN_GLOBAL && io.out_mode != OUT_GLOBAL;
-  const int tws = LT / M;
+  const int tws_lg = lgL - lgM;                    // twiddle w_M^e = tw[e << (lgL - lgM)]
+  // (line, bj) of the first item and the step per blockDim.x items (lines fastest)
+  int line = lines_fast ? (int)threadIdx.x % ls.nl : (int)threadIdx.x >> lgPL;
+  int bj = lines_fast ? (int)threadIdx.x / ls.nl : (int)threadIdx.x & ((1 << lgPL) - 1);
+  const int dl = lines_fast ? (int)blockDim.x % ls.nl : 0, dbj = lines_fast ? (int)blockDim.x / ls.nl : 0;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    int line, bj;
-    if (lines_fast) {
-      line = it % ls.nl;
-      bj = it / ls.nl;
-    } else {
-      line = it / per_line;
-      bj = it % per_line;
+    if (!lines_fast) {
+      line = it >> lgPL;
+      bj = it & ((1 << lgPL) - 1);
     }
-    const int b = bj / S, j = bj - b * S;
+    const int b = bj >> lgS, j = bj & ((1 << lgS) - 1);
+    const int S = 1 << lgS;
     float2* p = a + ls.base(line) + (b * M + j) * ls.es;
     const int step = S * ls.es;
     float2 x[R];
@@ -152,7 +155,7 @@ __device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         float2 y = x[bitrev(k, B)];
-        if (k > 0 && j > 0) y = cmulf(y, __ldg(&tw[((j * k) & (M - 1)) * tws]));
+        if (k > 0 && j > 0) y = cmulf(y, tw[((j * k) & (M - 1)) << tws_lg]);
         if (io.out_mode == OUT_SPECTRUM) {
           const float2 f = __ldg(&io.F[(p - a) + k * step]);
           y = cmulf(y, io.conjF ? make_float2(f.x, -f.y) : f);
@@ -163,7 +166,7 @@ __device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2
 #pragma unroll
       for (int k = 1; k < R; ++k) {
         if (j > 0) {
-          const float2 w = __ldg(&tw[((j * k) & (M - 1)) * tws]);
+          const float2 w = tw[((j * k) & (M - 1)) << tws_lg];
           x[k] = cmulf(x[k], make_float2(w.x, -w.y));
         }
       }
@@ -184,18 +187,29 @@ __device__ void fft_stage(float2* a, const Lines& ls, int L, int M, const float2
         for (int q = 0; q < R; ++q) p[q * step] = x[bitrev(q, B)];
       }
     }
+    if (lines_fast) {
+      line += dl;
+      bj += dbj;
+      if (line >= ls.nl) {
+        line -= ls.nl;
+        ++bj;
+      }
+    }
   }
 }
 
 __device__ inline int stage_radix(int M) { return M >= 16 ? 16 : M; }
 
+__device__ inline int ilog2(int v) { return 31 - __clz(v); }
+
 template <bool INV>
-__device__ void fft_stage_any(float2* a, const Lines& ls, int L, int M, const float2* tw, int LT, const StageIO& io) {
+__device__ void fft_stage_any(float2* a, const Lines& ls, int L, int M, const float2* tw, const StageIO& io) {
+  const int lgL = ilog2(L), lgM = ilog2(M);
   switch (stage_radix(M)) {
-    case 16: fft_stage<16, INV>(a, ls, L, M, tw, LT, io); break;
-    case 8: fft_stage<8, INV>(a, ls, L, M, tw, LT, io); break;
-    case 4: fft_stage<4, INV>(a, ls, L, M, tw, LT, io); break;
-    default: fft_stage<2, INV>(a, ls, L, M, tw, LT, io); break;
+    case 16: fft_stage<16, INV>(a, ls, lgL, lgM, tw, io); break;
+    case 8: fft_stage<8, INV>(a, ls, lgL, lgM, tw, io); break;
+    case 4: fft_stage<4, INV>(a, ls, lgL, lgM, tw, io); break;
+    default: fft_stage<2, INV>(a, ls, lgL, lgM, tw, io); break;
   }
 }
 
@@ -216,12 +230,12 @@ __device__ inline Lines axis_lines(int L, int P, int d, int axis, int E) {
 }
 
 // Forward transform of a fully populated grid (the samples' table), every line, last axis first.
-__device__ void fft_forward_full(float2* a, int L, int P, int d, const float2* tw, int LT) {
+__device__ void fft_forward_full(float2* a, int L, int P, int d, const float2* tw) {
   StageIO io{};
   for (int axis = d - 1; axis >= 0; --axis) {
     const Lines ls = axis_lines(L, P, d, axis, L);
     for (int M = L; M > 1; M /= stage_radix(M)) {
-      fft_stage_any<false>(a, ls, L, M, tw, LT, io);
+      fft_stage_any<false>(a, ls, L, M, tw, io);
       __syncthreads();
     }
   }
@@ -231,7 +245,7 @@ __device__ void fft_forward_full(float2* a, int L, int P, int d, const float2* t
 // ending with the product by the spectrum F (or its conjugate).  Lines whose coordinates on the
 // axes not yet transformed exceed n are zero and skipped.
 __device__ void fft_forward_column(float2* a, int L, int P, int d, int n, const float2* X, const float2* F,
-                                   int conjF, const float2* tw, int LT) {
+                                   int conjF, const float2* tw) {
   for (int axis = d - 1; axis >= 0; --axis) {
     const Lines ls = axis_lines(L, P, d, axis, n + 1);
     for (int M = L; M > 1; M /= stage_radix(M)) {
@@ -246,7 +260,7 @@ __device__ void fft_forward_column(float2* a, int L, int P, int d, int n, const 
         io.F = F;
         io.conjF = conjF;
       }
-      fft_stage_any<false>(a, ls, L, M, tw, LT, io);
+      fft_stage_any<false>(a, ls, L, M, tw, io);
       __syncthreads();
     }
   }
@@ -255,8 +269,7 @@ __device__ void fft_forward_column(float2* a, int L, int P, int d, int n, const 
 // Inverse of the forward pass (scaled by 1/L^d), first axis first; only lines whose coordinates
 // on the axes already back in the sample domain are below K are computed, and the last axis
 // writes the rows of the box {0..K-1}^d straight into the output column Y.
-__device__ void fft_inverse_column(float2* a, int L, int P, int d, int K, float2* Y, float scale, const float2* tw,
-                                   int LT) {
+__device__ void fft_inverse_column(float2* a, int L, int P, int d, int K, float2* Y, float scale, const float2* tw) {
   for (int axis = 0; axis < d; ++axis) {
     const Lines ls = axis_lines(L, P, d, axis, K);
     int Ms[16], ns = 0;
@@ -269,7 +282,7 @@ __device__ void fft_inverse_column(float2* a, int L, int P, int d, int K, float2
         io.Y = Y;
         io.scale = scale;
       }
-      fft_stage_any<true>(a, ls, L, Ms[s], tw, LT, io);
+      fft_stage_any<true>(a, ls, L, Ms[s], tw, io);
       __syncthreads();
     }
   }
@@ -295,6 +308,8 @@ __global__ void __launch_bounds__(512) k_fft_table(Dev D) {
   extern __shared__ float2 a[];
   const ProbDesc& p = D.P[blockIdx.x];
   const int L = p.fL, d = p.d, P = fft_pitch(p), npts = fft_points(p);
+  float2* tw = a + npts;                          // exp(-2 pi i q / L), q < L
+  for (int q = threadIdx.x; q < L; q += blockDim.x) tw[q] = D.ftw[q * (D.fLT / L)];
   for (int i = threadIdx.x; i < npts; i += blockDim.x) a[i] = make_float2(0.f, 0.f);
   __syncthreads();
   for (int i = threadIdx.x; i < p.Gd; i += blockDim.x) {
@@ -307,7 +322,7 @@ __global__ void __launch_bounds__(512) k_fft_table(Dev D) {
     a[g] = D.gF[p.grid + i];
   }
   __syncthreads();
-  fft_forward_full(a, L, P, d, D.ftw, D.fLT);
+  fft_forward_full(a, L, P, d, tw);
   for (int i = threadIdx.x; i < npts; i += blockDim.x) D.fhat[p.foff + i] = a[i];
 }
 
@@ -333,11 +348,14 @@ __global__ void __launch_bounds__(512) k_toeplitz_fft(Dev D, int adjoint, int xb
   const int L = p.fL, d = p.d, n = p.n, P = fft_pitch(p);
   int Ld = 1;
   for (int l = 0; l < d; ++l) Ld *= L;
+  float2* tw = a + fft_points(p);                 // exp(-2 pi i q / L), q < L
+  for (int q = threadIdx.x; q < L; q += blockDim.x) tw[q] = D.ftw[q * (D.fLT / L)];
+  __syncthreads();
   int ldx, ldy;
   const float2* X = fbuf(D, xbuf, p, ldx) + (long long)col * ldx;
   float2* Y = fbuf(D, ybuf, p, ldy) + (long long)col * ldy;
-  fft_forward_column(a, L, P, d, n, X, D.fhat + p.foff, adjoint, D.ftw, D.fLT);
-  fft_inverse_column(a, L, P, d, y_ext ? n + 2 : n + 1, Y, 1.0f / (float)Ld, D.ftw, D.fLT);
+  fft_forward_column(a, L, P, d, n, X, D.fhat + p.foff, adjoint, tw);
+  fft_inverse_column(a, L, P, d, y_ext ? n + 2 : n + 1, Y, 1.0f / (float)Ld, tw);
 }
 
 int fft_threads(int maxpts) { return maxpts >= 8192 ? 512 : maxpts >= 2048 ? 256 : 128; }
@@ -360,7 +378,7 @@ long long fft_points_host(int n, int d) {
 void launch_fft_tables(const Dev& D, int maxpts, cudaStream_t s) {
   note_launch();
   k_fft_twiddles<<<(D.fLT + 255) / 256, 256, 0, s>>>(D.ftw, D.fLT);
-  const size_t sm = sizeof(float2) * (size_t)maxpts;
+  const size_t sm = sizeof(float2) * ((size_t)maxpts + D.fLT);
   cudaFuncSetAttribute(k_fft_table, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_launch();
   k_fft_table<<<D.nprob, fft_threads(maxpts), sm, s>>>(D);
@@ -368,7 +386,7 @@ void launch_fft_tables(const Dev& D, int maxpts, cudaStream_t s) {
 
 void launch_toeplitz_fft(const Dev& D, int maxpts, int maxw, int adjoint, int xbuf, int wsel, int ybuf, int y_ext,
                          cudaStream_t s) {
-  const size_t sm = sizeof(float2) * (size_t)maxpts;
+  const size_t sm = sizeof(float2) * ((size_t)maxpts + D.fLT);
   static size_t set = 0;
   if (sm > set) {
     cudaFuncSetAttribute(k_toeplitz_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -144,7 +144,8 @@ struct Batch {
   } fft;
 };
 
-constexpr int FFT_MAX_POINTS = 128 * 129;   // one embedded grid (L = 128, d = 2, padded): 129 KB of complex64
+// one embedded grid and its twiddles in shared memory: L = 128, d = 2 (padded) is 130 KB of complex64
+constexpr int FFT_MAX_POINTS = 128 * 129 + 128;
 
 bool is_tc(int prec) { return prec == PRONY_BF16X3 || prec == PRONY_BF16X2 || prec == PRONY_TF32X3; }
 
@@ -377,7 +378,7 @@ int setup_fft(prony_ctx* ctx, Batch& B) {
   for (auto& p : B.P) {
     p.fL = fft_length(p.n);
     const long long pts = fft_points_host(p.n, p.d);
-    if (pts > FFT_MAX_POINTS) return PRONY_EINVAL;
+    if (pts + p.fL > FFT_MAX_POINTS) return PRONY_EINVAL;
     p.foff = foff;
     foff += pts;
     maxpts = std::max(maxpts, (int)pts);
