@@ -451,18 +451,17 @@ __global__ void k_argmax(Dev D, int buf) {
 }
 
 // ----------------------------------------------------------------------------- Vandermonde RHS / residual
-// rhs: b_i = sum_{k in I_n} conj(z_i^k) f(k);  resid: ||sum_j c_j z_j^k - f(k)||^2.
-// z_i^k = prod_l E_l[i][k_l] with E_l[i][x] = exp(-+2 pi i t_i(l) x) built by an FP64 recurrence
-// once per block and kept in shared memory rounded to FP32; each term is formed in FP32 and
-// summed in FP64.  A term carries a relative error of a few u32 and the errors of the N terms
-// add up like a random walk, so b is accurate to ~u32 / sqrt(N) of its size; the residual to
-// ~u32 |f|.  Blocks take RHS_ROWS rows of one problem; for b, the threads split into m groups
-// (one term each) that share the block's rows, for the residual each thread takes rows.
+// rhs: b_i = sum_{k in I_n} conj(z_i^k) f(k);  resid: ||sum_j c_j z_j^k - f(k)||^2, all in FP64
+// (the normal equations square the condition of A: nodes closer than 1/n, as in the Section 5
+// workloads, need b to full FP64 accuracy).  z_i^k = prod_l E_l[i][k_l] with E_l[i][x] =
+// exp(-+2 pi i t_i(l) x) from an FP64 recurrence, built once per block of RHS_ROWS rows.  For b,
+// the threads split into m groups (one term each) that share the block's rows; for the
+// residual each thread takes rows.
 constexpr int RHS_ROWS = 1024;
 constexpr int RHS_TABLE_MAX = 6144;          // d m (n + 1) (checked when a problem is accepted)
 
 __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
-  extern __shared__ float2 tabf[];   // [d][m][n+1] powers, then RHS_ROWS samples f, then [d][RHS_ROWS] digits
+  extern __shared__ double2 tab[];   // [d][m][n+1] powers, then [d][RHS_ROWS] digits (16-bit)
   __shared__ double2 part[256];
   __shared__ double shr[32];
   const int pi = blockIdx.y;
@@ -474,9 +473,7 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
   if (r0 >= p.N) return;
   const int nrows = min(RHS_ROWS, p.N - r0);
   const int n1 = p.n + 1;
-  const int tsize = p.d * m * n1;
-  float2* fs = tabf + tsize;
-  int* kd = (int*)(fs + RHS_ROWS);                 // kd[l * RHS_ROWS + rr]: digit l of row rr
+  short* kd = (short*)(tab + RHS_TABLE_MAX);       // kd[l * RHS_ROWS + rr]: digit l of row rr (n < 6144)
   const double* t = (const double*)(D.small + p.soff + D.L.t);
   const double2* c = (const double2*)(D.small + p.soff + D.L.c);
   const double sign = resid ? -1.0 : 1.0;
@@ -494,41 +491,39 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
       e1 = make_double2(cs, sign * sn);
     }
     double2 e = make_double2(1.0, 0.0);
-    float2* row = tabf + ((size_t)l * m + i) * n1;
+    double2* row = tab + ((size_t)l * m + i) * n1;
     for (int x = 0; x < n1; ++x) {
-      row[x] = make_float2((float)e.x, (float)e.y);
+      row[x] = e;
       e = cmul(e, e1);
     }
   }
   for (int rr = threadIdx.x; rr < nrows; rr += blockDim.x) {
-    int rem = r0 + rr, gi = 0, mul = 1;
+    int rem = r0 + rr;
     for (int l = p.d - 1; l >= 0; --l) {
-      const int k = rem % n1;
+      kd[l * RHS_ROWS + rr] = (short)(rem % n1);
       rem /= n1;
-      gi += (k + p.n) * mul;
-      mul *= p.G;
-      kd[l * RHS_ROWS + rr] = k;
     }
-    const double2 f = D.grid64[p.grid + gi];
-    fs[rr] = make_float2((float)f.x, (float)f.y);
   }
   __syncthreads();
   auto power = [&](int i, int rr) {
-    float2 e = tabf[(size_t)i * n1 + kd[rr]];
-    for (int l = 1; l < p.d; ++l) e = cmulf(e, tabf[((size_t)l * m + i) * n1 + kd[l * RHS_ROWS + rr]]);
+    double2 e = tab[(size_t)i * n1 + kd[rr]];
+    for (int l = 1; l < p.d; ++l) e = cmul(e, tab[((size_t)l * m + i) * n1 + kd[l * RHS_ROWS + rr]]);
     return e;
+  };
+  auto sample = [&](int rr) {
+    int gi = 0, mul = 1;
+    for (int l = p.d - 1; l >= 0; --l) {
+      gi += (kd[l * RHS_ROWS + rr] + p.n) * mul;
+      mul *= p.G;
+    }
+    return D.grid64[p.grid + gi];
   };
   if (!resid) {
     const int tpi = blockDim.x / m;                 // threads per term (m <= 64: at least 4)
     const int i = threadIdx.x / tpi, q = threadIdx.x % tpi;
     double2 acc = make_double2(0.0, 0.0);
-    if (i < m) {
-      for (int rr = q; rr < nrows; rr += tpi) {
-        const float2 v = cmulf(power(i, rr), fs[rr]);
-        acc.x += (double)v.x;
-        acc.y += (double)v.y;
-      }
-    }
+    if (i < m)
+      for (int rr = q; rr < nrows; rr += tpi) acc = cadd(acc, cmul(power(i, rr), sample(rr)));
     part[threadIdx.x] = acc;
     __syncthreads();
     double2* b = (double2*)(D.small + p.soff + D.L.rhs);
@@ -541,14 +536,10 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
   } else {
     double r2 = 0.0;
     for (int rr = threadIdx.x; rr < nrows; rr += blockDim.x) {
-      float2 v = make_float2(-fs[rr].x, -fs[rr].y);
-      for (int i = 0; i < m; ++i) {
-        const float2 ci = make_float2((float)c[i].x, (float)c[i].y);
-        const float2 e = cmulf(ci, power(i, rr));
-        v.x += e.x;
-        v.y += e.y;
-      }
-      r2 += (double)v.x * v.x + (double)v.y * v.y;
+      const double2 f = sample(rr);
+      double2 v = make_double2(-f.x, -f.y);
+      for (int i = 0; i < m; ++i) v = cadd(v, cmul(c[i], power(i, rr)));
+      r2 += cabs2(v);
     }
     double tot = block_sum(r2, shr);
     if (threadIdx.x == 0) atomicAdd(&s.ls_num2, tot);
@@ -750,7 +741,7 @@ void launch_argmax(const Dev& D, int buf, cudaStream_t s) {
 
 void launch_rhs(const Dev& D, int resid, cudaStream_t s) {
   static bool attr = false;
-  const size_t sm = sizeof(float2) * (RHS_TABLE_MAX + RHS_ROWS) + sizeof(int) * PRONY_DMAX * RHS_ROWS;
+  const size_t sm = sizeof(double2) * RHS_TABLE_MAX + sizeof(short) * PRONY_DMAX * RHS_ROWS;
   if (!attr) {
     cudaFuncSetAttribute(k_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;

@@ -525,7 +525,11 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   const double tol_rank = o.tol_rank > 0 ? o.tol_rank : 1e-3;
   const double tol_power = o.tol_power > 0 ? o.tol_power : default_tol_power(prec);
   const int max_iter = o.max_iter > 0 ? o.max_iter : 30;
-  const double tol_drop = 1e-3;
+  // columns of T V whose CholeskyQR pivot falls below tol_drop^2 of the largest are dropped (the
+  // noise of FP32 data); never above the rank tolerance, so that a term the rank test keeps
+  // (sigma_m / sigma_1 >= tol_rank) is not lost first, and never below the FP32 resolution of the
+  // Gram (3e-4 on singular-value ratios)
+  const double tol_drop = std::min(1e-3, std::max(tol_rank, 3e-4));
   const double tol_lanczos = tol_rank;   // alpha, beta <= tol ||T||_F stop Algorithm 2 (Section 2.1)
 
   // Toeplitz launch, bracketed by events when profiling
