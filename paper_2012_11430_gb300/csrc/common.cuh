@@ -316,6 +316,9 @@ void launch_refine_lm(double* t, double2* c, int m, int d, const int* lo, const 
 constexpr int LM_LAUNCHES_PER_STEP = 4;
 
 // kernels_lanczos.cu (Algorithm 2, batched)
+// kernels_small.cu: condition node of the device-side power loop (CUDA graph WHILE node)
+void launch_loop_cond(cudaGraphConditionalHandle h, const int* all_done, int* count, int cap, cudaStream_t s);
+
 // kernels_fft.cu (Toeplitz products by circulant embedding and FP32 FFTs)
 int fft_length(int n);
 long long fft_points_host(int n, int d);   // points of one embedded grid in shared memory (padded)

@@ -401,3 +401,17 @@ void launch_check(const Dev& D, double tol_power, int max_iter, int* all_done, c
   note_launch();
   k_check<<<(D.nprob + 127) / 128, 128, 0, s>>>(D, tol_power, max_iter, all_done);
 }
+
+namespace {
+// Condition of the device-side power loop: run the body again while some problem iterates and
+// fewer than `cap` bodies ran (the cap bounds the loop whatever the flags say).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* all_done, int* count, int cap) {
+  const int c = ++(*count);
+  cudaGraphSetConditional(h, (*all_done == 0 && c < cap) ? 1u : 0u);
+}
+}  // namespace
+
+void launch_loop_cond(cudaGraphConditionalHandle h, const int* all_done, int* count, int cap, cudaStream_t s) {
+  note_launch();
+  k_loop_cond<<<1, 1, 0, s>>>(h, all_done, count, cap);
+}

@@ -88,6 +88,10 @@ struct prony_ctx {
     double lambda0;
   } lm_key{};
   cudaGraphExec_t lm_exec = nullptr;
+  // device-side power loop (iterations 2..max_iter) of the last batch layout, and its key
+  std::string loop_key;
+  cudaGraphExec_t loop_exec = nullptr;
+  int loop_body_launches = 0;
 };
 
 namespace {
@@ -518,6 +522,85 @@ struct RunOut {
   int want_S = 0;
 };
 
+// Key of everything a captured power-loop graph bakes in: the device layout (pointers, sizes),
+// the problem descriptors, the product configuration and the tolerances.
+std::string loop_graph_key(const Batch& B, const int* dflag, int cap, double tol_drop, double tol_power) {
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  put(&B.D, sizeof(Dev));
+  put(B.P.data(), sizeof(ProbDesc) * B.P.size());
+  const TcConf& T = B.tc;
+  const long long tc[] = {T.on, T.kind, T.ntbox, T.stages, T.win_cap, T.nks, T.cs, T.prob_stride, T.njobs_ext,
+                          T.njobs_in, (long long)(size_t)T.jobs_ext, (long long)(size_t)T.jobs_in,
+                          (long long)(size_t)T.err, B.fft.on, B.fft.maxpts, B.njobs_ext, B.njobs_in, B.nks,
+                          B.maxw, (long long)(size_t)B.jobs_ext, (long long)(size_t)B.jobs_in,
+                          (long long)(size_t)dflag, cap};
+  put(tc, sizeof(tc));
+  put(&tol_drop, sizeof(double));
+  put(&tol_power, sizeof(double));
+  return k;
+}
+
+// Iterations 2..cap+1 of the power loop on the device: a graph with a WHILE node whose body is
+// one iteration followed by the condition kernel; captured once per batch layout, replayed after.
+template <typename Body>
+int power_loop_graph(prony_ctx* ctx, const Batch& B, Body& iteration, int* dflag, int cap, double tol_drop,
+                     double tol_power, cudaStream_t s) {
+  int* count = (int*)ctx->flag.p + 1;            // body executions of this launch
+  const std::string key = loop_graph_key(B, dflag, cap, tol_drop, tol_power);
+  if (!ctx->loop_exec || key != ctx->loop_key) {
+    if (ctx->loop_exec) {
+      cudaGraphExecDestroy(ctx->loop_exec);
+      ctx->loop_exec = nullptr;
+    }
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaMemsetParams mp = {};
+    mp.dst = count;
+    mp.value = 0;
+    mp.elementSize = sizeof(int);
+    mp.width = 1;
+    mp.height = 1;
+    cudaGraphNode_t mnode, cnode;
+    CK(cudaGraphAddMemsetNode(&mnode, g, nullptr, 0, &mp));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CK(cudaGraphAddNode(&cnode, g, &mnode, nullptr, 1, &cp));
+    const long long before = g_launches.load();
+    CK(cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    int rc = iteration(2);
+    launch_loop_cond(h, dflag, count, cap, s);
+    cudaGraph_t body;
+    const cudaError_t ce = cudaStreamEndCapture(s, &body);
+    ctx->loop_body_launches = (int)(g_launches.load() - before);
+    note_launches(-ctx->loop_body_launches);      // counted when the body runs (below)
+    if (rc || ce != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return rc ? rc : cuda_fail(ce, "cudaStreamEndCapture");
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->loop_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      ctx->loop_exec = nullptr;
+      return cuda_fail(ie, "cudaGraphInstantiate");
+    }
+    ctx->loop_key = key;
+  }
+  CK(cudaGraphLaunch(ctx->loop_exec, s));
+  // launches of this call: the body's kernels times the bodies run
+  int runs = 0;
+  CK(cudaMemcpyAsync(&runs, count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  note_launches((long long)runs * ctx->loop_body_launches);
+  return PRONY_OK;
+}
+
 int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   cudaStream_t s = ctx->stream;
   const Dev& D = B.D;
@@ -599,7 +682,8 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     ctx->snaps.emplace_back(D.nprob);
     CK(cudaMemcpyAsync(ctx->snaps.back().data(), D.st, sizeof(ProbState) * D.nprob, cudaMemcpyDeviceToHost, s));
   }
-  for (int it = 1; it <= max_iter; ++it) {
+  // one power iteration (Algorithm 3); dflag ends nonzero when every problem has stopped
+  auto iteration = [&](int it) -> int {
     // U = qr(T V_{k-1})  (rows I_n of Y)
     tall_qr(B, BUF_Y, W_V, W_U, QR_DROP, tol_drop, 0, BUF_U, s);
     // Vbar = T^* U
@@ -615,6 +699,10 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     launch_apply(D, BUF_U, W_U, W_V, D.L.q, 1, BUF_Y, -1, 1, s);
     CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
     launch_check(D, tol_power, max_iter, dflag, s);
+    return PRONY_OK;
+  };
+  for (int it = 1; it <= max_iter; ++it) {
+    if ((rc = iteration(it))) return rc;
     CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     if (ctx->prof) {
       ctx->snaps.emplace_back(D.nprob);
@@ -622,6 +710,12 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     }
     CK(cudaStreamSynchronize(s));
     if (*ctx->h_flag != 0) break;
+    if (it == 1 && !ctx->prof && max_iter > 1) {
+      // iterations 2.. as one CUDA graph: a WHILE node whose body is one iteration and whose
+      // condition kernel reads dflag on the device -- no host round trip per iteration
+      if ((rc = power_loop_graph(ctx, B, iteration, dflag, max_iter - 1, tol_drop, tol_power, s))) return rc;
+      break;
+    }
   }
   if (ctx->prof) {
     // accumulate durations and algorithmic work of the Toeplitz launches of this solve
@@ -817,6 +911,7 @@ int prony_ctx_destroy(prony_ctx* c) {
                   &c->st, &c->jobs, &c->flag, &c->tout, &c->cout, &c->misc, &c->misc2, &c->misc3,
                   &c->xb, &c->tabF, &c->tabH, &c->tcjobs, &c->tcerr, &c->lmws};
   if (c->lm_exec) cudaGraphExecDestroy(c->lm_exec);
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->h_flag) cudaFreeHost(c->h_flag);
