@@ -62,3 +62,34 @@ def test_ctx_create_without_device_reports_error(lib):
 def test_built_for_sm103a():
     from paper_2012_11430_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of prony_opts / prony_info / prony_stats have the C layout: sizes and
+    field offsets printed by a C program compiled against include/prony.h."""
+    import shutil
+    import subprocess
+    from paper_2012_11430_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"prony_opts": binding.PronyOpts, "prony_info": binding.PronyInfo, "prony_stats": binding.PronyStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "prony.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('  printf("enum PRONY_FFT32 %d\\n", (int)PRONY_FFT32);')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+    assert got[("enum", "PRONY_FFT32")] == binding.PRONY_FFT32
