@@ -88,10 +88,12 @@ struct prony_ctx {
     double lambda0;
   } lm_key{};
   cudaGraphExec_t lm_exec = nullptr;
-  // device-side power loop (iterations 2..max_iter) of the last batch layout, and its key
-  std::string loop_key;
-  cudaGraphExec_t loop_exec = nullptr;
-  int loop_body_launches = 0;
+  // device-side loops (0: power iterations 2.., 1: Lanczos steps) of the last batch layout
+  struct LoopGraph {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    int body_launches = 0;
+  } loops[2];
 };
 
 namespace {
@@ -522,9 +524,9 @@ struct RunOut {
   int want_S = 0;
 };
 
-// Key of everything a captured power-loop graph bakes in: the device layout (pointers, sizes),
-// the problem descriptors, the product configuration and the tolerances.
-std::string loop_graph_key(const Batch& B, const int* dflag, int cap, double tol_drop, double tol_power) {
+// Key of everything a captured loop graph bakes in: the device layout (pointers, sizes), the
+// problem descriptors, the product configuration and the loop's own parameters.
+std::string loop_graph_key(const Batch& B, const int* dflag, int cap, const double* params, int nparams) {
   std::string k;
   auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
   put(&B.D, sizeof(Dev));
@@ -536,22 +538,21 @@ std::string loop_graph_key(const Batch& B, const int* dflag, int cap, double tol
                           B.maxw, (long long)(size_t)B.jobs_ext, (long long)(size_t)B.jobs_in,
                           (long long)(size_t)dflag, cap};
   put(tc, sizeof(tc));
-  put(&tol_drop, sizeof(double));
-  put(&tol_power, sizeof(double));
+  put(params, sizeof(double) * nparams);
   return k;
 }
 
-// Iterations 2..cap+1 of the power loop on the device: a graph with a WHILE node whose body is
-// one iteration followed by the condition kernel; captured once per batch layout, replayed after.
-template <typename Body>
-int power_loop_graph(prony_ctx* ctx, const Batch& B, Body& iteration, int* dflag, int cap, double tol_drop,
-                     double tol_power, cudaStream_t s) {
-  int* count = (int*)ctx->flag.p + 1;            // body executions of this launch
-  const std::string key = loop_graph_key(B, dflag, cap, tol_drop, tol_power);
-  if (!ctx->loop_exec || key != ctx->loop_key) {
-    if (ctx->loop_exec) {
-      cudaGraphExecDestroy(ctx->loop_exec);
-      ctx->loop_exec = nullptr;
+// A loop on the device: a graph with a WHILE node whose body is one step (enqueued by `step`,
+// which leaves dflag nonzero once every problem has stopped) followed by the condition kernel,
+// capped at `cap` bodies.  Captured once per key into the context's slot, replayed after.
+template <typename Step>
+int device_loop(prony_ctx* ctx, int slot, const std::string& key, Step& step, int* dflag, int cap, cudaStream_t s) {
+  auto& L = ctx->loops[slot];
+  int* count = (int*)ctx->flag.p + 1 + slot;     // bodies run by this launch
+  if (!L.exec || key != L.key) {
+    if (L.exec) {
+      cudaGraphExecDestroy(L.exec);
+      L.exec = nullptr;
     }
     cudaGraph_t g;
     CK(cudaGraphCreate(&g, 0));
@@ -574,30 +575,29 @@ int power_loop_graph(prony_ctx* ctx, const Batch& B, Body& iteration, int* dflag
     const long long before = g_launches.load();
     CK(cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                      cudaStreamCaptureModeRelaxed));
-    int rc = iteration(2);
+    int rc = step();
     launch_loop_cond(h, dflag, count, cap, s);
     cudaGraph_t body;
     const cudaError_t ce = cudaStreamEndCapture(s, &body);
-    ctx->loop_body_launches = (int)(g_launches.load() - before);
-    note_launches(-ctx->loop_body_launches);      // counted when the body runs (below)
+    L.body_launches = (int)(g_launches.load() - before);
+    note_launches(-L.body_launches);               // counted when the bodies run (below)
     if (rc || ce != cudaSuccess) {
       cudaGraphDestroy(g);
       return rc ? rc : cuda_fail(ce, "cudaStreamEndCapture");
     }
-    const cudaError_t ie = cudaGraphInstantiate(&ctx->loop_exec, g, 0);
+    const cudaError_t ie = cudaGraphInstantiate(&L.exec, g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) {
-      ctx->loop_exec = nullptr;
+      L.exec = nullptr;
       return cuda_fail(ie, "cudaGraphInstantiate");
     }
-    ctx->loop_key = key;
+    L.key = key;
   }
-  CK(cudaGraphLaunch(ctx->loop_exec, s));
-  // launches of this call: the body's kernels times the bodies run
+  CK(cudaGraphLaunch(L.exec, s));
   int runs = 0;
   CK(cudaMemcpyAsync(&runs, count, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  note_launches((long long)runs * ctx->loop_body_launches);
+  note_launches((long long)runs * L.body_launches);
   return PRONY_OK;
 }
 
@@ -655,7 +655,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
         launch_apply(D, basis, wsel, W_ONE, D.L.work1, 1, BUF_B2, BUF_B2, 0, s);
       }
     };
-    for (int step = 0; step < cap; ++step) {
+    auto lz_step = [&]() -> int {
       launch_lz_load(D, 0, s);                                       // v_k
       toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, 0);   // T v_k
       launch_lz_axpy(D, 0, s);                                       // - beta_k u_{k-1}
@@ -668,9 +668,19 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
       launch_lz_accept(D, 1, tol_lanczos, cap, s);                   // beta_{k+1}, v_{k+1}
       CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
       launch_lz_all_done(D, dflag, s);
-      CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (*ctx->h_flag != 0) break;
+      return PRONY_OK;
+    };
+    if (ctx->prof) {
+      for (int step = 0; step < cap; ++step) {
+        if ((rc = lz_step())) return rc;
+        CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (*ctx->h_flag != 0) break;
+      }
+    } else {
+      // the steps as one CUDA graph with a device-side WHILE loop (no host round trip per step)
+      const double par[] = {tol_lanczos, (double)prec};
+      if ((rc = device_loop(ctx, 1, loop_graph_key(B, dflag, cap, par, 2), lz_step, dflag, cap, s))) return rc;
     }
     launch_lz_finish(D, s);
   } else {
@@ -713,7 +723,10 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     if (it == 1 && !ctx->prof && max_iter > 1) {
       // iterations 2.. as one CUDA graph: a WHILE node whose body is one iteration and whose
       // condition kernel reads dflag on the device -- no host round trip per iteration
-      if ((rc = power_loop_graph(ctx, B, iteration, dflag, max_iter - 1, tol_drop, tol_power, s))) return rc;
+      const double par[] = {tol_drop, tol_power, (double)prec};
+      auto body = [&]() -> int { return iteration(2); };
+      if ((rc = device_loop(ctx, 0, loop_graph_key(B, dflag, max_iter - 1, par, 3), body, dflag, max_iter - 1, s)))
+        return rc;
       break;
     }
   }
@@ -911,7 +924,8 @@ int prony_ctx_destroy(prony_ctx* c) {
                   &c->st, &c->jobs, &c->flag, &c->tout, &c->cout, &c->misc, &c->misc2, &c->misc3,
                   &c->xb, &c->tabF, &c->tabH, &c->tcjobs, &c->tcerr, &c->lmws};
   if (c->lm_exec) cudaGraphExecDestroy(c->lm_exec);
-  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  for (auto& l : c->loops)
+    if (l.exec) cudaGraphExecDestroy(l.exec);
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->h_flag) cudaFreeHost(c->h_flag);
