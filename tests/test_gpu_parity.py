@@ -567,3 +567,35 @@ def test_table_accuracy_noise_sweep_gpu(ctx):
     res = ctx.solve(_paper_noise(P, 1e-3), 3, 20, 5, default_opts(precision="bf16x3", tol_rank=1e-3),
                     allow=(PRONY_ERANK,))
     assert res.info["rank_detected"] == tab["rank_eps1e-3_tol1e-3"] == 4 and res.info["status"] == PRONY_ERANK
+
+
+# ------------------------------------------------------------------ full sizes, bench launch configuration
+def _full_batch_check(ctx, probs, sample, snr_db):
+    """One batched call at full size (the launch configuration the bench times); the sampled
+    problems against the FP64 oracle (forward error within 1.5x + 1e-6), every problem against
+    properties that hold at any size: status OK, m terms, and a least-squares residual no worse
+    than twice the noise amplitude (a misplaced node leaves a residual of the order of |c|)."""
+    from paper_2012_11430_gb300 import default_opts
+    outs, rc = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
+                                 [p.m for p in probs], default_opts())
+    assert rc == 0
+    amp = 10.0 ** (-snr_db / 20.0)
+    for p, r in zip(probs, outs):
+        assert r.info["status"] == 0 and r.info["rank_used"] == p.m, (p.name, r.info)
+        assert r.info["ls_resid"] <= 2.0 * amp, (p.name, r.info["ls_resid"], amp)
+    for i in sample:
+        p, r = probs[i], outs[i]
+        t_o, c_o, _ = O.prony(p.grid, p.d, p.n, p.m, svd="power", tol_power=1e-13)
+        te_g, ce_g = W.match_to_truth(r.t, r.c, p.t, p.c)
+        te_o, ce_o = W.match_to_truth(t_o, c_o, p.t, p.c)
+        assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (p.name, te_g, te_o, ce_g, ce_o)
+
+
+def test_full_size_C4_batch(ctx):
+    probs = W.batch_problems(4096)
+    _full_batch_check(ctx, probs, sample=range(0, 4096, 512), snr_db=30.0)
+
+
+def test_full_size_C2_batch152(ctx):
+    probs = [W.config_problem("C2", seed_offset=i) for i in range(152)]
+    _full_batch_check(ctx, probs, sample=(0, 151), snr_db=40.0)
