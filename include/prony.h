@@ -58,8 +58,9 @@ typedef enum {
  *   PRONY_BF16X2 : BF16 hi+lo split, three tensor-core products.
  *   PRONY_FFT32  : no dense product: T embedded in a circulant of L^d points (L the power of
  *                  two >= 2n+2), FP32 FFTs in shared memory, O(L^d log L) per column instead
- *                  of O(N^2).  Needs L^(d-1) (L+1) + L <= 128 * 130 for every problem of the
- *                  call (d = 1: n <= 4095; d = 2: n <= 63; d = 3: n <= 7), else PRONY_EINVAL. */
+ *                  of O(N^2).  Needs d <= 3 and L^(d-1) (L+1) + L <= 128 * 130 for every
+ *                  problem of the call (d = 1: n <= 4095; d = 2: n <= 63; d = 3: n <= 7), else
+ *                  PRONY_EINVAL. */
 typedef enum { PRONY_FP32 = 0, PRONY_BF16X3 = 1, PRONY_TF32X3 = 2, PRONY_BF16X2 = 3, PRONY_FFT32 = 4 } prony_precision;
 
 typedef struct {
@@ -102,7 +103,8 @@ int prony_ctx_create(prony_ctx** ctx, int device);
 int prony_ctx_destroy(prony_ctx* ctx);
 
 /* Algorithm 1 for one problem.  samples: (2n+2)^d grid (see above).  d >= 1,
- * n >= 1, 1 <= m <= (n+1)^d, m <= 64.  opts may be NULL (defaults).
+ * n >= 1, 1 <= m <= (n+1)^d, m <= 64, d m (n+1) <= 6144 (the phase tables of the right-hand
+ * side), (n+1)^d <= 2e8, else PRONY_EINVAL.  opts may be NULL (defaults).
  * Outputs: t_out[m*d] (row j = t_j, components in [0,1)), c_out[m]; the pairs
  * are sorted lexicographically by t.  info may be NULL. */
 int prony_solve(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m,

@@ -75,7 +75,7 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
 // The line set of one axis: nl lines of L points at element stride es.  A line is fixed by its
 // coordinates on the other axes (no = d - 1 of them, slowest first, extents ext, strides str):
 // those before the transformed axis run below E (pruning), those after it over [0, L).
-struct Lines {
+struct Lines {                                    // d <= 3 (checked when the batch is set up)
   int nl, es, no;
   int ext[2], str[2];
   __device__ int base(int li) const {

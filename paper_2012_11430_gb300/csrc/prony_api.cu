@@ -384,7 +384,7 @@ int setup_fft(prony_ctx* ctx, Batch& B) {
   for (auto& p : B.P) {
     p.fL = fft_length(p.n);
     const long long pts = fft_points_host(p.n, p.d);
-    if (pts + p.fL > FFT_MAX_POINTS) return PRONY_EINVAL;
+    if (p.d > 3 || pts + p.fL > FFT_MAX_POINTS) return PRONY_EINVAL;   // line sets cover d <= 3
     p.foff = foff;
     foff += pts;
     maxpts = std::max(maxpts, (int)pts);

@@ -94,8 +94,10 @@ def test_eval_matches_expsum(ctx):
 
 
 def _check_solution(res, t_ref, c_ref, t_tol=1e-6, c_tol=1e-5):
-    t_err = float(np.max(W.torus_dist(res.t, t_ref))) if len(t_ref) else 0.0
-    c_err = float(np.linalg.norm(res.c - c_ref) / np.linalg.norm(c_ref))
+    """(t, c) against a reference, nodes paired by minimum torus distance (a node within rounding
+    of the wrap 0 = 1 sorts first on one side and last on the other, so sorted lists may not
+    line up)."""
+    t_err, c_err = W.match_to_truth(res.t, res.c, t_ref, c_ref) if len(t_ref) else (0.0, 0.0)
     assert t_err <= t_tol and c_err <= c_tol, (t_err, c_err, res.info)
 
 
@@ -599,3 +601,29 @@ def test_full_size_C4_batch(ctx):
 def test_full_size_C2_batch152(ctx):
     probs = [W.config_problem("C2", seed_offset=i) for i in range(152)]
     _full_batch_check(ctx, probs, sample=(0, 151), snr_db=40.0)
+
+
+# ------------------------------------------------------------------ maximum sizes
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32x3", "fft32"])
+@pytest.mark.parametrize("name,d,n,m,seed", [
+    ("m64", 2, 31, 64, 4242),       # m = PRONY_MMAX, r0 = 2m = 128 = PRONY_RMAX (the widest blocks)
+    ("d4", 4, 3, 3, 4343),          # d = PRONY_DMAX
+    ("d4b", 4, 4, 5, 4344),
+    ("d1long", 1, 700, 8, 4345),    # long one-dimensional signal (d m (n + 1) <= 6144)
+])
+def test_maximum_sizes(ctx, prec, name, d, n, m, seed):
+    """Noise-free recovery at the limits of the boundary: the most terms (64, blocks of 128
+    columns), the highest dimension (4) and a long 1-D signal.  The FFT products cover d <= 3 and
+    refuse d = 4 with PRONY_EINVAL."""
+    from paper_2012_11430_gb300 import PronyError, PRONY_EINVAL, default_opts
+    P = W.make_problem(name, d, n, m, seed)
+    opts = default_opts(precision=prec)
+    if prec == "fft32" and d == 4:
+        with pytest.raises(PronyError) as e:
+            ctx.solve(P.grid, d, n, m, opts)
+        assert e.value.code == PRONY_EINVAL
+        return
+    res = ctx.solve(P.grid, d, n, m, opts)
+    assert res.info["status"] == 0 and res.info["rank_used"] == m, res.info
+    order = np.lexsort(P.t.T[::-1])
+    _check_solution(res, P.t[order], P.c[order])
