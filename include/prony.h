@@ -125,7 +125,8 @@ int prony_build_S(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m
 int prony_eval(prony_ctx* ctx, const double* t, const prony_c128* c, int m, int d,
                const int* k, int K, prony_c128* f_out);
 
-/* Many independent problems of uneven (d, n, m).
+/* Many independent problems of uneven (d, n, m); P >= 1 (an empty batch is PRONY_EINVAL), each
+ * problem within the limits of prony_solve.
  * sample_off[p]: offset (in prony_c128) of problem p's grid inside `samples`;
  * out_off[p]: offset (in terms) of its results: t_out[(out_off[p]+j)*dmax + l] for
  * l < d[p] (dmax = the largest d of the call; entries l >= d[p] are left untouched),

@@ -183,7 +183,8 @@ def test_degenerate_inputs_fail_cleanly(ctx, prec):
 
 
 def test_invalid_arguments(ctx):
-    from paper_2012_11430_gb300 import PronyError
+    import ctypes
+    from paper_2012_11430_gb300 import PronyError, PRONY_EINVAL
     P = W.config_problem("C1")
     with pytest.raises(PronyError):
         ctx.solve(P.grid, 2, 15, 0)
@@ -191,6 +192,16 @@ def test_invalid_arguments(ctx):
         ctx.solve(P.grid, 2, 15, 65)
     with pytest.raises(ValueError):
         ctx.solve(P.grid, 2, 14, 5)
+    with pytest.raises(PronyError):                 # d m (n + 1) above the right-hand-side tables
+        g = np.zeros((2 * 1000 + 2,), dtype=np.complex128)
+        ctx.solve(g, 1, 1000, 8)
+    # an empty batch
+    z = np.zeros(1, dtype=np.int64)
+    rc = ctx._lib.prony_solve_batched(ctx._h, 0, z.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                                      z.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                                      P.grid.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                                      z.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p), None, None)
+    assert rc == PRONY_EINVAL
 
 
 def test_batched_matches_single_and_oracle(ctx):
