@@ -13,12 +13,14 @@
 #include "../../include/prony.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 #include <atomic>
 
@@ -80,6 +82,10 @@ struct prony_ctx {
   long long launch_base = 0;
   cudaError_t launch_err = cudaSuccess;   // first failed tensor-core launch of the current call
   std::map<std::string, std::pair<int, int>> tc_tuned;   // batch shape -> (cluster size, K split)
+  // the tensor-core job list on the device: (cs, nks, P, then n and d of every problem) it was
+  // built for, and its ext / in counts (a repeated batch layout skips the rebuild and the upload)
+  std::vector<int> tcjob_sig;
+  int tcjob_next = 0, tcjob_nin = 0;
   // refinement: workspace and the CUDA graph of the last argument set
   DBuf lmws;
   struct LmKey {
@@ -195,8 +201,34 @@ int max_window(const ProbDesc& p, int L, int nks) {
 
 // Job list of the tensor-core products for a cluster size and K split: per problem and K range,
 // its 128-row tiles padded to a multiple of the cluster size (mt >= tiles: filler CTA).
+// Grows the tensor-core job buffer; a reallocation invalidates the job list it held.
+static int ensure_tcjobs(prony_ctx* ctx, size_t bytes) {
+  const size_t cap = ctx->tcjobs.cap;
+  const int rc = ensure(ctx->tcjobs, bytes);
+  if (ctx->tcjobs.cap != cap) ctx->tcjob_sig.clear();
+  return rc;
+}
+
 int tc_set_jobs(prony_ctx* ctx, Batch& B, int cs, int nks) {
   TcConf& T = B.tc;
+  std::vector<int> sig;
+  sig.reserve(3 + 2 * B.P.size());
+  sig.push_back(cs);
+  sig.push_back(nks);
+  sig.push_back((int)B.P.size());
+  for (const auto& p : B.P) {
+    sig.push_back(p.n);
+    sig.push_back(p.d);
+  }
+  if (ctx->tcjobs.p && sig == ctx->tcjob_sig) {
+    T.njobs_ext = ctx->tcjob_next;
+    T.njobs_in = ctx->tcjob_nin;
+    T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
+    T.jobs_in = T.jobs_ext + T.njobs_ext;
+    T.cs = cs;
+    T.nks = nks;
+    return PRONY_OK;
+  }
   std::vector<ToeplitzJob> jobs;
   auto add_jobs = [&](bool ext) {
     for (int i = 0; i < (int)B.P.size(); ++i) {
@@ -212,9 +244,12 @@ int tc_set_jobs(prony_ctx* ctx, Batch& B, int cs, int nks) {
   add_jobs(false);
   T.njobs_in = (int)jobs.size() - T.njobs_ext;
   int rc;
-  if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
+  if ((rc = ensure_tcjobs(ctx, sizeof(ToeplitzJob) * jobs.size()))) return rc;
   CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
+  ctx->tcjob_sig = std::move(sig);
+  ctx->tcjob_next = T.njobs_ext;
+  ctx->tcjob_nin = T.njobs_in;
   T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
   T.jobs_in = T.jobs_ext + T.njobs_ext;
   T.cs = cs;
@@ -240,21 +275,59 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   // accumulator leaves free), leaving room for a window of the 2 npl split-plane tables of at
   // least 64 KB
   if (T.ntbox > 256) return PRONY_EINVAL;
-  T.stages = 4;
-  while (T.stages > 1 && 1024 + T.stages * stage + 64 * 1024 > avail) --T.stages;
-  T.win_cap = (int)((avail - 1024 - T.stages * stage) / (8 * npl)) & ~3;
-  if (T.win_cap < 256) return PRONY_EINVAL;
+  int st_max = 4;
+  while (st_max > 1 && 1024 + st_max * stage + 64 * 1024 > avail) --st_max;
+  auto win_cap_for = [&](int st) { return (int)((avail - 1024 - st * stage) / (8 * npl)) & ~3; };
   // split K: enough CTAs to fill the GPU, and every window within the shared-memory capacity
-  int nks = std::max(1, std::min(16, (2 * 152 + tiles_in - 1) / std::max(1, tiles_in)));
-  nks = std::max(nks, (maxnc + 511) / 512);        // at most 512 K chunks per CTA
-  for (;; ++nks) {
-    bool fits = true;
-    for (const auto& p : B.P) {
-      nks = std::min(nks, std::max(1, (p.N + 31) / 32));
-      if (max_window(p, p.n + 2, nks) > T.win_cap || max_window(p, p.n + 1, nks) > T.win_cap) fits = false;
+  int nks_lo = std::max(1, std::min(16, (2 * 152 + tiles_in - 1) / std::max(1, tiles_in)));
+  nks_lo = std::max(nks_lo, (maxnc + 511) / 512);  // at most 512 K chunks per CTA
+  // largest window of a problem shape (it depends on n, d and the split only), computed once per
+  // shape of the batch
+  std::map<std::pair<int, int>, int> shapes;          // (n, d) -> a problem of that shape
+  for (int i = 0; i < (int)B.P.size(); ++i) shapes.emplace(std::make_pair(B.P[i].n, B.P[i].d), i);
+  std::map<std::tuple<int, int, int>, int> wmemo;      // (problem, nks, ext) -> window words
+  auto window_of = [&](int i, int nks, int ext) {
+    auto key = std::make_tuple(i, nks, ext);
+    auto it = wmemo.find(key);
+    if (it != wmemo.end()) return it->second;
+    const ProbDesc& p = B.P[i];
+    const int wl = max_window(p, ext ? p.n + 2 : p.n + 1, nks);
+    wmemo.emplace(key, wl);
+    return wl;
+  };
+  auto split_for = [&](int cap) {
+    int nks = nks_lo;
+    for (;; ++nks) {
+      bool fits = true;
+      for (const auto& sh : shapes) {
+        const ProbDesc& p = B.P[sh.second];
+        nks = std::min(nks, std::max(1, (p.N + 31) / 32));
+        if (window_of(sh.second, nks, 1) > cap || window_of(sh.second, nks, 0) > cap) fits = false;
+      }
+      if (fits || nks >= maxnc) break;
     }
-    if (fits || nks >= maxnc) break;
+    return nks;
+  };
+  // Fewer B stages leave room for a longer window and so may allow a smaller split: fewer CTAs,
+  // each of which pays its window load and its epilogue once.  The stage count is the largest
+  // (from st_max down to two) that reaches the smallest split.
+  int st_min = std::min(st_max, 2);
+  if (const char* e = getenv("PRONY_TC_BSTAGES")) {   // tuning override: exactly this many B stages
+    const int v = atoi(e);
+    if (v >= 1) st_max = st_min = std::min(v, st_max);
   }
+  int nks = INT_MAX;
+  T.stages = st_max;
+  for (int st = st_max; st >= st_min; --st) {
+    if (win_cap_for(st) < 256) continue;
+    const int k = split_for(win_cap_for(st));
+    if (k < nks) {
+      nks = k;
+      T.stages = st;
+    }
+  }
+  if (nks == INT_MAX) return PRONY_EINVAL;
+  T.win_cap = win_cap_for(T.stages);
   T.nks_min = nks;
   T.prob_stride = tc_prob_stride(prec, T.ntbox, maxnc);
   // Cluster sizes: the CTAs of a cluster share the B' stages of one problem and K range; tiles
@@ -338,7 +411,7 @@ int tc_autotune(prony_ctx* ctx, Batch& B, const Dev& D, int prec, cudaStream_t s
   for (const auto& p : B.P)
     maxjobs += (size_t)2 * T.nks_min * ((p.Next + 127) / 128 + 4 + (p.N + 127) / 128 + 4);
   int rc;
-  if ((rc = ensure(ctx->tcjobs, sizeof(ToeplitzJob) * maxjobs))) return rc;
+  if ((rc = ensure_tcjobs(ctx, sizeof(ToeplitzJob) * maxjobs))) return rc;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -448,12 +521,14 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
   int nks = (int)std::max<long long>(1, std::min<long long>(304 / std::max<long long>(1, tiles_in), 16));
   nks = std::min(nks, std::max(1, maxN / 64));
   B.nks = nks;
+  // job list of the FP32 CUDA-core products (the tensor-core and FFT paths build their own)
   std::vector<ToeplitzJob> jobs;
-  for (int i = 0; i < np; ++i)
+  const bool simt = o.precision == PRONY_FP32;
+  for (int i = 0; simt && i < np; ++i)
     for (int mt = 0; mt < (B.P[i].Next + 63) / 64; ++mt)
       for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
   B.njobs_ext = (int)jobs.size();
-  for (int i = 0; i < np; ++i)
+  for (int i = 0; simt && i < np; ++i)
     for (int mt = 0; mt < (B.P[i].N + 63) / 64; ++mt)
       for (int ks = 0; ks < nks; ++ks) jobs.push_back({i, mt, ks, nks});
   B.njobs_in = (int)jobs.size() - B.njobs_ext;
@@ -474,8 +549,9 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
   if ((rc = ensure(ctx->jobs, sizeof(ToeplitzJob) * jobs.size()))) return rc;
   if ((rc = ensure(ctx->flag, 256))) return rc;
   CK(cudaMemcpyAsync(ctx->P.p, B.P.data(), sizeof(ProbDesc) * np, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->jobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
-                     ctx->stream));
+  if (!jobs.empty())
+    CK(cudaMemcpyAsync(ctx->jobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
   CK(cudaMemsetAsync(ctx->small.p, 0, (size_t)L.bytes * np, ctx->stream));
   Dev& D = B.D;
   D.P = (const ProbDesc*)ctx->P.p;
