@@ -224,6 +224,7 @@ typedef struct {
   double toeplitz_bytes;     /* summed algorithmic bytes of those launches */
   int tc_cluster;            /* tensor-core path of the last batch: CTAs per cluster (0: not used) */
   int tc_ksplit;             /* and the K split of its products, as chosen by the autotuner */
+  int tc_bstages;            /* and its B' stages in shared memory (0: not used) */
 } prony_stats;
 
 int prony_set_profiling(prony_ctx* ctx, int enable);   /* also resets the statistics */

@@ -31,7 +31,8 @@ EXPORTS = [
 class PronyStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("toeplitz_launches", ctypes.c_longlong),
                 ("toeplitz_ms", ctypes.c_double), ("toeplitz_flops", ctypes.c_double),
-                ("toeplitz_bytes", ctypes.c_double), ("tc_cluster", ctypes.c_int), ("tc_ksplit", ctypes.c_int)]
+                ("toeplitz_bytes", ctypes.c_double), ("tc_cluster", ctypes.c_int), ("tc_ksplit", ctypes.c_int),
+                ("tc_bstages", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -837,6 +837,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
       }
       ctx->stats.tc_cluster = B.tc.on ? B.tc.cs : 0;
       ctx->stats.tc_ksplit = B.tc.on ? B.tc.nks : 0;
+      ctx->stats.tc_bstages = B.tc.on ? B.tc.stages : 0;
       ctx->stats.toeplitz_launches += 1;
       ctx->stats.toeplitz_ms += ms;
       ctx->stats.toeplitz_flops += fl;

@@ -614,6 +614,40 @@ def test_full_size_C2_batch152(ctx):
     _full_batch_check(ctx, probs, sample=(0, 151), snr_db=40.0)
 
 
+@pytest.mark.parametrize("env,expect", [
+    ({"PRONY_TC_BSTAGES": "4"}, {"tc_bstages": 4}), ({"PRONY_TC_BSTAGES": "2"}, {"tc_bstages": 2}),
+    ({"PRONY_TC_CLUSTER": "1"}, {"tc_cluster": 1}), ({"PRONY_TC_TUNE": "0"}, {}),
+])
+def test_tensor_core_sizing_overrides(ctx, monkeypatch, env, expect):
+    """Every launch configuration of the tensor-core products (B stages, cluster size, K split,
+    with or without the autotuner) solves the same C2 problems to the same forward error as the
+    default one (different FP32 summation orders only), and the statistics report the override."""
+    from paper_2012_11430_gb300 import default_opts
+    probs = [W.config_problem("C2", seed_offset=i) for i in range(12)]
+    args = ([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs], [p.m for p in probs],
+            default_opts(precision="bf16x3"))
+    base, rc = ctx.solve_batched(*args)
+    assert rc == 0
+    with monkeypatch.context() as mp:
+        for k, v in env.items():
+            mp.setenv(k, v)
+        ctx.set_profiling(True)
+        try:
+            outs, rc = ctx.solve_batched(*args)
+            st = ctx.stats()
+        finally:
+            ctx.set_profiling(False)
+    assert rc == 0
+    for k, v in expect.items():
+        assert st[k] == v, (k, st)
+    assert st["tc_bstages"] >= 1 and st["tc_ksplit"] >= 1 and st["tc_cluster"] >= 1, st
+    for p, a, b in zip(probs, base, outs):
+        assert b.info["status"] == 0 and b.info["rank_used"] == p.m, b.info
+        te_a, ce_a = W.match_to_truth(a.t, a.c, p.t, p.c)
+        te_b, ce_b = W.match_to_truth(b.t, b.c, p.t, p.c)
+        assert te_b <= 1.5 * te_a + 1e-6 and ce_b <= 1.5 * ce_a + 1e-6, (p.name, te_a, te_b, ce_a, ce_b)
+
+
 # ------------------------------------------------------------------ maximum sizes
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32x3", "fft32"])
 @pytest.mark.parametrize("name,d,n,m,seed", [
