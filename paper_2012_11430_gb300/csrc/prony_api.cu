@@ -151,7 +151,8 @@ struct Batch {
   int maxw = 0;
   TcConf tc;
   struct FftConf {
-    bool on = false;
+    bool on = false;  // every Toeplitz product by FFT (PRONY_FFT32)
+    bool lz = false;  // the single-column products of the Lanczos steps only (other precisions)
     int maxpts = 0;   // largest embedded grid of the batch (shared memory of one CTA, in points)
   } fft;
 };
@@ -450,6 +451,14 @@ int tc_autotune(prony_ctx* ctx, Batch& B, const Dev& D, int prec, cudaStream_t s
   return PRONY_OK;
 }
 
+// Whether every problem of the batch is within the FFT products' limits (d <= 3, one embedded
+// grid and its twiddles in a CTA's shared memory).
+bool fft_fits(const Batch& B) {
+  for (const auto& p : B.P)
+    if (p.d > 3 || fft_points_host(p.n, p.d) + fft_length(p.n) > FFT_MAX_POINTS) return false;
+  return true;
+}
+
 // FFT products: embedding length and transform offset of every problem, device tables.
 int setup_fft(prony_ctx* ctx, Batch& B) {
   long long foff = 0;
@@ -577,7 +586,16 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
   B.jobs_ext = (ToeplitzJob*)ctx->jobs.p;
   B.jobs_in = B.jobs_ext + B.njobs_ext;
   if (o.precision == PRONY_FFT32) return setup_fft(ctx, B);
-  if (is_tc(o.precision)) return setup_tc(ctx, B, o.precision, maxR0);
+  if (is_tc(o.precision) && (rc = setup_tc(ctx, B, o.precision, maxR0))) return rc;
+  if (o.svd_method == 1 && fft_fits(B)) {
+    // The Lanczos steps multiply by one column at a time: a tensor-core or CUDA-core product
+    // costs nearly as much for one column as for twenty (the tensor-core kernel is bound by its
+    // MMA issue, not by the width), an FFT product in proportion to its columns.  The Lanczos
+    // vectors only start the power loop, whose products keep the chosen precision.
+    if ((rc = setup_fft(ctx, B))) return rc;
+    B.fft.on = false;
+    B.fft.lz = true;
+  }
   return PRONY_OK;
 }
 
@@ -610,7 +628,7 @@ std::string loop_graph_key(const Batch& B, const int* dflag, int cap, const doub
   const TcConf& T = B.tc;
   const long long tc[] = {T.on, T.kind, T.ntbox, T.stages, T.win_cap, T.nks, T.cs, T.prob_stride, T.njobs_ext,
                           T.njobs_in, (long long)(size_t)T.jobs_ext, (long long)(size_t)T.jobs_in,
-                          (long long)(size_t)T.err, B.fft.on, B.fft.maxpts, B.njobs_ext, B.njobs_in, B.nks,
+                          (long long)(size_t)T.err, B.fft.on, B.fft.lz, B.fft.maxpts, B.njobs_ext, B.njobs_in, B.nks,
                           B.maxw, (long long)(size_t)B.jobs_ext, (long long)(size_t)B.jobs_in,
                           (long long)(size_t)dflag, cap};
   put(tc, sizeof(tc));
@@ -716,7 +734,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   }
   launch_prep(D, s);
   if (B.tc.on) launch_split_tables(D, B.tc.kind, s);
-  if (B.fft.on) launch_fft_tables(D, B.fft.maxpts, s);
+  if (B.fft.on || B.fft.lz) launch_fft_tables(D, B.fft.maxpts, s);
   launch_init_v0(D, o.seed, s);
   int* dflag = (int*)ctx->flag.p;
   if (o.svd_method == 1) {
@@ -731,14 +749,18 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
         launch_apply(D, basis, wsel, W_ONE, D.L.work1, 1, BUF_B2, BUF_B2, 0, s);
       }
     };
+    auto lz_product = [&](int adjoint) {                         // B2 = T B1 or T^* B1, one column
+      if (B.fft.lz) launch_toeplitz_fft(D, B.fft.maxpts, 1, adjoint, BUF_B1, W_ONE, BUF_B2, 0, s);
+      else toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, adjoint);
+    };
     auto lz_step = [&]() -> int {
       launch_lz_load(D, 0, s);                                       // v_k
-      toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, 0);   // T v_k
+      lz_product(0);                                                 // T v_k
       launch_lz_axpy(D, 0, s);                                       // - beta_k u_{k-1}
       reorth(BUF_U, W_LK);
       launch_lz_accept(D, 0, tol_lanczos, cap, s);                   // alpha_k, u_k
       launch_lz_load(D, 1, s);                                       // u_k
-      toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, 1);   // T^* u_k
+      lz_product(1);                                                 // T^* u_k
       launch_lz_axpy(D, 1, s);                                       // - alpha_k v_k
       reorth(BUF_V, W_LK1);
       launch_lz_accept(D, 1, tol_lanczos, cap, s);                   // beta_{k+1}, v_{k+1}

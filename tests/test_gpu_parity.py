@@ -395,7 +395,7 @@ def _lanczos_reference_steps(P, seed=1):
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("name,d,n,m,seed", [
     ("C1", 2, 15, 5, None), ("d1", 1, 12, 3, 5), ("d2rag", 2, 9, 7, 7), ("d3", 3, 5, 4, 8),
-    ("d2m12", 2, 23, 12, 10),
+    ("d2m12", 2, 23, 12, 10), ("d4", 4, 3, 3, 11),   # d = 4: Lanczos products at the chosen precision
 ])
 def test_lanczos_start_noise_free(ctx, prec, name, d, n, m, seed):
     """Algorithm 2 (Lanczos bidiagonalisation, full reorthogonalisation) as the subspace step:
