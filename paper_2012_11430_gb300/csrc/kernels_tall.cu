@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
   const int ntile = sym ? NA * (NA + 1) / 2 : NA * NB;
   const int nthr = blockDim.x;
   const int per_batch = min(ntile, nthr);
-  const int RG = max(1, min(8, nthr / per_batch));     // row groups (1 when tiles >= threads)
+  const int RG = max(1, min(RS, nthr / per_batch));    // row groups (1 when tiles >= threads)
   const int nbatch = (ntile + per_batch - 1) / per_batch;
   double2* out = (double2*)(D.small + p.soff + out_off);
   // staging role: one row, columns c0, c0 + cstep, ... (k-th: X column if below a, else Z)
@@ -694,10 +694,10 @@ void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshif
   static size_t set = 0;
   static std::map<size_t, int> slots_for;      // shared memory size -> resident blocks on the GPU
   // two buffers of staged rows of X and Z (float4 per value); afterwards the same space holds the
-  // row-group partial sums, (RG - 1) x tiles x 16 packed entries with RG = min(8, 256 / tiles):
-  // at most 224 x 16
+  // row-group partial sums, (RG - 1) x tiles x 16 packed entries with RG = min(RS, 256 / tiles):
+  // fewer than 256 x 16
   const int RS = gram_rows(D.L.LDR);
-  const size_t sm = std::max(sizeof(float4) * (4 * (size_t)D.L.LDR * (RS + 1)), sizeof(unsigned long long) * 224 * 16);
+  const size_t sm = std::max(sizeof(float4) * (4 * (size_t)D.L.LDR * (RS + 1)), sizeof(unsigned long long) * 256 * 16);
   if (sm > set) {
     cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;
