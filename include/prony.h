@@ -227,6 +227,12 @@ typedef struct {
   int tc_bstages;            /* and its B' stages in shared memory (0: not used) */
 } prony_stats;
 
+/* Tuning overrides of the tensor-core products, read from the environment at every call:
+ *   PRONY_TC_CLUSTER=c   largest thread-block cluster the autotuner may pick (1, 2 or 4)
+ *   PRONY_TC_BSTAGES=s   exactly s B' stages in shared memory (default: the most stages, from
+ *                        4 down to 2, that reach the smallest K split whose windows fit)
+ *   PRONY_TC_TUNE=0      no autotuning: cluster of at most 2 and the smallest K split
+ * They change launch configurations only, never the arithmetic beyond FP32 summation order. */
 int prony_set_profiling(prony_ctx* ctx, int enable);   /* also resets the statistics */
 int prony_get_stats(prony_ctx* ctx, prony_stats* out);
 
