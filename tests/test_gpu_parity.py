@@ -672,3 +672,43 @@ def test_maximum_sizes(ctx, prec, name, d, n, m, seed):
     assert res.info["status"] == 0 and res.info["rank_used"] == m, res.info
     order = np.lexsort(P.t.T[::-1])
     _check_solution(res, P.t[order], P.c[order])
+
+
+def test_device_and_host_pointer_batches_agree(ctx):
+    """The two batched entry points on one uneven batch (mixed d, n, m): device pointers on a
+    caller's stream (the call the benchmark times) and pinned host buffers (its end-to-end call)
+    give the list API's results, t rows of the batch's largest d.  The calls differ only in the
+    order of atomic additions (K-split partial sums in FP32), hence the parity tolerances."""
+    import torch
+    from paper_2012_11430_gb300 import default_opts
+    probs = W.batch_problems(12) + [W.make_problem("mix3", 3, 5, 4, 41), W.make_problem("mix1", 1, 30, 6, 42)]
+    ds, ns, ms = [p.d for p in probs], [p.n for p in probs], [p.m for p in probs]
+    sizes = [p.grid.size for p in probs]
+    soff = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    ooff = np.concatenate([[0], np.cumsum(ms)[:-1]]).astype(np.int64)
+    total, dmax = int(sum(ms)), max(ds)
+    opts = default_opts()
+    ref, rc = ctx.solve_batched([p.grid for p in probs], ds, ns, ms, opts)
+    assert rc == 0
+    host = torch.from_numpy(np.concatenate([p.grid.reshape(-1) for p in probs])).pin_memory()
+    stream = torch.cuda.Stream()
+    dev = host.cuda()
+    t_dev = torch.full((total * dmax,), float("nan"), dtype=torch.float64, device="cuda")
+    c_dev = torch.zeros(total, dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    infos_d, rc_d = ctx.solve_batched_dev(dev, ds, ns, ms, soff, ooff, t_dev, c_dev, opts, stream.cuda_stream)
+    stream.synchronize()
+    t_host = torch.zeros(total * dmax, dtype=torch.float64).pin_memory()
+    c_host = torch.zeros(total, dtype=torch.complex128).pin_memory()
+    infos_h, rc_h = ctx.solve_batched_host(host, ds, ns, ms, soff, ooff, t_host, c_host, opts)
+    assert rc_d == 0 and rc_h == 0
+    td, cd = t_dev.cpu().numpy(), c_dev.cpu().numpy()
+    th, ch = t_host.numpy(), c_host.numpy()
+    for i, (p, r) in enumerate(zip(probs, ref)):
+        o = int(ooff[i])
+        assert infos_d[i]["status"] == 0 and infos_h[i]["status"] == 0
+        for t_x, c_x in ((td, cd), (th, ch)):
+            t_i = t_x[o * dmax:(o + p.m) * dmax].reshape(p.m, dmax)[:, :p.d]
+            dt = np.abs(t_i - r.t)
+            assert np.max(np.minimum(dt, 1.0 - dt)) <= 1e-6, (p.name, t_i, r.t)
+            assert np.max(np.abs(c_x[o:o + p.m] - r.c)) <= 1e-5 * np.max(np.abs(r.c)), p.name
