@@ -120,6 +120,23 @@ int prony_build_S(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m
                   const prony_opts* opts, prony_c128* S_out, double* sigma_out,
                   prony_c128* U_out, prony_c128* V_out, prony_info* info);
 
+/* The FP64 steps of Algorithm 1 after the Toeplitz products, on caller-given matrices, for
+ * checking them in isolation: the SVD Q = U_Q Sigma V_Q^* of the projected block
+ * Q = U^* T V (final step of Algorithm 3), S_l = U_Q^* M_l V_Q Sigma^{-1} with M_l = U^* T_l V
+ * (Eq. generateSl), the eigenvectors W of C_mu = sum_l mu_l S_l (mu drawn from `seed`, as in
+ * prony_solve), z_j(l) = (W^{-1} S_l W)_jj and t_j(l) = -arg z_j(l) / 2 pi mod 1
+ * (Eq. diagonalizeSl).  These are the kernels prony_solve runs after its power loop.
+ * Q: a x m row-major, M: d blocks of a x m row-major (m <= a <= 128, m <= 64, d <= 4), host
+ * pointers.  Outputs (host): sigma_out[m] descending; S_out[d*m*m] row-major per l in the
+ * basis of the computed singular vectors (unique up to a phase per vector); z_out[m*d],
+ * t_out[m*d] row j for eigenvector j (unsorted); status_out (nullable): PRONY_OK or
+ * PRONY_ENOCONV if an iteration reached its cap.  jacobi_cap / eigqr_cap (<= 0: defaults, 30
+ * one-sided Jacobi sweeps and 30 m + 30 shifted-QR steps) lower the caps of the FP32
+ * iterations whose results the FP64 steps refine. */
+int prony_small_steps(prony_ctx* ctx, int d, int m, int a, const prony_c128* Q, const prony_c128* M,
+                      unsigned long long seed, int jacobi_cap, int eigqr_cap, double* sigma_out,
+                      prony_c128* S_out, prony_c128* z_out, double* t_out, int* status_out);
+
 /* Eq. 1 at K integer points: f_out[q] = sum_j c_j exp(-2 pi i <t_j, k_q>).
  * t[m*d] row-major, c[m], k[K*d] row-major.  Phases reduced in FP64. */
 int prony_eval(prony_ctx* ctx, const double* t, const prony_c128* c, int m, int d,
@@ -197,13 +214,15 @@ int prony_toeplitz_mm_dev(prony_ctx* ctx, const prony_c128* grid_dev, int d, int
  * other allocating routine: its scratch (problem descriptor, job list, complex64
  * copies of the grid) lives in one fixed file-scope device array of
  * PRONY_STATIC_SCRATCH_BYTES that every GPU loading the library holds until exit.
- * Arguments as prony_toeplitz_mm_dev; it runs on the current device, is asynchronous
- * on `stream` (results are ready when the stream reaches that point) and returns
- * PRONY_EINVAL (message: prony_last_error) when (2n+2)^d > PRONY_STATIC_MAX_GRID.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
- * share the array and each rewrites what it reads; calls that overlap on the GPU
- * (e.g. on two streams at once) race on it. */
+ * Arguments and validation as prony_toeplitz_mm_dev (r <= (n+1)^d); it runs on the current
+ * device, is asynchronous on `stream` (results are ready when the stream reaches that point)
+ * and returns PRONY_EINVAL (message: prony_last_error) when (2n+2)^d > PRONY_STATIC_MAX_GRID.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress).  The first call on each device also loads the library's module
+ * there and reserves the PRONY_STATIC_SCRATCH_BYTES, which may synchronise: make it once as
+ * a warm-up, outside latency-critical loops and before any stream capture.  All calls share
+ * the array and each rewrites what it reads; calls that overlap on the GPU (e.g. on two
+ * streams at once) race on it.  The product runs without a K split (one CTA per row tile). */
 #define PRONY_STATIC_MAX_GRID (1 << 20)
 #define PRONY_STATIC_SCRATCH_BYTES (512 + 65536 * 16 + 16 * PRONY_STATIC_MAX_GRID)   /* 17 MiB */
 int prony_toeplitz_mm_static(const prony_c128* grid_dev, int d, int n, const void* X_dev, int r, int L,
@@ -222,17 +241,18 @@ typedef struct {
   double toeplitz_ms;        /* summed CUDA-event durations of the Toeplitz launches */
   double toeplitz_flops;     /* summed algorithmic flops of those launches */
   double toeplitz_bytes;     /* summed algorithmic bytes of those launches */
-  int tc_cluster;            /* tensor-core path of the last batch: CTAs per cluster (0: not used) */
-  int tc_ksplit;             /* and the K split of its products, as chosen by the autotuner */
+  int tc_ksplit;             /* tensor-core path of the last batch: K split of its products, as
+                                chosen by the autotuner (0: not used) */
   int tc_bstages;            /* and its B' stages in shared memory (0: not used) */
 } prony_stats;
 
 /* Tuning overrides of the tensor-core products, read from the environment at every call:
- *   PRONY_TC_CLUSTER=c   largest thread-block cluster the autotuner may pick (1, 2 or 4)
  *   PRONY_TC_BSTAGES=s   exactly s B' stages in shared memory (default: the most stages, from
  *                        4 down to 2, that reach the smallest K split whose windows fit)
- *   PRONY_TC_TUNE=0      no autotuning: cluster of at most 2 and the smallest K split
- * They change launch configurations only, never the arithmetic beyond FP32 summation order. */
+ *   PRONY_TC_TUNE=0      no autotuning: the smallest K split
+ * They change launch configurations only, never the arithmetic beyond FP32 summation order.
+ * For a given launch configuration every product is deterministic: split-K partial sums are
+ * added in the order of their K ranges, whatever order the CTAs finish in. */
 int prony_set_profiling(prony_ctx* ctx, int enable);   /* also resets the statistics */
 int prony_get_stats(prony_ctx* ctx, prony_stats* out);
 

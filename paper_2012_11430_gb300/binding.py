@@ -24,14 +24,14 @@ EXPORTS = [
     "prony_default_opts", "prony_status_string", "prony_last_error", "prony_ctx_create", "prony_ctx_destroy",
     "prony_solve", "prony_build_S", "prony_eval", "prony_solve_batched", "prony_solve_batched_dev",
     "prony_expsum_fwd_dev", "prony_expsum_bwd_dev", "prony_toeplitz_mm_dev", "prony_set_profiling",
-    "prony_get_stats", "prony_toeplitz_mm_static", "prony_refine_lm_dev",
+    "prony_get_stats", "prony_toeplitz_mm_static", "prony_refine_lm_dev", "prony_small_steps",
 ]
 
 
 class PronyStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("toeplitz_launches", ctypes.c_longlong),
                 ("toeplitz_ms", ctypes.c_double), ("toeplitz_flops", ctypes.c_double),
-                ("toeplitz_bytes", ctypes.c_double), ("tc_cluster", ctypes.c_int), ("tc_ksplit", ctypes.c_int),
+                ("toeplitz_bytes", ctypes.c_double), ("tc_ksplit", ctypes.c_int),
                 ("tc_bstages", ctypes.c_int)]
 
     def as_dict(self) -> dict:
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
     lib.prony_toeplitz_mm_static.argtypes = [P, I, I, P, I, I, I, P, P]
     lib.prony_set_profiling.argtypes = [P, I]
     lib.prony_get_stats.argtypes = [P, ctypes.POINTER(PronyStats)]
+    lib.prony_small_steps.argtypes = [P, I, I, I, P, P, ULL, I, I, P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("prony_default_opts", "prony_status_string", "prony_last_error"):
             getattr(lib, name).restype = I
@@ -212,6 +213,25 @@ class Context:
         _check(rc, "prony_build_S", allow)
         # column-major N x m on the C side == row-major m x N here
         return S, sig, (U.T.copy() if want_uv else None), (V.T.copy() if want_uv else None), info.as_dict()
+
+    def small_steps(self, Q, M, seed: int = 1, jacobi_cap: int = 0, eigqr_cap: int = 0):
+        """The FP64 steps after the products on given Q (a x m) and M (d, a, m): returns
+        (sigma, S (d, m, m), z (m, d), t (m, d), status)."""
+        Q = np.ascontiguousarray(Q, dtype=np.complex128)
+        M = np.ascontiguousarray(M, dtype=np.complex128)
+        a, m = Q.shape
+        d = M.shape[0]
+        if M.shape != (d, a, m):
+            raise ValueError("M must be (d, a, m)")
+        sig = np.zeros(m)
+        S = np.zeros((d, m, m), dtype=np.complex128)
+        z = np.zeros((m, d), dtype=np.complex128)
+        t = np.zeros((m, d))
+        st = ctypes.c_int(0)
+        _check(self._lib.prony_small_steps(self._h, d, m, a, _ptr(Q), _ptr(M), ctypes.c_ulonglong(seed),
+                                           int(jacobi_cap), int(eigqr_cap), _ptr(sig), _ptr(S), _ptr(z), _ptr(t),
+                                           ctypes.byref(st)), "prony_small_steps")
+        return sig, S, z, t, st.value
 
     def eval(self, t, c, k) -> np.ndarray:
         t = np.ascontiguousarray(t, dtype=np.float64)

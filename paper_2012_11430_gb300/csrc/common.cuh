@@ -59,6 +59,7 @@ struct ProbState {
   int lk;                     // Lanczos (Algorithm 2): vectors u_1..u_lk accepted
   int lstop;                  // Lanczos: why it stopped (1 alpha, 2 beta below the tolerance, 3 block full)
   double lalpha, lbeta;       // Lanczos: last alpha, beta
+  int oa_conv;                // refinement of the SVD of Q: 0 running, 2 last step pending, 1 converged
 };
 
 // Small per-problem workspace: byte offsets inside the block at ProbDesc::soff.
@@ -137,7 +138,46 @@ struct Dev {
   float2* fhat;
   float2* ftw;
   int fLT;
+  // iteration caps of the small FP32 iterations (0: defaults, 30 Jacobi sweeps and 30 m + 30
+  // shifted-QR steps); lowered only to exercise the PRONY_ENOCONV path
+  int cap_jacobi, cap_eigqr;
+  // fixed-order sums over the blocks of one problem: `red_stride` bytes of partials per problem,
+  // one arrival counter per problem (zero between launches)
+  char* red;
+  long long red_stride;
+  int* rcnt;
+  // first failed workspace bound check (site number, 0: none); the host turns it into PRONY_ECUDA
+  int* oob;
 };
+
+// Bound check of a workspace access: on failure records `site` in D.oob (first failure wins)
+// and returns false, so that the caller skips the access instead of writing out of bounds.
+__device__ inline bool ws_ok(const Dev& D, bool ok, int site) {
+  if (!ok && D.oob) atomicCAS(D.oob, 0, site);
+  return ok;
+}
+
+// Deterministic cross-block sums: every block of problem `pi` that takes part stores its
+// partial values in its own slot of the problem's region of D.red, then calls red_arrive with
+// the number of blocks taking part.  It returns true in every thread of the last block to arrive
+// (all other partials are then visible to it), which adds the slots in block order -- so the
+// result does not depend on the order in which the blocks finish.  The counter is reset for the
+// next launch.  Every thread of the block must call it.
+__device__ inline bool red_arrive(const Dev& D, int pi, int expected) {
+  __shared__ int s_last_block;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int old = atomicAdd(&D.rcnt[pi], 1);
+    s_last_block = old == expected - 1;
+    if (s_last_block) D.rcnt[pi] = 0;
+  }
+  __syncthreads();
+  const bool last = s_last_block != 0;
+  if (last) __threadfence();
+  return last;
+}
+__device__ inline char* red_region(const Dev& D, int pi) { return D.red + (size_t)pi * D.red_stride; }
 
 // ----------------------------------------------------------------------------- complex helpers
 __host__ __device__ inline float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -265,6 +305,9 @@ __host__ __device__ inline int sel_width(const ProbState& s, const ProbDesc& p, 
 enum BufSel { BUF_V = 0, BUF_U = 1, BUF_B1 = 2, BUF_B2 = 3, BUF_Y = 4 };
 
 // kernels_tall.cu
+// Bytes of cross-block partials per problem that the tall kernels need for a batch of this
+// layout (D.nprob, D.maxN, D.maxGd, D.L set).
+long long red_bytes_per_problem(const Dev& D);
 void launch_prep(const Dev& D, cudaStream_t s);
 void launch_init_v0(const Dev& D, unsigned long long seed, cudaStream_t s);
 void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_t s);
@@ -289,10 +332,14 @@ void launch_eval_points(const double* t, const double2* c, int m, int d, const i
                         cudaStream_t s);
 
 // kernels_toeplitz.cu
+// One CTA of a Toeplitz product: problem, row tile, K range ks of nks.  The K ranges of a row tile
+// are consecutive jobs (ks innermost): with a K split the CTA of range 0 is job blockIdx - ks.
 struct ToeplitzJob { int prob, mt, ks, nks; };
-void launch_zero_buf(const Dev& D, int buf, int wsel, int y_ext, cudaStream_t s);
-void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int xbuf, int wsel,
-                     int ybuf, int y_ext, int maxw, int precision, cudaStream_t s);
+// Split K workspace: `part` holds one slot of simt_part_elems(maxw) complex64 per job, `cnt` one
+// zeroed int per job (every launch leaves it zeroed).
+size_t simt_part_elems(int maxw);
+void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int xbuf, int wsel, int ybuf,
+                     int y_ext, int maxw, float2* part, int* cnt, long long part_jobs, cudaStream_t s);
 
 // kernels_tc.cu (tensor-core Toeplitz products: split BF16 planes or TF32 hi + lo)
 int tc_planes(int kind);
@@ -300,12 +347,15 @@ size_t tc_stage_bytes(int kind, int ntbox);
 size_t tc_elem_bytes(int kind);
 size_t tc_smem_bytes(int kind, int ntbox, int stages, int win_cap);
 long long tc_prob_stride(int kind, int ntbox, int maxnc);
-int tc_max_cluster(int kind, int want, size_t smem);
+// Split K workspace of the tensor-core products: tc_part_floats(ntbox) floats per job, one zeroed
+// counter per job.
+size_t tc_part_floats(int ntbox);
 void launch_split_tables(const Dev& D, int kind, cudaStream_t s);
 void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, long long prob_stride, cudaStream_t s);
-cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel,
-                               int ybuf, int y_ext, int kind, int ntbox, int win_cap, int stages, int cs,
-                               const void* xb, long long prob_stride, int* err, cudaStream_t s);
+cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int wsel, int ybuf,
+                               int y_ext, int kind, int ntbox, int win_cap, int stages, const void* xb,
+                               long long prob_stride, float* part, int* cnt, long long part_jobs, int* err,
+                               cudaStream_t s);
 
 // kernels_refine.cu (Levenberg-Marquardt refinement of (t, c))
 long long lm_workspace_bytes(int m, int d);
@@ -334,7 +384,7 @@ void launch_lz_finish(const Dev& D, cudaStream_t s);
 void launch_lz_all_done(const Dev& D, int* flag, cudaStream_t s);
 
 // kernels_small.cu
-enum QrMode { QR_PLAIN = 0, QR_DROP = 1, QR_RANK = 2 };
+enum QrMode { QR_PLAIN = 0, QR_DROP = 1, QR_RANK = 2, QR_AUTO = 3 };   // AUTO: RANK on a problem's first iteration
 void launch_chol(const Dev& D, int wsel, int target, int mode, double tol, int rank_mode, cudaStream_t s);
 void launch_svd_S(const Dev& D, cudaStream_t s);
 void launch_canon(const Dev& D, cudaStream_t s);

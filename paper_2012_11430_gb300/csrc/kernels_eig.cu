@@ -1,18 +1,23 @@
 // FP64-accurate small steps of Algorithm 1, designed for GB300's FP64 unit (high latency per
-// dependent operation, low throughput): iterations run in FP32, and the quantities that fix the
-// results are then computed or refined in FP64 with matrix products only (latency-tolerant).
+// dependent operation, low throughput per SM): iterations run in FP32 on one CTA per problem,
+// and the quantities that fix the results are then computed or refined in FP64 with matrix
+// products only, which k_zgemm spreads over many CTAs per problem (every SM's FP64 units take
+// part even when the batch has fewer problems than SMs).
 //
-//  k_svd_S  SVD of Q = U^* T V (Algorithm 3, final step): FP32 one-sided Jacobi gives V_Q; FP64
-//           refinement of V_Q as eigenvectors of Q^*Q (Ogita & Aishima 2018, iterative refinement
-//           for the symmetric eigenvalue problem based on matrix multiplication, Hermitian form);
-//           sigma = sqrt(eigenvalues), U_Q = Q V_Q Sigma^{-1} and S_l = U_Q^* (U^* T_l V) V_Q
-//           Sigma^{-1} (Eq. generateSl) in FP64.
-//  k_eig_t  C_mu = sum_l mu_l S_l (FP64); W from an FP32 Hessenberg reduction, shifted complex QR
-//           and triangular eigenvectors; W^{-1} from an FP32 Gauss-Jordan inverse refined by one
-//           FP64 Newton-Schulz step X <- X (2I - W X); z_j(l) = (W^{-1} S_l W)_jj in FP64
-//           (Eq. diagonalizeSl).  The diagonal of W^{-1} S_l W is stationary in W: an error E in
-//           W (W = W_0 (I + E)) changes it only at second order, so z carries FP64 accuracy even
-//           though W comes from FP32 iterations.  t_j(l) = -arg z_j(l) / 2pi mod 1.
+//  SVD of Q = U^* T V (Algorithm 3, final step): k_svd_jacobi (FP32 one-sided Jacobi) gives a
+//           starting V; FP64 refinement of V as eigenvectors of H = Q^*Q (Ogita & Aishima 2018,
+//           iterative refinement for the symmetric eigenvalue problem based on matrix
+//           multiplication, Hermitian form): per step T1 = V^*V, T2 = H V, S = V^* T2 (k_zgemm),
+//           the correction F = I + E (k_oa_step), V <- V F (k_zgemm), until ||E||_F <= 1e-9;
+//           k_svd_sort orders the eigenpairs, sigma = sqrt(eigenvalues); U_Q = Q V_Q Sigma^{-1}
+//           and S_l = (U_Q^* (U^* T_l V)) V_Q Sigma^{-1} (Eq. generateSl) by k_zgemm.
+//  Eigen step: k_eig_w forms C_mu = sum_l mu_l S_l and finds W (FP32 Hessenberg reduction,
+//           shifted complex QR, triangular eigenvectors) and its FP32 inverse X; two FP64
+//           Newton-Schulz steps X <- 2X - X (W X) (k_zgemm); C_l = S_l W (k_zgemm);
+//           k_eig_z: z_j(l) = (X C_l)_jj, t_j(l) = -arg z_j(l) / 2pi mod 1 (Eq. diagonalizeSl).
+//           The diagonal of W^{-1} S_l W is stationary in W: an error E in W (W = W_0 (I + E))
+//           changes it only at second order, so z carries FP64 accuracy even though W comes
+//           from FP32 iterations.
 //  k_canon  phase-canonical singular basis for the S_l output.
 #include "common.cuh"
 
@@ -23,6 +28,16 @@ namespace {
 
 __device__ inline void set_status_e(ProbState& s, int st) {
   if (s.status == ST_OK) s.status = st;
+}
+
+// a problem takes part in the SVD of Q: its power loop ended with a U of width a <= r0 and a V of
+// width b <= m
+__device__ inline bool svd_live(const ProbDesc& p, const ProbState& st) {
+  return !st.done && st.status != ST_ENAN && st.wv > 0 && st.wu > 0 && st.wv <= p.m && st.wu <= p.r0;
+}
+// ... and in the eigen step (width m = wv of its S_l)
+__device__ inline bool eig_live(const ProbDesc& p, const ProbState& st) {
+  return !st.done && st.status != ST_ENAN && st.wv > 0 && st.wv <= p.m;
 }
 
 // ----------------------------------------------------------------------------- FP32 complex
@@ -51,32 +66,6 @@ __device__ inline float2 fsqrtc(float2 a) {
   return fc(fabsf(a.y) / (2.f * sx), a.y >= 0.f ? sx : -sx);
 }
 
-// ----------------------------------------------------------------------------- FP64 small products
-// C (M x N, ld ldc) = opA(A) (M x K) * opB(B) (K x N); opX = conjugate transpose when XH.
-// Four independent accumulators per entry keep several FP64 multiply-adds in flight.
-template <bool AH, bool BH>
-__device__ void zgemm(double2* C, int ldc, const double2* A, int lda, const double2* B, int ldb, int M, int N, int K) {
-  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
-    const int i = idx / N, j = idx % N;
-    double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-    int k = 0;
-    for (; k + 4 <= K; k += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        double2 a = AH ? cconj(A[(k + u) * lda + i]) : A[i * lda + k + u];
-        double2 b = BH ? cconj(B[j * ldb + k + u]) : B[(k + u) * ldb + j];
-        acc[u] = cadd(acc[u], cmul(a, b));
-      }
-    }
-    for (; k < K; ++k) {
-      double2 a = AH ? cconj(A[k * lda + i]) : A[i * lda + k];
-      double2 b = BH ? cconj(B[j * ldb + k]) : B[k * ldb + j];
-      acc[0] = cadd(acc[0], cmul(a, b));
-    }
-    C[i * ldc + j] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
-  }
-}
-
 // block-wide sum of a double (tree; result in every thread)
 __device__ double block_sum_d(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -96,28 +85,228 @@ __device__ inline void rr_pair(int step, int k, int nb, int& pa, int& pb) {
   pb = who(nb - 1 - k);
 }
 
-// ----------------------------------------------------------------------------- SVD of Q and S_l
-__global__ void __launch_bounds__(256) k_svd_S(Dev D) {
-  extern __shared__ float2 fsm[];
-  __shared__ int s_rot;
+
+// ----------------------------------------------------------------------------- batched FP64 products
+// C = alpha op(A) op(B) [diag(1/sigma)] [+ beta C0] for every problem of the batch (and `nl`
+// consecutive matrices per problem), on the per-problem small workspace.  Matrices are row-major
+// complex FP64 at byte offsets of the problem's block; op = conjugate transpose when t* = 1.
+// One CTA computes a 16 x 16 tile of C: 256 threads, one entry each, K staged 16 at a time in
+// shared memory; four partial sums per entry (k mod 4) keep eight independent FP64 chains per
+// thread in flight.  Dimensions come from the problem's state (a = wu, b = wv).
+enum ZDim { ZD_A = 0, ZD_B = 1 };
+enum ZLive { ZL_SVD = 0, ZL_EIG = 1 };
+enum ZConv { ZC_ALL = 0, ZC_SKIP_CONV = 1, ZC_COPY_CONV = 2 };
+struct ZG {
+  long long a, b, c, c0;          // byte offsets (c0 < 0: no C0 term)
+  long long la, lb, lc;           // byte strides between the nl matrices of a problem
+  long long colscale;             // byte offset of sigma (< 0: no column scaling)
+  int lda, ldb, ldc;
+  int ta, tb;
+  int M, N, K;                    // ZDim selectors
+  int nl;
+  int live;                       // ZLive
+  int conv;                       // ZConv: skip (or copy A to C for) problems whose refinement converged
+  double alpha, beta;
+};
+constexpr int ZT = 16;
+
+__device__ inline int zdim(const ProbState& st, int sel) { return sel == ZD_A ? st.wu : st.wv; }
+
+__global__ void __launch_bounds__(256) k_zgemm(Dev D, ZG g) {
+  __shared__ double2 As[ZT][ZT + 1];
+  __shared__ double2 Bs[ZT][ZT + 1];
+  const int pi = blockIdx.y;
+  const ProbDesc& p = D.P[pi];
+  const ProbState& st = D.st[pi];
+  if (!(g.live == ZL_SVD ? svd_live(p, st) : eig_live(p, st))) return;
+  const int l = blockIdx.z;
+  if (l >= g.nl) return;
+  const int M = zdim(st, g.M), N = zdim(st, g.N), K = zdim(st, g.K);
+  const int tiles_n = (N + ZT - 1) / ZT;
+  const int i0 = (blockIdx.x / tiles_n) * ZT, j0 = (blockIdx.x % tiles_n) * ZT;
+  if (i0 >= M) return;
+  char* sb = D.small + p.soff;
+  const double2* A = (const double2*)(sb + g.a + l * g.la);
+  const double2* B = (const double2*)(sb + g.b + l * g.lb);
+  double2* C = (double2*)(sb + g.c + l * g.lc);
+  const int ty = threadIdx.x / ZT, tx = threadIdx.x % ZT;
+  const int i = i0 + ty, j = j0 + tx;
+  // refinement state: 0 running, 2 last correction pending, 1 converged (products skipped, V copied)
+  if ((g.conv == ZC_SKIP_CONV && st.oa_conv != 0) || (g.conv == ZC_COPY_CONV && st.oa_conv == 1)) {
+    if (g.conv == ZC_COPY_CONV && i < M && j < N) C[i * g.ldc + j] = A[i * g.lda + j];
+    return;
+  }
+  double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+  for (int k0 = 0; k0 < K; k0 += ZT) {
+    {
+      // A tile rows i0.., columns k0..; B tile rows k0.., columns j0..
+      const int r = threadIdx.x / ZT, c = threadIdx.x % ZT;
+      const int ai = i0 + r, ak = k0 + c;
+      double2 av = make_double2(0.0, 0.0);
+      if (ai < M && ak < K) av = g.ta ? cconj(A[ak * g.lda + ai]) : A[ai * g.lda + ak];
+      As[r][c] = av;
+      const int bk = k0 + r, bj = j0 + c;
+      double2 bv = make_double2(0.0, 0.0);
+      if (bk < K && bj < N) bv = g.tb ? cconj(B[bj * g.ldb + bk]) : B[bk * g.ldb + bj];
+      Bs[r][c] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ZT; kk += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double2 a = As[ty][kk + u], b = Bs[kk + u][tx];
+        acc[u].x = fma(a.x, b.x, acc[u].x);
+        acc[u].y = fma(a.x, b.y, acc[u].y);
+        acc[u].x = fma(-a.y, b.y, acc[u].x);
+        acc[u].y = fma(a.y, b.x, acc[u].y);
+      }
+    }
+    __syncthreads();
+  }
+  if (i >= M || j >= N) return;
+  double2 v = cscale(cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3])), g.alpha);
+  if (g.colscale >= 0) {
+    const double sj = ((const double*)(sb + g.colscale))[j];
+    v = sj > 0.0 ? cscale(v, 1.0 / sj) : make_double2(0.0, 0.0);
+  }
+  if (g.c0 >= 0) v = cadd(v, cscale(((const double2*)(sb + g.c0 + l * g.lc))[i * g.ldc + j], g.beta));
+  C[i * g.ldc + j] = v;
+}
+
+// One refinement step of V (eigenvectors of H = Q^*Q) from T1 = V^*V (work3) and S = V^* H V
+// (uq): lambda_i = s_ii / (1 - r_ii) with R = I - V^*V, the correction E with
+// e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) (r_ij / 2 within a cluster of
+// eigenvalues closer than delta = 2 (||S - diag(lambda)||_F + ||H||_F ||R||_F)), written as
+// F = I + E into work4 for V <- V F; lambda into the sigma slots.  A step whose ||E||_F is at most
+// 1e-9 (after the first) is the last one (state 2: its V F still runs; the next step marks the
+// refinement converged, state 1): another would change V by less than the FP64 rounding of the
+// products.
+__global__ void __launch_bounds__(256) k_oa_step(Dev D, int iter) {
   __shared__ double s_red[32];
+  __shared__ double s_lam[PRONY_MMAX];
+  const ProbDesc& p = D.P[blockIdx.x];
+  ProbState& st = D.st[blockIdx.x];
+  if (!svd_live(p, st)) return;
+  const int state = st.oa_conv;
+  __syncthreads();
+  if (state == 2 && threadIdx.x == 0) st.oa_conv = 1;
+  if (state != 0) return;
+  const int b = st.wv, LM = D.L.LDM;
+  char* sb = D.small + p.soff;
+  const double2* Hm = (const double2*)(sb + D.L.work1);
+  const double2* T1 = (const double2*)(sb + D.L.work3);
+  const double2* Sm = (const double2*)(sb + D.L.uq);
+  double2* F = (double2*)(sb + D.L.work4);
+  double* lam = (double*)(sb + D.L.sigma);
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+    s_lam[i] = Sm[i * LM + i].x / T1[i * LM + i].x;       // s_ii / (1 - r_ii), 1 - r_ii = (V^*V)_ii
+    lam[i] = s_lam[i];
+  }
+  __syncthreads();
+  double e1 = 0.0, e2 = 0.0, e3 = 0.0;
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+    const int i = idx / b, j = idx % b;
+    double2 sv = Sm[i * LM + j];
+    if (i == j) sv.x -= s_lam[i];
+    const double2 t = T1[i * LM + j];
+    const double2 r = make_double2((i == j ? 1.0 : 0.0) - t.x, -t.y);
+    e1 += cabs2(sv);
+    e2 += cabs2(Hm[i * LM + j]);
+    e3 += cabs2(r);
+  }
+  e1 = block_sum_d(e1, s_red);
+  e2 = block_sum_d(e2, s_red);
+  e3 = block_sum_d(e3, s_red);
+  const double delta = 2.0 * (sqrt(e1) + sqrt(e2) * sqrt(e3));
+  double en = 0.0;
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+    const int i = idx / b, j = idx % b;
+    const double2 t = T1[i * LM + j];
+    const double2 r = make_double2((i == j ? 1.0 : 0.0) - t.x, -t.y);
+    double2 e;
+    if (i != j && fabs(s_lam[i] - s_lam[j]) > delta)
+      e = cscale(cadd(Sm[i * LM + j], cscale(r, s_lam[j])), 1.0 / (s_lam[j] - s_lam[i]));
+    else
+      e = cscale(r, 0.5);
+    en += cabs2(e);
+    F[i * LM + j] = make_double2((i == j ? 1.0 : 0.0) + e.x, e.y);
+  }
+  en = block_sum_d(en, s_red);
+  if (threadIdx.x == 0 && iter >= 1 && en <= 1e-18) st.oa_conv = 2;
+}
+
+// Eigenpairs of H in descending order: V_Q (vq) = the columns of the refined V (at byte offset
+// `voff`) permuted, sigma = sqrt(lambda) sorted, sigma_m / sigma_1.
+__global__ void __launch_bounds__(256) k_svd_sort(Dev D, long long voff) {
   __shared__ double s_lam[PRONY_MMAX];
   __shared__ int s_rank[PRONY_MMAX];
   const ProbDesc& p = D.P[blockIdx.x];
   ProbState& st = D.st[blockIdx.x];
-  if (st.done || st.status == ST_ENAN) return;
+  if (!svd_live(p, st)) return;
+  const int b = st.wv, LM = D.L.LDM;
+  char* sb = D.small + p.soff;
+  const double2* Vm = (const double2*)(sb + voff);
+  double2* VQ = (double2*)(sb + D.L.vq);
+  double* sig = (double*)(sb + D.L.sigma);
+  for (int i = threadIdx.x; i < b; i += blockDim.x) s_lam[i] = sig[i];
+  __syncthreads();
+  for (int j = threadIdx.x; j < b; j += blockDim.x) {
+    int r = 0;
+    for (int i = 0; i < b; ++i)
+      if (s_lam[i] > s_lam[j] || (s_lam[i] == s_lam[j] && i < j)) ++r;
+    s_rank[j] = r;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+    const int i = idx / b, j = idx % b;
+    VQ[i * LM + s_rank[j]] = Vm[i * LM + j];
+  }
+  for (int j = threadIdx.x; j < b; j += blockDim.x) sig[s_rank[j]] = sqrt(fmax(s_lam[j], 0.0));
+  __syncthreads();
+  if (threadIdx.x == 0) st.sigma_ratio = sig[0] > 0.0 ? sig[b - 1] / sig[0] : 0.0;
+}
+
+// z_j(l) = sum_a X[j][a] C_l[a][j] with X = W^{-1} (work3 after the Newton-Schulz steps) and
+// C_l = S_l W (mproj slices); t_j(l) = -arg z_j(l) / 2 pi mod 1.
+__global__ void k_eig_z(Dev D) {
+  const ProbDesc& p = D.P[blockIdx.x];
+  ProbState& st = D.st[blockIdx.x];
+  if (!eig_live(p, st)) return;
+  const int m = st.wv, LM = D.L.LDM, LR = D.L.LDR;
+  char* sb = D.small + p.soff;
+  const double2* Xd = (const double2*)(sb + D.L.work3);
+  double* tout = (double*)(sb + D.L.t);
+  double2* zr = (double2*)(sb + D.L.zraw);
+  for (int q = threadIdx.x; q < m * p.d; q += blockDim.x) {
+    const int j = q / p.d, l = q % p.d;
+    const double2* Cl = (const double2*)(sb + D.L.mproj) + (size_t)l * LR * LM;
+    double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    for (int a = 0; a < m; ++a) acc[a & 3] = cadd(acc[a & 3], cmul(Xd[j * LM + a], Cl[a * LM + j]));
+    const double2 z = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+    zr[j * PRONY_DMAX + l] = z;
+    double tj = -atan2(z.y, z.x) / 6.283185307179586;
+    tj -= floor(tj);
+    if (tj >= 1.0) tj = 0.0;
+    tout[j * PRONY_DMAX + l] = tj;
+  }
+  if (threadIdx.x == 0) st.rank_used = m;
+}
+
+// ----------------------------------------------------------------------------- SVD of Q and S_l
+// FP32 one-sided Jacobi on the columns of Q: the starting V (FP64 copy in work2) of the FP64
+// refinement.  One CTA per problem.
+__global__ void __launch_bounds__(256) k_svd_jacobi(Dev D) {
+  extern __shared__ float2 fsm[];
+  __shared__ int s_rot;
+  const ProbDesc& p = D.P[blockIdx.x];
+  ProbState& st = D.st[blockIdx.x];
+  if (!svd_live(p, st)) return;
   const int a = st.wu, b = st.wv;
-  if (b <= 0 || a <= 0 || b > p.m || a > p.r0) return;
   const int LM = D.L.LDM, LR = D.L.LDR;
   char* sb = D.small + p.soff;
   const double2* Q = (const double2*)(sb + D.L.q);            // a x b, ld LM
-  double2* UQ = (double2*)(sb + D.L.uq);                        // a x b, ld LM
-  double2* VQ = (double2*)(sb + D.L.vq);                        // b x b, ld LM
-  double* sig = (double*)(sb + D.L.sigma);
-  double2* Hm = (double2*)(sb + D.L.work1);                     // b x b
-  double2* Vm = (double2*)(sb + D.L.work2);                     // b x b
-  double2* T1 = (double2*)(sb + D.L.work3);                     // up to a x b
-  double2* T2 = (double2*)(sb + D.L.work4);                     // up to a x b
+  double2* Vm = (double2*)(sb + D.L.work2);                     // b x b, ld LM
   float2* Qc = fsm;                                             // [b][a] columns (FP32)
   float2* Vc = fsm + (size_t)LM * LR;                           // [b][b] columns (FP32)
 
@@ -135,8 +324,10 @@ __global__ void __launch_bounds__(256) k_svd_S(Dev D) {
   const int nb = b + (b & 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const float jtol = 4.f * a * 5.9604645e-8f;
+  const int max_sweeps = D.cap_jacobi > 0 ? D.cap_jacobi : 30;
   int sweep = 0;
-  for (; sweep < 30 && b > 1; ++sweep) {
+  bool rotated = b > 1;                          // the last sweep still rotated (not converged)
+  for (; sweep < max_sweeps && b > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int step = 0; step < nb - 1; ++step) {
@@ -179,109 +370,18 @@ __global__ void __launch_bounds__(256) k_svd_S(Dev D) {
       }
       __syncthreads();
     }
+    rotated = s_rot != 0;
     if (!s_rot) break;
     __syncthreads();
   }
-  // ---- FP64: H = Q^* Q, then refine V (eigenvectors of H) by two matrix-product steps
   for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
     int i = idx / b, j = idx % b;
     float2 v = Vc[j * b + i];
     Vm[i * LM + j] = make_double2(v.x, v.y);
   }
-  zgemm<true, false>(Hm, LM, Q, LM, Q, LM, b, b, a);
-  __syncthreads();
-  for (int iter = 0; iter < 2; ++iter) {
-    zgemm<true, false>(T1, LM, Vm, LM, Vm, LM, b, b, b);        // V^* V
-    zgemm<false, false>(T2, LM, Hm, LM, Vm, LM, b, b, b);       // H V
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {   // R = I - V^* V  (into T1)
-      int i = idx / b, j = idx % b;
-      double2 r = T1[i * LM + j];
-      T1[i * LM + j] = make_double2((i == j ? 1.0 : 0.0) - r.x, -r.y);
-    }
-    __syncthreads();
-    // S = V^* (H V)  -> Hv scratch: reuse UQ rows as b x b scratch (overwritten later)
-    zgemm<true, false>(UQ, LM, Vm, LM, T2, LM, b, b, b);
-    __syncthreads();
-    for (int i = threadIdx.x; i < b; i += blockDim.x) s_lam[i] = UQ[i * LM + i].x / (1.0 - T1[i * LM + i].x);
-    __syncthreads();
-    // delta = 2 (||S - diag(lambda)||_F + ||H||_F ||R||_F)
-    double e1 = 0.0, e2 = 0.0, e3 = 0.0;
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-      int i = idx / b, j = idx % b;
-      double2 sv = UQ[i * LM + j];
-      if (i == j) sv.x -= s_lam[i];
-      e1 += cabs2(sv);
-      e2 += cabs2(Hm[i * LM + j]);
-      e3 += cabs2(T1[i * LM + j]);
-    }
-    e1 = block_sum_d(e1, s_red);
-    e2 = block_sum_d(e2, s_red);
-    e3 = block_sum_d(e3, s_red);
-    const double delta = 2.0 * (sqrt(e1) + sqrt(e2) * sqrt(e3));
-    // E (into T2): e_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i), or r_ij / 2 inside a cluster
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-      int i = idx / b, j = idx % b;
-      double2 r = T1[i * LM + j];
-      double2 e;
-      if (i != j && fabs(s_lam[i] - s_lam[j]) > delta) {
-        double2 sv = UQ[i * LM + j];
-        e = cscale(cadd(sv, cscale(r, s_lam[j])), 1.0 / (s_lam[j] - s_lam[i]));
-      } else {
-        e = cscale(r, 0.5);
-      }
-      T2[i * LM + j] = e;
-    }
-    __syncthreads();
-    zgemm<false, false>(T1, LM, Vm, LM, T2, LM, b, b, b);        // V E
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-      int i = idx / b, j = idx % b;
-      Vm[i * LM + j] = cadd(Vm[i * LM + j], T1[i * LM + j]);
-    }
-    __syncthreads();
-  }
-  // ---- order by eigenvalue of H = sigma^2 (descending)
-  for (int j = threadIdx.x; j < b; j += blockDim.x) {
-    int r = 0;
-    for (int i = 0; i < b; ++i)
-      if (s_lam[i] > s_lam[j] || (s_lam[i] == s_lam[j] && i < j)) ++r;
-    s_rank[j] = r;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {   // VQ (sorted columns)
-    int i = idx / b, j = idx % b;
-    VQ[i * LM + s_rank[j]] = Vm[i * LM + j];
-  }
-  for (int j = threadIdx.x; j < b; j += blockDim.x) sig[s_rank[j]] = sqrt(fmax(s_lam[j], 0.0));
-  __syncthreads();
-  // U_Q = Q V_Q Sigma^{-1}
-  zgemm<false, false>(UQ, LM, Q, LM, VQ, LM, a, b, b);
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < a * b; idx += blockDim.x) {
-    int i = idx / b, j = idx % b;
-    double sj = sig[j];
-    UQ[i * LM + j] = sj > 0.0 ? cscale(UQ[i * LM + j], 1.0 / sj) : make_double2(0.0, 0.0);
-  }
-  __syncthreads();
-  // S_l = U_Q^* (M_l V_Q) Sigma^{-1}
-  for (int l = 0; l < p.d; ++l) {
-    const double2* Ml = (const double2*)(sb + D.L.mproj) + (size_t)l * LR * LM;
-    double2* S = (double2*)(sb + D.L.S) + (size_t)l * LM * LM;
-    zgemm<false, false>(T1, LM, Ml, LM, VQ, LM, a, b, b);
-    __syncthreads();
-    zgemm<true, false>(S, LM, UQ, LM, T1, LM, b, b, a);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-      int i = idx / b, j = idx % b;
-      double sj = sig[j];
-      S[i * LM + j] = sj > 0.0 ? cscale(S[i * LM + j], 1.0 / sj) : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    st.sigma_ratio = sig[0] > 0.0 ? sig[b - 1] / sig[0] : 0.0;
-    if (sweep >= 30) set_status_e(st, ST_ENOCONV);
+    st.oa_conv = 0;
+    if (sweep >= max_sweeps && rotated) set_status_e(st, ST_ENOCONV);
   }
 }
 
@@ -324,7 +424,10 @@ __global__ void k_canon(Dev D) {
 }
 
 // ----------------------------------------------------------------------------- eigen step
-__global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
+// C_mu, its eigenvectors W (FP32 Hessenberg reduction, shifted complex QR, triangular
+// eigenvectors; FP64 copy in work2) and the FP32 Gauss-Jordan inverse X of W (FP64 copy in
+// work3).  One CTA per problem.
+__global__ void __launch_bounds__(256) k_eig_w(Dev D, unsigned long long seed) {
   extern __shared__ float2 esm[];
   __shared__ double2 mu[PRONY_DMAX];
   __shared__ float2 hv[PRONY_MMAX];
@@ -333,9 +436,8 @@ __global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
   __shared__ int s_fail, s_pr;
   const ProbDesc& p = D.P[blockIdx.x];
   ProbState& st = D.st[blockIdx.x];
-  if (st.done || st.status == ST_ENAN) return;
+  if (!eig_live(p, st)) return;                 // shared memory holds 3 maxM^2 entries
   const int m = st.wv;
-  if (m <= 0 || m > p.m) return;                // shared memory holds 3 maxM^2 entries
   const int LM = D.L.LDM;
   const int LD = m;                             // smem leading dimension
   float2* H = esm;                              // m x m  (C_mu, then Schur form, then W^{-1} work)
@@ -343,10 +445,8 @@ __global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
   float2* Y = Z + LD * LD;                      // m x m  (triangular eigenvectors, then W^{-1})
   char* sb = D.small + p.soff;
   const double2* S = (const double2*)(sb + D.L.S);
-  double2* Cd = (double2*)(sb + D.L.work1);     // C_mu (FP64), then S_l W
   double2* Wd = (double2*)(sb + D.L.work2);     // W (FP64)
-  double2* Xd = (double2*)(sb + D.L.work3);     // W^{-1} (FP64)
-  double2* Rd = (double2*)(sb + D.L.work4);     // scratch
+  double2* Xd = (double2*)(sb + D.L.work3);     // W^{-1} (FP64, FP32 accurate)
   if (threadIdx.x == 0) {
     double nrm = 0.0;
     for (int l = 0; l < p.d; ++l) {
@@ -367,7 +467,6 @@ __global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
     int i = idx / m, j = idx % m;
     double2 acc = make_double2(0.0, 0.0);
     for (int l = 0; l < p.d; ++l) acc = cadd(acc, cmul(mu[l], S[(size_t)l * LM * LM + i * LM + j]));
-    Cd[i * LM + j] = acc;
     H[i * LD + j] = fc((float)acc.x, (float)acc.y);
     Z[i * LD + j] = fc(i == j ? 1.f : 0.f, 0.f);
   }
@@ -423,7 +522,7 @@ __global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
     const int lane = threadIdx.x;
     const float eps = 5.9604645e-8f;
     int hi = m - 1, its = 0, total = 0;
-    const int cap = 30 * m + 30;
+    const int cap = D.cap_eigqr > 0 ? D.cap_eigqr : 30 * m + 30;
     while (hi > 0) {
       if (total > cap) break;
       int l = hi;
@@ -578,63 +677,94 @@ __global__ void __launch_bounds__(256) k_eig_t(Dev D, unsigned long long seed) {
       Y[i * LD + j] = fsub(Y[i * LD + j], fmul(f, Y[k * LD + j]));
     }
     __syncthreads();
-  }
-  // ---- FP64: X = W^{-1} refined by Newton-Schulz X <- X (2I - W X)
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+  }  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
     int i = idx / m, j = idx % m;
     float2 x = Y[i * LD + j];
     Xd[i * LM + j] = make_double2(x.x, x.y);
   }
-  __syncthreads();
-  for (int it = 0; it < 2; ++it) {
-    zgemm<false, false>(Rd, LM, Wd, LM, Xd, LM, m, m, m);            // W X
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      int i = idx / m, j = idx % m;
-      double2 r = Rd[i * LM + j];
-      Rd[i * LM + j] = make_double2((i == j ? 2.0 : 0.0) - r.x, -r.y);
-    }
-    __syncthreads();
-    zgemm<false, false>(Cd, LM, Xd, LM, Rd, LM, m, m, m);            // X (2I - W X)
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      int i = idx / m, j = idx % m;
-      Xd[i * LM + j] = Cd[i * LM + j];
-    }
-    __syncthreads();
-  }
-  // ---- z_j(l) = sum_a X[j][a] (S_l W)[a][j];  t = -arg z / 2 pi  mod 1
-  double* tout = (double*)(sb + D.L.t);
-  for (int l = 0; l < p.d; ++l) {
-    zgemm<false, false>(Cd, LM, S + (size_t)l * LM * LM, LM, Wd, LM, m, m, m);
-    __syncthreads();
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-      for (int a = 0; a < m; ++a) acc[a & 3] = cadd(acc[a & 3], cmul(Xd[j * LM + a], Cd[a * LM + j]));
-      double2 z = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
-      ((double2*)(sb + D.L.zraw))[j * PRONY_DMAX + l] = z;
-      double tj = -atan2(z.y, z.x) / 6.283185307179586;
-      tj -= floor(tj);
-      if (tj >= 1.0) tj = 0.0;
-      tout[j * PRONY_DMAX + l] = tj;
-    }
-    __syncthreads();
-  }
   if (threadIdx.x == 0 && s_fail == 2) set_status_e(st, ST_ENOCONV);
-  if (threadIdx.x == 0) st.rank_used = m;
 }
 
 }  // namespace
 
+namespace {
+constexpr int OA_MAX = 4;     // refinement steps launched (converged problems skip the rest)
+
+void launch_zgemm(const Dev& D, const ZG& g, cudaStream_t s) {
+  // tiles of the largest product of the batch: widths are at most r0 (a) and m (b)
+  const int mx = g.M == ZD_A ? D.L.LDR : D.L.LDM, nx = g.N == ZD_A ? D.L.LDR : D.L.LDM;
+  const int tiles = ((mx + ZT - 1) / ZT) * ((nx + ZT - 1) / ZT);
+  note_launch();
+  k_zgemm<<<dim3(tiles, D.nprob, g.nl), ZT * ZT, 0, s>>>(D, g);
+}
+
+ZG zg(long long a, int lda, int ta, long long b, int ldb, int tb, long long c, int ldc, int M, int N, int K,
+      int live) {
+  ZG g{};
+  g.a = a; g.b = b; g.c = c; g.c0 = -1;
+  g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+  g.ta = ta; g.tb = tb;
+  g.M = M; g.N = N; g.K = K;
+  g.nl = 1;
+  g.colscale = -1;
+  g.live = live;
+  g.conv = ZC_ALL;
+  g.alpha = 1.0;
+  g.beta = 0.0;
+  return g;
+}
+}  // namespace
+
 void launch_svd_S(const Dev& D, cudaStream_t s) {
   static size_t set = 0;
-  size_t sm = sizeof(float2) * ((size_t)D.L.LDM * D.L.LDR + (size_t)D.L.LDM * D.L.LDM);
+  const SmallLay& L = D.L;
+  const int LM = L.LDM;
+  size_t sm = sizeof(float2) * ((size_t)L.LDM * L.LDR + (size_t)L.LDM * L.LDM);
   if (sm > set) {
-    cudaFuncSetAttribute(k_svd_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_svd_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     set = sm;
   }
+  // H = Q^* Q (work1); starting V (work2) by FP32 Jacobi
+  launch_zgemm(D, zg(L.q, LM, 1, L.q, LM, 0, L.work1, LM, ZD_B, ZD_B, ZD_A, ZL_SVD), s);
   note_launch();
-  k_svd_S<<<D.nprob, 256, sm, s>>>(D);
+  k_svd_jacobi<<<D.nprob, 256, sm, s>>>(D);
+  // refinement steps; V alternates between work2 and the first S_l slot (free until the end)
+  long long v = L.work2, vn = L.S;
+  for (int it = 0; it < OA_MAX; ++it) {
+    ZG t1 = zg(v, LM, 1, v, LM, 0, L.work3, LM, ZD_B, ZD_B, ZD_B, ZL_SVD);   // V^* V
+    t1.conv = ZC_SKIP_CONV;
+    launch_zgemm(D, t1, s);
+    ZG t2 = zg(L.work1, LM, 0, v, LM, 0, L.work4, LM, ZD_B, ZD_B, ZD_B, ZL_SVD);   // H V
+    t2.conv = ZC_SKIP_CONV;
+    launch_zgemm(D, t2, s);
+    ZG sv = zg(v, LM, 1, L.work4, LM, 0, L.uq, LM, ZD_B, ZD_B, ZD_B, ZL_SVD);   // V^* H V
+    sv.conv = ZC_SKIP_CONV;
+    launch_zgemm(D, sv, s);
+    note_launch();
+    k_oa_step<<<D.nprob, 256, 0, s>>>(D, it);
+    ZG vf = zg(v, LM, 0, L.work4, LM, 0, vn, LM, ZD_B, ZD_B, ZD_B, ZL_SVD);   // V F
+    vf.conv = ZC_COPY_CONV;
+    launch_zgemm(D, vf, s);
+    std::swap(v, vn);
+  }
+  note_launch();
+  k_svd_sort<<<D.nprob, 256, 0, s>>>(D, v);
+  // U_Q = Q V_Q Sigma^{-1} (a x b)
+  ZG uq = zg(L.q, LM, 0, L.vq, LM, 0, L.uq, LM, ZD_A, ZD_B, ZD_B, ZL_SVD);
+  uq.colscale = L.sigma;
+  launch_zgemm(D, uq, s);
+  // P_l = U_Q^* M_l (b x b, into work1 + l (work2 - work1)); S_l = P_l V_Q Sigma^{-1}
+  ZG pl = zg(L.uq, LM, 1, L.mproj, LM, 0, L.work1, LM, ZD_B, ZD_B, ZD_A, ZL_SVD);
+  pl.nl = D.maxD;
+  pl.lb = 16LL * L.LDR * L.LDM;
+  pl.lc = L.work2 - L.work1;
+  launch_zgemm(D, pl, s);
+  ZG sl = zg(L.work1, LM, 0, L.vq, LM, 0, L.S, LM, ZD_B, ZD_B, ZD_B, ZL_SVD);
+  sl.nl = D.maxD;
+  sl.la = L.work2 - L.work1;
+  sl.lc = 16LL * L.LDM * L.LDM;
+  sl.colscale = L.sigma;
+  launch_zgemm(D, sl, s);
 }
 
 void launch_canon(const Dev& D, cudaStream_t s) {
@@ -644,11 +774,32 @@ void launch_canon(const Dev& D, cudaStream_t s) {
 
 void launch_eig_t(const Dev& D, unsigned long long seed, cudaStream_t s) {
   static size_t set = 0;
+  const SmallLay& L = D.L;
+  const int LM = L.LDM;
   size_t sm = sizeof(float2) * 3 * (size_t)D.maxM * D.maxM;
   if (sm > set) {
-    cudaFuncSetAttribute(k_eig_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1024));
+    cudaFuncSetAttribute(k_eig_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(sm, 1024));
     set = sm;
   }
   note_launch();
-  k_eig_t<<<D.nprob, 256, std::max<size_t>(sm, 16), s>>>(D, seed);
+  k_eig_w<<<D.nprob, 256, std::max<size_t>(sm, 16), s>>>(D, seed);
+  // two Newton-Schulz steps X <- 2X - X (W X): W in work2, X in work3 -> work1 -> work3
+  long long x = L.work3, xn = L.work1;
+  for (int it = 0; it < 2; ++it) {
+    launch_zgemm(D, zg(L.work2, LM, 0, x, LM, 0, L.work4, LM, ZD_B, ZD_B, ZD_B, ZL_EIG), s);   // R = W X
+    ZG ns = zg(x, LM, 0, L.work4, LM, 0, xn, LM, ZD_B, ZD_B, ZD_B, ZL_EIG);                  // 2X - X R
+    ns.alpha = -1.0;
+    ns.c0 = x;
+    ns.beta = 2.0;
+    launch_zgemm(D, ns, s);
+    std::swap(x, xn);
+  }
+  // C_l = S_l W into the mproj slices, then z and t
+  ZG cl = zg(L.S, LM, 0, L.work2, LM, 0, L.mproj, LM, ZD_B, ZD_B, ZD_B, ZL_EIG);
+  cl.nl = D.maxD;
+  cl.la = 16LL * L.LDM * L.LDM;
+  cl.lc = 16LL * L.LDR * L.LDM;
+  launch_zgemm(D, cl, s);
+  note_launch();
+  k_eig_z<<<D.nprob, 128, 0, s>>>(D);
 }

@@ -351,9 +351,11 @@ __global__ void __launch_bounds__(512) k_toeplitz_fft(Dev D, int adjoint, int xb
   float2* tw = a + fft_points(p);                 // exp(-2 pi i q / L), q < L
   for (int q = threadIdx.x; q < L; q += blockDim.x) tw[q] = D.ftw[q * (D.fLT / L)];
   __syncthreads();
-  int ldx, ldy;
-  const float2* X = fbuf(D, xbuf, p, ldx) + (long long)col * ldx;
-  float2* Y = fbuf(D, ybuf, p, ldy) + (long long)col * ldy;
+  int ldx = 0, ldy = 0;
+  const float2* X = fbuf(D, xbuf, p, ldx);      // sets ldx: the offset is added afterwards
+  float2* Y = fbuf(D, ybuf, p, ldy);
+  X += (long long)col * ldx;
+  Y += (long long)col * ldy;
   fft_forward_column(a, L, P, d, n, X, D.fhat + p.foff, adjoint, tw);
   fft_inverse_column(a, L, P, d, y_ext ? n + 2 : n + 1, Y, 1.0f / (float)Ld, tw);
 }

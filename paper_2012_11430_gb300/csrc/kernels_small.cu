@@ -28,7 +28,7 @@ __device__ inline void set_status(ProbState& s, int st) {
 // column l = A[:, i] / sqrt(A[i][i]) goes to shared memory and the trailing block takes the rank-1
 // update A[j][k] -= l_j conj(l_k).  R^{-1} (R = L^H) is formed by one warp per column with the
 // partial sums of the back substitution spread over the lanes.
-__global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int mode, double tol, int rank_mode) {
+__global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int mode_in, double tol, int rank_mode) {
   extern __shared__ float2 A[];                 // [w][LDR]
   __shared__ int perm[PRONY_RMAX];
   __shared__ float2 lcol[PRONY_RMAX];
@@ -37,6 +37,9 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   const ProbDesc& p = D.P[blockIdx.x];
   ProbState& st = D.st[blockIdx.x];
   if (st.done) return;
+  // QR_AUTO: the rank step (column pivoting and rank test, Algorithm 3) on a problem's first
+  // power iteration, plain CholeskyQR afterwards
+  const int mode = mode_in == QR_AUTO ? (st.iter == 0 ? QR_RANK : QR_PLAIN) : mode_in;
   const int w = swidth(st, p, wsel);
   const int LR = D.L.LDR;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

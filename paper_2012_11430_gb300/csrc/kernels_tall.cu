@@ -94,10 +94,21 @@ __global__ void k_prep(Dev D) {
     if (inI) accF += a2;
   }
   double sT = block_sum(accT, sh);
-  if (threadIdx.x == 0) atomicAdd(&D.st[pi].normT2, sT);
   double sF = block_sum(accF, sh);
-  if (threadIdx.x == 0) atomicAdd(&D.st[pi].normf2, sF);
   if (bad) atomicOr(&D.st[pi].nonfinite, 1);
+  // block sums in fixed block order
+  double2* slot = (double2*)red_region(D, pi);
+  if (threadIdx.x == 0 && ws_ok(D, 16LL * (blockIdx.x + 1) <= D.red_stride, 11)) slot[blockIdx.x] = make_double2(sT, sF);
+  if (red_arrive(D, pi, gridDim.x) && threadIdx.x == 0) {
+    double t2 = 0.0, f2 = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const double2 v = __ldcg(slot + b);
+      t2 += v.x;
+      f2 += v.y;
+    }
+    D.st[pi].normT2 = t2;
+    D.st[pi].normf2 = f2;
+  }
 }
 
 // V_0 entry (i, j) = complex normal from Philox counter i*r0 + j (Algorithm 3 start block).
@@ -192,6 +203,8 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
   const int RG = max(1, min(RS, nthr / per_batch));    // row groups (1 when tiles >= threads)
   const int nbatch = (ntile + per_batch - 1) / per_batch;
   double2* out = (double2*)(D.small + p.soff + out_off);
+  float2* mine = (float2*)red_region(D, pi) + (size_t)blockIdx.x * a * b;   // this block's partial Gram
+  const bool mine_ok = ws_ok(D, 8LL * a * b * (blockIdx.x + 1) <= D.red_stride, 12);
   // staging role: one row, columns c0, c0 + cstep, ... (k-th: X column if below a, else Z)
   const int my_rr = threadIdx.x % RS, c0 = threadIdx.x / RS, cstep = nthr / RS;
   float2 held[GRAM_KMAX];
@@ -311,14 +324,27 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
           const int ia = ti + NA * i, jb = tj + NB * j;
           if (ia < a && jb < b) {
             const float2 v = upk2(acc[i][j]);
-            atomicAdd(&out[ia * out_ld + jb].x, (double)v.x);
-            atomicAdd(&out[ia * out_ld + jb].y, (double)v.y);
-            if (sym && ti != tj) {                // mirror entry of a tile above the diagonal
-              atomicAdd(&out[jb * out_ld + ia].x, (double)v.x);
-              atomicAdd(&out[jb * out_ld + ia].y, -(double)v.y);
+            if (mine_ok) {
+              mine[ia * b + jb] = v;
+              if (sym && ti != tj) mine[jb * b + ia] = make_float2(v.x, -v.y);   // mirror of a tile above the diagonal
             }
           }
         }
+    }
+  }
+  // the blocks' partial Grams (one slot of a x b each) added in block order, in FP64
+  const int nblk = (p.N + chunk - 1) / chunk;
+  if (red_arrive(D, pi, nblk)) {
+    const float2* slots = (const float2*)red_region(D, pi);
+    for (int e = threadIdx.x; e < a * b; e += blockDim.x) {
+      double sx = 0.0, sy = 0.0;
+      for (int k = 0; k < nblk; ++k) {
+        const float2 v = __ldcg(slots + (size_t)k * a * b + e);
+        sx += (double)v.x;
+        sy += (double)v.y;
+      }
+      double2* o = &out[(e / b) * out_ld + e % b];
+      *o = make_double2(o->x + sx, o->y + sy);
     }
   }
 }
@@ -420,7 +446,14 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
   }
   if (norm_only) {
     double t = block_sum(nrm, shr);
-    if (threadIdx.x == 0) atomicAdd(&s.resid2, t);
+    double* slot = (double*)red_region(D, pi);
+    if (threadIdx.x == 0 && ws_ok(D, 8LL * (blockIdx.x + 1) <= D.red_stride, 13)) slot[blockIdx.x] = t;
+    const int nblk = (p.N + rows - 1) / rows;
+    if (red_arrive(D, pi, nblk) && threadIdx.x == 0) {
+      double r2 = 0.0;
+      for (int k = 0; k < nblk; ++k) r2 += __ldcg(slot + k);
+      s.resid2 = r2;
+    }
   }
 }
 
@@ -527,12 +560,20 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
     part[threadIdx.x] = acc;
     __syncthreads();
     double2* b = (double2*)(D.small + p.soff + D.L.rhs);
-    if (i < m && q == 0) {
+    double2* slots = (double2*)red_region(D, pi);
+    if (i < m && q == 0 && ws_ok(D, 16LL * m * (blockIdx.x + 1) <= D.red_stride, 14)) {
       double2 sum = make_double2(0.0, 0.0);
       for (int u = 0; u < tpi; ++u) sum = cadd(sum, part[threadIdx.x + u]);
-      atomicAdd(&b[i].x, sum.x);
-      atomicAdd(&b[i].y, sum.y);
+      slots[(size_t)blockIdx.x * m + i] = sum;
     }
+    // block sums of b in block order
+    const int nblk = (p.N + RHS_ROWS - 1) / RHS_ROWS;
+    if (red_arrive(D, pi, nblk))
+      for (int ii = threadIdx.x; ii < m; ii += blockDim.x) {
+        double2 sum = b[ii];
+        for (int k = 0; k < nblk; ++k) sum = cadd(sum, __ldcg(slots + (size_t)k * m + ii));
+        b[ii] = sum;
+      }
   } else {
     double r2 = 0.0;
     for (int rr = threadIdx.x; rr < nrows; rr += blockDim.x) {
@@ -542,7 +583,14 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
       r2 += cabs2(v);
     }
     double tot = block_sum(r2, shr);
-    if (threadIdx.x == 0) atomicAdd(&s.ls_num2, tot);
+    double* slot = (double*)red_region(D, pi);
+    if (threadIdx.x == 0 && ws_ok(D, 8LL * (blockIdx.x + 1) <= D.red_stride, 15)) slot[blockIdx.x] = tot;
+    const int nblk = (p.N + RHS_ROWS - 1) / RHS_ROWS;
+    if (red_arrive(D, pi, nblk) && threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int k = 0; k < nblk; ++k) sum += __ldcg(slot + k);
+      s.ls_num2 = sum;
+    }
   }
 }
 
@@ -689,32 +737,62 @@ void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_
   k_zero_small<<<g, 256, 0, s>>>(D, off, bytes);
 }
 
-void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
-                 int out_ld, cudaStream_t s) {
-  static size_t set = 0;
+// The dynamic shared memory attribute of k_gram only ever grows (a launch needs it to cover its
+// own size; lowering it for a smaller batch would make a later larger launch fail).
+static size_t g_gram_attr = 0;
+static void gram_attr(size_t sm) {
+  if (sm > g_gram_attr) {
+    cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    g_gram_attr = sm;
+  }
+}
+
+// Launch geometry of k_gram for a batch: dynamic shared memory, rows per block and blocks per
+// problem (the batch fills the resident blocks once, at least RS rows per block).
+static void gram_geometry(const Dev& D, size_t& sm, int& chunk, int& nblk) {
   static std::map<size_t, int> slots_for;      // shared memory size -> resident blocks on the GPU
   // two buffers of staged rows of X and Z (float4 per value); afterwards the same space holds the
   // row-group partial sums, (RG - 1) x tiles x 16 packed entries with RG = min(RS, 256 / tiles):
   // fewer than 256 x 16
   const int RS = gram_rows(D.L.LDR);
-  const size_t sm = std::max(sizeof(float4) * (4 * (size_t)D.L.LDR * (RS + 1)), sizeof(unsigned long long) * 256 * 16);
-  if (sm > set) {
-    cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    set = sm;
-  }
+  sm = std::max(sizeof(float4) * (4 * (size_t)D.L.LDR * (RS + 1)), sizeof(unsigned long long) * 256 * 16);
   auto it = slots_for.find(sm);
   if (it == slots_for.end()) {
     int occ = 1, dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram, 256, sm);
+    gram_attr(sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gram, 256, sm) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 2;
+    }
     it = slots_for.emplace(sm, std::max(1, occ) * sms).first;
   }
-  // rows per block: the batch fills the resident blocks once (one wave), at least RS rows
   const int per_prob = std::max(1, it->second / std::max(1, D.nprob));
-  int chunk = std::max(RS, (D.maxN + per_prob - 1) / per_prob);
+  chunk = std::max(RS, (D.maxN + per_prob - 1) / per_prob);
   chunk = (chunk + RS - 1) / RS * RS;
-  dim3 g((D.maxN + chunk - 1) / chunk, D.nprob);
+  nblk = (D.maxN + chunk - 1) / chunk;
+}
+
+long long red_bytes_per_problem(const Dev& D) {
+  size_t sm;
+  int chunk, nblk;
+  gram_geometry(D, sm, chunk, nblk);
+  long long b = (long long)nblk * D.L.LDR * D.L.LDR * (long long)sizeof(float2);           // k_gram
+  b = std::max<long long>(b, 64LL * sizeof(double2));                                         // k_prep (<= 64 blocks)
+  b = std::max<long long>(b, (D.maxN + 63) / 64 * (long long)sizeof(double));                // k_apply norms
+  b = std::max<long long>(b, (D.maxN + RHS_ROWS - 1) / RHS_ROWS * (long long)std::max(1, D.L.LDM) *
+                                 (long long)sizeof(double2));                                  // k_rhs
+  return (b + 255) / 256 * 256;
+}
+
+void launch_gram(const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw, long long out_off,
+                 int out_ld, cudaStream_t s) {
+  size_t sm;
+  int chunk, nblk;
+  gram_geometry(D, sm, chunk, nblk);
+  gram_attr(sm);
+  dim3 g(nblk, D.nprob);
   note_launch();
   k_gram<<<g, 256, sm, s>>>(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld, chunk);
 }

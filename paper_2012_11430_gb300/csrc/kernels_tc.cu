@@ -10,14 +10,11 @@
 //
 // B' depends on the problem and the K chunk only, so one small kernel (k_xb_prep) writes it once
 // per product, already in the shared-memory image the MMA reads (planes stacked, rows of 128
-// bytes, 128-byte swizzle), one contiguous tile per K chunk; a CTA moves its share of a stage
-// with one bulk copy.  The CTAs of a thread-block cluster work on consecutive 128-row tiles of
-// the same problem and K range: each copies a share of every B' stage and multicasts it to all,
-// which divides the L2 -> SM traffic of B' by the cluster size.
+// bytes, 128-byte swizzle), one contiguous tile per K chunk; a CTA moves a stage with one bulk
+// copy.
 //
 // One CTA = 128 output rows x all 2w columns x a range of K chunks.  Warp roles:
-//   warp 0      bulk copies: the CTA's window of the split-plane sample tables and its share of
-//               every B' stage (multicast)
+//   warp 0      bulk copies: the CTA's window of the split-plane sample tables and every B' stage
 //   warp 1      MMA issue (one thread): tcgen05.mma, A from tensor memory, B from shared memory
 //   warps 2-9   A' producers: each chunk's Toeplitz tile is gathered from the window (its BF16
 //               planes are split once per solve, k_split_tables, two input points per word) and
@@ -26,8 +23,9 @@
 // The Toeplitz matrix is never formed in HBM: each A' element is F at grid index gk(k) - gh(h).
 // A pipeline stage is one K chunk (its B' tile in shared memory and its A' tile in tensor
 // memory); one full and one empty mbarrier per stage; every wait is bounded.
-// A CTA whose tile lies past the last row of its problem (a cluster filler) only loads and
-// releases its share of B'.
+// Split K: the CTAs of one row tile (consecutive jobs) each store their FP32 partial tile in a
+// workspace slot; the last of them to finish (a per-tile arrival counter) adds the partials in
+// the order of their K ranges and writes Y, so results do not depend on which CTA ends first.
 #include "common.cuh"
 #include "tc_ptx.cuh"
 #include "../../include/prony.h"
@@ -242,7 +240,9 @@ struct TcParams {
   int ntbox;                      // B' rows reserved per plane and problem (>= every NT)
   int win_cap;                    // window capacity (words per table, a multiple of 4)
   int stages;                     // B stages in shared memory (A stages: from the TMEM left by D)
-  int cs;                         // cluster size (CTAs sharing the B' stages)
+  float* part;                    // split K: one partial tile (ntbox columns x 128 rows) per job
+  int* cnt;                       // split K: arrivals per row tile, indexed by its first job (zero between launches)
+  long long part_jobs;            // split K: jobs the workspace holds
 };
 
 // Tensor-memory layout of a CTA whose B' tile has NT rows per plane.  With the planes stacked
@@ -264,6 +264,24 @@ __device__ inline TcLayout tc_layout(int NT) {
   return t;
 }
 
+// 16 accumulator columns c0..c0+15 of this thread's TMEM lane, the per-plane blocks summed.
+template <int NPL>
+__device__ __forceinline__ void tc_load_acc(uint32_t taddr, bool stacked, int NT, float* v) {
+  uint32_t u[16];
+  tmem_ld_x16(taddr, u);
+  tmem_ld_wait();
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(u[e]);
+  if (stacked) {
+    for (int b = 1; b < NPL; ++b) {
+      tmem_ld_x16(taddr + b * NT, u);
+      tmem_ld_wait();
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] += __uint_as_float(u[e]);
+    }
+  }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P, int* err) {
@@ -277,11 +295,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint64_t bar_win, bar_d;
   __shared__ uint64_t bar_full[TC_MAXSTAGE], bar_empty[TC_MAXSTAGE];
   __shared__ uint32_t s_tmem;
-  __shared__ int s_err;
+  __shared__ int s_err, s_last;
   __shared__ int ghalf[2 * TC_MAXCH];   // grid offset of each half chunk on one grid line, else -1
 
-  // Everything that decides an early return depends on the problem and K range only, which the
-  // CTAs of a cluster share, so a cluster returns as a whole.
   const ToeplitzJob job = jobs[blockIdx.x];
   const ProbDesc& p = D.P[job.prob];
   const ProbState& st = D.st[job.prob];
@@ -291,29 +307,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int L = P.y_ext ? p.n + 2 : p.n + 1;
   const int rows_total = P.y_ext ? p.Next : p.N;
   const int row0 = job.mt * TC_BM;
+  if (row0 >= rows_total) return;
   const int nc = (p.N + 31) / 32;
   const int cper = (nc + job.nks - 1) / job.nks;
   const int c_begin = job.ks * cper, c_end = min(nc, c_begin + cper);
-  if (c_begin >= c_end) return;
-  const int nchunks = c_end - c_begin;
+  const int nchunks = max(0, c_end - c_begin);
   const int NT = ((2 * w + 15) / 16) * 16;
   const TcLayout lay = tc_layout<KIND>(NT);
   // One pipeline stage = one K chunk: its B' tile in shared memory and its A' tile in tensor
   // memory, filled together (full barrier: eight A' warps + the loader's byte count) and
   // released together by one commit of the MMAs that read them.
   const int S = min(P.stages, lay.sa);
-  const int CS = P.cs;
-  const uint32_t crank = CS > 1 ? cluster_ctarank() : 0u;
-  const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
-  bool filler = row0 >= rows_total;
-  if (nchunks > TC_MAXCH || NT > P.ntbox || S < 1) {   // host sizing rules these out (cluster-uniform)
+  if (nchunks > TC_MAXCH || NT > P.ntbox || S < 1) {   // host sizing rules these out
     if (threadIdx.x == 0) atomicExch(err, 3);
     return;
   }
 
   // window of grid indices needed by this CTA: [gk(first row) - gh(last h), gk(last row) - gh(first h)]
   int wlo = 0, wlen = 0;
-  if (!filler) {
+  bool idle = nchunks == 0;                     // an empty K range (a split wider than the problem)
+  if (!idle) {
     const int last_row = min(rows_total, row0 + TC_BM) - 1;
     const int h_first = 32 * c_begin, h_last = min(p.N, 32 * c_end) - 1;
     wlo = grid_of_row(row0, L, p) - grid_of_h(h_last, p);
@@ -322,15 +335,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     wlen = ((whi - wlo + 1) + 3) & ~3;
     if (wlen > P.win_cap) {
       if (threadIdx.x == 0) atomicExch(err, 3);
-      filler = true;
+      idle = true;
     }
   }
+  if (idle && job.nks == 1) return;             // no partial to contribute
   const uint32_t* gtab = (P.adjoint ? D.tabH : D.tabF) + p.toff;
 
-  // shared memory: B stages (1024-aligned, the same offsets in every CTA), then the window of
-  // the split-plane tables.  A B stage holds KHALVES x NPL x NT rows of 128 bytes: for each
-  // 128-byte K segment the planes are stacked with a stride of NT rows, so one descriptor spans
-  // B_0 .. B_{NPL-1}.
+  // shared memory: B stages (1024-aligned), then the window of the split-plane tables.  A B stage
+  // holds KHALVES x NPL x NT rows of 128 bytes: for each 128-byte K segment the planes are
+  // stacked with a stride of NT rows, so one descriptor spans B_0 .. B_{NPL-1}.
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
@@ -338,8 +351,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t half_bytes = (uint32_t)(NPL * NT) * 128u;
   unsigned char* Bs = sm;
   uint32_t* wtab = (uint32_t*)(sm + (size_t)P.stages * stage_bytes);   // table a at wtab + a * win_cap
-
-  if (filler && CS == 1) return;                 // no cluster to serve
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -351,9 +362,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(&bar_d, 1);
     for (int i = 0; i < S; ++i) {
       mbar_init(&bar_full[i], TC_APROD + 1);    // eight A' warps + the loader (with the byte count)
-      mbar_init(&bar_empty[i], CS);             // one release per CTA of the cluster
+      mbar_init(&bar_empty[i], 1);              // the commit of the stage's MMAs
     }
     s_err = 0;
+    s_last = 0;
     fence_barrier_init();
   }
   // grid offset gh of the first of each 16 input points when all 16 lie on one grid line
@@ -364,54 +376,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CS > 1) cluster_sync();                     // every barrier of the cluster is initialised
   tc_fence_after();
   const uint32_t tb = s_tmem;
 
   if (warp == 0) {
-    // ------------------------------------------------------------- bulk copies: window and B' share
-    if (lane == 0) {
-      if (!filler) {
-        mbar_arrive_expect_tx(&bar_win, (uint32_t)(K::NTAB * wlen) * 4u);
+    // ------------------------------------------------------------- bulk copies: window and B' stages
+    if (lane == 0 && !idle) {
+      mbar_arrive_expect_tx(&bar_win, (uint32_t)(K::NTAB * wlen) * 4u);
 #pragma unroll
-        for (int part = 0; part < 2; ++part)
+      for (int part = 0; part < 2; ++part)
 #pragma unroll
-          for (int pl = 0; pl < NPL; ++pl)
-            tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap, gtab + (long long)(GPL * part + pl) * p.Gd4 + wlo,
-                        (uint32_t)wlen * 4u, &bar_win);
-      }
-      // this CTA's share of each B' tile: a contiguous range of whole 1 KB blocks
+        for (int pl = 0; pl < NPL; ++pl)
+          tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap, gtab + (long long)(GPL * part + pl) * p.Gd4 + wlo,
+                      (uint32_t)wlen * 4u, &bar_win);
       const uint32_t tile_bytes = (uint32_t)K::KHALVES * half_bytes;
-      const int kb = (int)(tile_bytes >> 10);
-      const uint32_t off = (uint32_t)((int)crank * kb / CS) << 10;
-      const uint32_t len = (uint32_t)(((int)crank + 1) * kb / CS - (int)crank * kb / CS) << 10;
       const unsigned char* src0 = P.xb + P.prob_stride * job.prob + (size_t)c_begin * tile_bytes;
       int issued = 0;
       int s = 0;
       uint32_t ph = 0;                            // stage and round parity (no divisions in the loop)
       for (int it = 0; it < nchunks; ++it) {
-        // stage s is free once every CTA of the cluster has consumed its previous contents
+        // stage s is free once the MMAs that read its previous contents have completed
         if (it >= S && !mbar_wait_spin(&bar_empty[s], ph ^ 1u, TC_SPIN)) { s_err = 1; break; }
         mbar_arrive_expect_tx(&bar_full[s], tile_bytes);
-        if (len > 0) {
-          unsigned char* dst = Bs + (size_t)s * stage_bytes + off;
-          const unsigned char* src = src0 + (size_t)it * tile_bytes + off;
-          if (CS > 1) tma_load_1d_mc(dst, src, len, &bar_full[s], cmask);
-          else tma_load_1d(dst, src, len, &bar_full[s]);
-        }
+        tma_load_1d(Bs + (size_t)s * stage_bytes, src0 + (size_t)it * tile_bytes, tile_bytes, &bar_full[s]);
         ++issued;
         if (++s == S) { s = 0; ph ^= 1u; }
       }
-      // Tail: the last stages are released by every CTA of the cluster, so every copy into this
-      // CTA and every copy this CTA multicast have landed before it exits.
+      // Tail: the last stages are released by the MMAs that read them, so every copy into this
+      // CTA has landed before it exits.
       if (!s_err)
         for (int it = max(0, issued - S); it < issued; ++it)
           if (!mbar_wait_spin(&bar_empty[it % S], (it / S) & 1, TC_SPIN)) { s_err = 1; break; }
-      if (!filler && !mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
+      if (!mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
-    if (lane == 0) {
+    if (lane == 0 && !idle) {
       uint32_t idesc[NPL];                        // stacked: A_a times B_0..B_{NPL-1-a}
 #pragma unroll
       for (int a = 0; a < NPL; ++a) {
@@ -426,53 +426,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         tc_fence_after();
-        if (!filler) {
-          const uint32_t a0 = tb + lay.acol0 + (uint32_t)s * NPL * K::PCOLS;
-          const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
+        const uint32_t a0 = tb + lay.acol0 + (uint32_t)s * NPL * K::PCOLS;
+        const uint32_t bsm = smem_u32(Bs + (size_t)s * stage_bytes);
 #pragma unroll
-          for (int kk = 0; kk < K::KSTEPS; ++kk) {
-            // K step kk: 8 TMEM columns of A; 32 bytes into the 128-byte segment kk / 4 of B
-            const uint32_t bseg = bsm + (uint32_t)(kk >> 2) * half_bytes;
-            const uint64_t bdk = sdesc_sw128(bseg) + 2 * (kk & 3);
-            const uint32_t first = (it == 0 && kk == 0) ? 0u : 1u;
-            if (lay.stacked) {
+        for (int kk = 0; kk < K::KSTEPS; ++kk) {
+          // K step kk: 8 TMEM columns of A; 32 bytes into the 128-byte segment kk / 4 of B
+          const uint32_t bseg = bsm + (uint32_t)(kk >> 2) * half_bytes;
+          const uint64_t bdk = sdesc_sw128(bseg) + 2 * (kk & 3);
+          const uint32_t first = (it == 0 && kk == 0) ? 0u : 1u;
+          if (lay.stacked) {
 #pragma unroll
-              for (int a = 0; a < NPL; ++a)
-                mma_ts(K::TF32, tb, a0 + a * K::PCOLS + 8 * kk, bdk, idesc[a], (a > 0) ? 1u : first);
-            } else {
+            for (int a = 0; a < NPL; ++a)
+              mma_ts(K::TF32, tb, a0 + a * K::PCOLS + 8 * kk, bdk, idesc[a], (a > 0) ? 1u : first);
+          } else {
 #pragma unroll
-              for (int pr = 0; pr < NPROD; ++pr) {
-                const uint64_t bd = sdesc_sw128(bseg + (uint32_t)(PB[pr] * NT) * 128u) + 2 * (kk & 3);
-                mma_ts(K::TF32, tb, a0 + PA[pr] * K::PCOLS + 8 * kk, bd, idesc[0], (pr > 0) ? 1u : first);
-              }
+            for (int pr = 0; pr < NPROD; ++pr) {
+              const uint64_t bd = sdesc_sw128(bseg + (uint32_t)(PB[pr] * NT) * 128u) + 2 * (kk & 3);
+              mma_ts(K::TF32, tb, a0 + PA[pr] * K::PCOLS + 8 * kk, bd, idesc[0], (pr > 0) ? 1u : first);
             }
           }
         }
-        // release the stage (B' in every CTA of the cluster, A' here) once these MMAs are done;
-        // a filler CTA issued none and releases its copy of the stage directly
-        if (filler) {
-          for (int r = 0; r < CS; ++r) mbar_arrive_remote(&bar_empty[s], (uint32_t)r);
-        } else if (CS > 1) {
-          tc_commit_mc(&bar_empty[s], cmask);
-        } else {
-          tc_commit(&bar_empty[s]);
-        }
+        tc_commit(&bar_empty[s]);                 // releases the stage once these MMAs are done
         if (++s == S) { s = 0; ph ^= 1u; }
       }
-      if (!filler) tc_commit(&bar_d);      // arrives when every MMA issued above has completed
+      tc_commit(&bar_d);                          // arrives when every MMA issued above has completed
     }
   } else {
     // ------------------------------------------------------------- A' producers + epilogue
     // Warps 2..9: quadrant q = warp & 3 (TMEM lanes 32q..32q+31 = tile rows), half hh of every
-    // K chunk (input points 32c + 16hh .. +15).  A filler CTA's warps only signal the stages.
+    // K chunk (input points 32c + 16hh .. +15).
     const int q = warp & 3;
     const int hh = (warp - 2) >> 2;
     const int i = 32 * q + lane;                // row within the tile
     const int row = row0 + i;
-    const bool vrow = row < rows_total && !filler;
+    const bool vrow = row < rows_total;
     const int gk = vrow ? grid_of_row(row, L, p) - wlo : 0;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    bool ok = filler || __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
+    bool ok = idle || __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
     if (!ok) s_err = 1;
     constexpr int NW = K::TF32 ? 16 : 8;          // words per part and plane: 16 points
     int s = 0;
@@ -482,7 +472,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         s_err = 1;
         break;
       }
-      if (!filler) {
+      {
         const int g0 = ghalf[2 * it + hh];
         // TMEM column of (plane pl, part, point j of this half): BF16 two points per column at
         // pl * 32 + part * 16 + hh * 8 + j / 2; TF32 one point per column at pl * 64 + part * 32 + hh * 16 + j
@@ -545,39 +535,73 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (++s == S) { s = 0; ph ^= 1u; }
     }
     // epilogue: D (TMEM) -> Y; the two warps of a quadrant take alternate 16-column groups
-    if (!filler) {
-      if (__all_sync(0xffffffffu, mbar_wait(&bar_d, 0, TC_SPIN)) && !s_err) {
+    const bool dready = idle || __all_sync(0xffffffffu, mbar_wait(&bar_d, 0, TC_SPIN));
+    if (!dready) s_err = 1;
+    int ldy;
+    float2* Y = tc_buf(D, P.ybuf, p, ldy);
+    if (job.nks == 1) {
+      if (dready && !s_err) {
         tc_fence_after();
-        int ldy;
-        float2* Y = tc_buf(D, P.ybuf, p, ldy);
         for (int c0 = 16 * hh; c0 < NT; c0 += 32) {
-          uint32_t v[16];
-          tmem_ld_x16(tb + lane_off + c0, v);
-          tmem_ld_wait();
-          if (lay.stacked) {                      // sum the per-plane column blocks
-            for (int b = 1; b < NPL; ++b) {
-              uint32_t vb[16];
-              tmem_ld_x16(tb + lane_off + b * NT + c0, vb);
-              tmem_ld_wait();
+          float v[16];
+          tc_load_acc<NPL>(tb + lane_off + c0, lay.stacked, NT, v);
+          if (vrow) {
 #pragma unroll
-              for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(vb[e]));
+            for (int e = 0; e < 8; ++e) {
+              const int j = c0 / 2 + e;
+              if (j < w) Y[(long long)j * ldy + row] = make_float2(v[2 * e], v[2 * e + 1]);
             }
+          }
+        }
+      }
+    } else {
+      // split K: this CTA's partial tile (zeros for an empty K range) into its slot, column-major
+      // (coalesced over the rows of a warp); then one arrival on the tile's counter
+      const size_t slot = (size_t)P.ntbox * TC_BM;
+      float* mine = P.part + (size_t)blockIdx.x * slot;
+      const bool mine_ok = ws_ok(D, (long long)blockIdx.x - job.ks + job.nks <= P.part_jobs && job.ks < job.nks, 21);
+      if (dready && !s_err && !idle) tc_fence_after();
+      for (int c0 = 16 * hh; c0 < NT; c0 += 32) {
+        float v[16];
+        if (dready && !s_err && !idle) {
+          tc_load_acc<NPL>(tb + lane_off + c0, lay.stacked, NT, v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = 0.f;
+        }
+        if (mine_ok) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) mine[(size_t)(c0 + e) * TC_BM + i] = v[e];
+        }
+      }
+      __threadfence();
+      named_bar_sync(1, 32 * TC_APROD);
+      const int first_job = blockIdx.x - job.ks;  // the tile's CTAs are consecutive jobs
+      if (warp == 2 && lane == 0) s_last = mine_ok && atomicAdd(&P.cnt[first_job], 1) == job.nks - 1;
+      named_bar_sync(1, 32 * TC_APROD);
+      if (s_last) {
+        // every other CTA of the tile has stored its partial (fence before its arrival): add the
+        // partials in the order of their K ranges
+        __threadfence();
+        const float* base = P.part + (size_t)first_job * slot;
+        for (int c0 = 16 * hh; c0 < NT; c0 += 32) {
+          float v[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = __ldcg(base + (size_t)(c0 + e) * TC_BM + i);
+          for (int k = 1; k < job.nks; ++k) {
+            const float* src = base + (size_t)k * slot + (size_t)c0 * TC_BM + i;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] += __ldcg(src + (size_t)e * TC_BM);
           }
           if (vrow) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int j = c0 / 2 + e;
-              if (j < w) {
-                float2 val = make_float2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
-                float2* yp = &Y[(long long)j * ldy + row];
-                if (job.nks == 1) *yp = val;
-                else atomicAdd(yp, val);
-              }
+              if (j < w) Y[(long long)j * ldy + row] = make_float2(v[2 * e], v[2 * e + 1]);
             }
           }
         }
-      } else {
-        s_err = 1;
+        if (warp == 2 && lane == 0) P.cnt[first_job] = 0;   // ready for the next launch
       }
     }
   }
@@ -587,10 +611,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     tc_fence_after();
     // on an error path, let the MMAs already issued finish before the columns are released
-    if (s_err && !filler) mbar_wait(&bar_d, 0, TC_SPIN);
+    if (s_err && !idle) mbar_wait(&bar_d, 0, TC_SPIN);
     tmem_dealloc(tb, 512);
   }
-  if (CS > 1) cluster_sync();                     // no CTA leaves while a peer may still signal it
 }
 
 }  // namespace
@@ -636,26 +659,18 @@ static cudaError_t launch_tc_kind(const Dev& D, const ToeplitzJob* jobs, int njo
     if (e != cudaSuccess) return e;
     set = sm;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(njobs);
-  cfg.blockDim = dim3(TC_THREADS);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = P.cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_toeplitz_tc<KIND>, D, jobs, P, err);
+  k_toeplitz_tc<KIND><<<njobs, TC_THREADS, sm, s>>>(D, jobs, P, err);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int wsel,
-                               int ybuf, int y_ext, int kind, int ntbox, int win_cap, int stages, int cs,
-                               const void* xb, long long prob_stride, int* err, cudaStream_t s) {
-  if (nks > 1) launch_zero_buf(D, ybuf, wsel, y_ext, s);
-  TcParams P{(const unsigned char*)xb, prob_stride, adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, cs};
+size_t tc_part_floats(int ntbox) { return (size_t)ntbox * TC_BM; }
+
+cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int wsel, int ybuf,
+                               int y_ext, int kind, int ntbox, int win_cap, int stages, const void* xb,
+                               long long prob_stride, float* part, int* cnt, long long part_jobs, int* err,
+                               cudaStream_t s) {
+  TcParams P{(const unsigned char*)xb, prob_stride, adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, part, cnt,
+             part_jobs};
   const size_t sm = tc_smem_bytes(kind, ntbox, stages, win_cap);
   note_launch();
   switch (kind) {
@@ -663,37 +678,4 @@ cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs,
     case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2>(D, jobs, njobs, P, err, sm, s);
     default: return launch_tc_kind<PRONY_TF32X3>(D, jobs, njobs, P, err, sm, s);
   }
-}
-
-template <int KIND>
-static int max_active_clusters(const cudaLaunchConfig_t& cfg, size_t sm) {
-  int n = 0;
-  cudaFuncSetAttribute(k_toeplitz_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (cudaOccupancyMaxActiveClusters(&n, k_toeplitz_tc<KIND>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
-}
-
-// Largest cluster size (<= want) for which `cs` CTAs with this shared memory fit on the GPU at once.
-int tc_max_cluster(int kind, int want, size_t sm) {
-  for (int cs = want; cs > 1; cs /= 2) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs * 16);
-    cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = sm;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = kind == PRONY_BF16X3 ? max_active_clusters<PRONY_BF16X3>(cfg, sm)
-            : kind == PRONY_BF16X2 ? max_active_clusters<PRONY_BF16X2>(cfg, sm)
-                                   : max_active_clusters<PRONY_TF32X3>(cfg, sm);
-    if (n > 0) return cs;
-  }
-  return 1;
 }

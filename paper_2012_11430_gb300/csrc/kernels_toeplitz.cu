@@ -7,8 +7,10 @@
 // gk(k) - gh(h) with gk(k) = sum_l (k_l + n) G^(d-1-l), gh(h) = sum_l h_l G^(d-1-l).
 //
 // This file holds the FP32 CUDA-core kernel (PRONY_FP32).  Work is a list of
-// jobs (problem, 64-row tile, K split) over all problems of a batch; partial sums
-// of the K splits meet in Y with atomics (Y zeroed per live problem first).
+// jobs (problem, 64-row tile, K split) over all problems of a batch, the K splits of a tile
+// consecutive.  With a K split every CTA of a tile stores its partial sums in a workspace slot
+// and the last to arrive (a per-tile counter) adds them in the order of their K ranges, so the
+// result does not depend on the order in which the CTAs finish.
 #include "common.cuh"
 #include <algorithm>
 #include <climits>
@@ -29,25 +31,10 @@ __device__ inline float2* tbuf(const Dev& D, int buf, const ProbDesc& p, int& ld
 
 __device__ inline int twidth(const ProbState& s, const ProbDesc& p, int sel) { return sel_width(s, p, sel); }
 
-__global__ void k_zero_buf(Dev D, int buf, int wsel, int y_ext) {
-  const ProbDesc& p = D.P[blockIdx.y];
-  const ProbState& s = D.st[blockIdx.y];
-  if (s.done) return;
-  int ld;
-  float2* Yb = tbuf(D, buf, p, ld);
-  const int w = twidth(s, p, wsel);
-  const long long rows = y_ext ? p.Next : p.N;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < rows * w;
-       q += (long long)gridDim.x * blockDim.x) {
-    int c = (int)(q / rows);
-    long long r = q % rows;
-    Yb[(long long)c * ld + r] = make_float2(0.f, 0.f);
-  }
-}
-
 template <int TN, int TBK>
 __global__ void __launch_bounds__(256) k_toeplitz_simt(Dev D, const ToeplitzJob* jobs, int adjoint, int xbuf,
-                                                       int wsel, int ybuf, int y_ext) {
+                                                       int wsel, int ybuf, int y_ext, float2* part, int* cnt,
+                                                       int maxw, long long part_jobs) {
   constexpr int NCOL = 16 * TN;
   __shared__ int gk[TBM];
   __shared__ int gh[TBK];
@@ -65,7 +52,7 @@ __global__ void __launch_bounds__(256) k_toeplitz_simt(Dev D, const ToeplitzJob*
   if (row0 >= rows_total) return;
   const int chunk = ((p.N + job.nks - 1) / job.nks + TBK - 1) / TBK * TBK;
   const int kb = job.ks * chunk, ke = min(p.N, kb + chunk);
-  if (kb >= ke) return;
+  if (kb >= ke && job.nks == 1) return;       // (an empty K range of a split still reports zeros)
   const float2* F = (adjoint ? D.gH : D.gF) + p.grid;
   int ldx, ldy;
   const float2* X = tbuf(D, xbuf, p, ldx);
@@ -135,50 +122,71 @@ __global__ void __launch_bounds__(256) k_toeplitz_simt(Dev D, const ToeplitzJob*
         }
     }
   }
+  if (job.nks == 1) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int row = row0 + ty * 4 + i;
-    if (row >= rows_total) continue;
+    for (int i = 0; i < 4; ++i) {
+      int row = row0 + ty * 4 + i;
+      if (row >= rows_total) continue;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      int c = tx + 16 * j;
-      if (c < w) {
-        float2* yp = &Y[(long long)c * ldy + row];
-        if (job.nks == 1) {
-          *yp = acc[i][j];
-        } else {
-          atomicAdd(&yp->x, acc[i][j].x);
-          atomicAdd(&yp->y, acc[i][j].y);
-        }
+      for (int j = 0; j < TN; ++j) {
+        int c = tx + 16 * j;
+        if (c < w) Y[(long long)c * ldy + row] = acc[i][j];
       }
     }
+    return;
   }
+  // split K: partial tile into this job's slot (column c, row i at c * TBM + i), then one arrival
+  __shared__ int s_last;
+  const size_t slot = (size_t)maxw * TBM;
+  float2* mine = part + (size_t)blockIdx.x * slot;
+  const bool mine_ok = ws_ok(D, (long long)blockIdx.x - job.ks + job.nks <= part_jobs && w <= maxw, 22);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int c = tx + 16 * j;
+      if (c < w && mine_ok) mine[(size_t)c * TBM + ty * 4 + i] = acc[i][j];
+    }
+  __threadfence();
+  __syncthreads();
+  const int first_job = blockIdx.x - job.ks;
+  if (threadIdx.x == 0) s_last = mine_ok && atomicAdd(&cnt[first_job], 1) == job.nks - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const float2* base = part + (size_t)first_job * slot;
+  for (int idx = threadIdx.x; idx < w * TBM; idx += blockDim.x) {
+    const int c = idx / TBM, i = idx % TBM, row = row0 + i;
+    float2 v = __ldcg(base + idx);
+    for (int k = 1; k < job.nks; ++k) {
+      const float2 u = __ldcg(base + (size_t)k * slot + idx);
+      v.x += u.x;
+      v.y += u.y;
+    }
+    if (row < rows_total) Y[(long long)c * ldy + row] = v;
+  }
+  if (threadIdx.x == 0) cnt[first_job] = 0;   // ready for the next launch
 }
 
 template <int TN>
 void run_simt(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int xbuf, int wsel, int ybuf, int y_ext,
-              cudaStream_t s) {
+              float2* part, int* cnt, int maxw, long long part_jobs, cudaStream_t s) {
   constexpr int KB = TN > 5 ? 16 : 32;   // keep the static tiles under 48 KB
   note_launch();
-  k_toeplitz_simt<TN, KB><<<njobs, 256, 0, s>>>(D, jobs, adjoint, xbuf, wsel, ybuf, y_ext);
+  k_toeplitz_simt<TN, KB><<<njobs, 256, 0, s>>>(D, jobs, adjoint, xbuf, wsel, ybuf, y_ext, part, cnt, maxw,
+                                                  part_jobs);
 }
 
 }  // namespace
 
-void launch_zero_buf(const Dev& D, int buf, int wsel, int y_ext, cudaStream_t s) {
-  dim3 g(64, D.nprob);
-  note_launch();
-  k_zero_buf<<<g, 256, 0, s>>>(D, buf, wsel, y_ext);
-}
+size_t simt_part_elems(int maxw) { return (size_t)maxw * TBM; }
 
-void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int nks, int adjoint, int xbuf, int wsel,
-                     int ybuf, int y_ext, int maxw, int precision, cudaStream_t s) {
-  (void)precision;
-  if (nks > 1) launch_zero_buf(D, ybuf, wsel, y_ext, s);
+void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int xbuf, int wsel, int ybuf,
+                     int y_ext, int maxw, float2* part, int* cnt, long long part_jobs, cudaStream_t s) {
   int tn = (maxw + 15) / 16;
-  if (tn <= 1) run_simt<1>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, s);
-  else if (tn <= 2) run_simt<2>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, s);
-  else if (tn <= 3) run_simt<3>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, s);
-  else if (tn <= 5) run_simt<5>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, s);
-  else run_simt<8>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, s);
+  if (tn <= 1) run_simt<1>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, part, cnt, maxw, part_jobs, s);
+  else if (tn <= 2) run_simt<2>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, part, cnt, maxw, part_jobs, s);
+  else if (tn <= 3) run_simt<3>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, part, cnt, maxw, part_jobs, s);
+  else if (tn <= 5) run_simt<5>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, part, cnt, maxw, part_jobs, s);
+  else run_simt<8>(D, jobs, njobs, adjoint, xbuf, wsel, ybuf, y_ext, part, cnt, maxw, part_jobs, s);
 }

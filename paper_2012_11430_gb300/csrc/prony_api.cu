@@ -23,6 +23,7 @@
 #include <tuple>
 #include <vector>
 #include <atomic>
+#include <functional>
 
 namespace {
 
@@ -69,6 +70,9 @@ struct prony_ctx {
   cudaStream_t stream = nullptr;
   DBuf grid64, gF, gH, V, U, B1, B2, Y, small, P, st, jobs, flag, tout, cout, misc, misc2, misc3;
   DBuf xb, tabF, tabH, tcjobs, tcerr;   // tensor-core path: B' planes, split sample tables, jobs, error flag
+  DBuf part, cnt;                       // split K products: partial tiles per job, arrival counters per tile
+  DBuf red, rcnt;                       // fixed-order cross-block sums: partials and counters per problem
+  DBuf oob;                             // first failed workspace bound check of a kernel (0: none)
   DBuf fhat, ftw;                       // FFT path: sample transforms, twiddles
   int* h_flag = nullptr;            // pinned
   std::vector<ProbState> h_st;
@@ -81,8 +85,8 @@ struct prony_ctx {
   prony_stats stats{};
   long long launch_base = 0;
   cudaError_t launch_err = cudaSuccess;   // first failed tensor-core launch of the current call
-  std::map<std::string, std::pair<int, int>> tc_tuned;   // batch shape -> (cluster size, K split)
-  // the tensor-core job list on the device: (cs, nks, P, then n and d of every problem) it was
+  std::map<std::string, int> tc_tuned;   // batch shape -> K split
+  // the tensor-core job list on the device: (nks, P, then n and d of every problem) it was
   // built for, and its ext / in counts (a repeated batch layout skips the rebuild and the upload)
   std::vector<int> tcjob_sig;
   int tcjob_next = 0, tcjob_nin = 0;
@@ -94,12 +98,13 @@ struct prony_ctx {
     double lambda0;
   } lm_key{};
   cudaGraphExec_t lm_exec = nullptr;
-  // device-side loops (0: power iterations 2.., 1: Lanczos steps) of the last batch layout
-  struct LoopGraph {
+  // the whole solve as one CUDA graph, for the last batch layout and options
+  struct SolveGraph {
     std::string key;
     cudaGraphExec_t exec = nullptr;
-    int body_launches = 0;
-  } loops[2];
+    long long fixed_launches = 0, body_launches[2] = {0, 0};
+    bool has_loop[2] = {false, false};
+  } solve_graph;
 };
 
 namespace {
@@ -131,10 +136,10 @@ long long ipow(long long b, int e) {
 // Tensor-core configuration of a batch (split BF16 planes).
 struct TcConf {
   bool on = false;
-  bool tuned = false;                 // cs / nks chosen (from the context's cache or by timing)
-  int nks_min = 1, cs_max = 1;        // tuning range
+  bool tuned = false;                 // nks chosen (from the context's cache or by timing)
+  int nks_min = 1;                    // tuning range: nks_min, 2 nks_min
   std::string key;                    // batch shape signature
-  int kind = PRONY_BF16X3, ntbox = 16, stages = 2, win_cap = 0, nks = 1, cs = 1;
+  int kind = PRONY_BF16X3, ntbox = 16, stages = 2, win_cap = 0, nks = 1;
   long long prob_stride = 0;          // bytes of B' tiles per problem
   int njobs_ext = 0, njobs_in = 0;
   ToeplitzJob* jobs_ext = nullptr;
@@ -149,6 +154,9 @@ struct Batch {
   ToeplitzJob* jobs_ext = nullptr;
   ToeplitzJob* jobs_in = nullptr;
   int maxw = 0;
+  float2* part = nullptr;             // split K workspace of the products (FP32 path / tensor-core path)
+  int* cnt = nullptr;
+  long long part_jobs = 0;            // jobs the split K workspace holds
   TcConf tc;
   struct FftConf {
     bool on = false;  // every Toeplitz product by FFT (PRONY_FFT32)
@@ -200,8 +208,22 @@ int max_window(const ProbDesc& p, int L, int nks) {
   return mx;
 }
 
-// Job list of the tensor-core products for a cluster size and K split: per problem and K range,
-// its 128-row tiles padded to a multiple of the cluster size (mt >= tiles: filler CTA).
+// Split K workspace for `njobs` jobs of `slot_bytes` each: partial tiles and zeroed arrival
+// counters (every product launch leaves its counters zeroed again).
+int ensure_split_ws(prony_ctx* ctx, Batch& B, size_t njobs, size_t slot_bytes) {
+  int rc;
+  if ((rc = ensure(ctx->part, njobs * slot_bytes))) return rc;
+  const size_t cap = ctx->cnt.cap;
+  if ((rc = ensure(ctx->cnt, sizeof(int) * njobs))) return rc;
+  if (ctx->cnt.cap != cap) CK(cudaMemsetAsync(ctx->cnt.p, 0, ctx->cnt.cap, ctx->stream));
+  B.part = (float2*)ctx->part.p;
+  B.cnt = (int*)ctx->cnt.p;
+  B.part_jobs = (long long)std::min(ctx->part.cap / std::max<size_t>(1, slot_bytes), ctx->cnt.cap / sizeof(int));
+  return PRONY_OK;
+}
+
+// Job list of the tensor-core products for a K split: per problem, its 128-row tiles, and per
+// tile its K ranges as consecutive jobs.
 // Grows the tensor-core job buffer; a reallocation invalidates the job list it held.
 static int ensure_tcjobs(prony_ctx* ctx, size_t bytes) {
   const size_t cap = ctx->tcjobs.cap;
@@ -210,51 +232,49 @@ static int ensure_tcjobs(prony_ctx* ctx, size_t bytes) {
   return rc;
 }
 
-int tc_set_jobs(prony_ctx* ctx, Batch& B, int cs, int nks) {
+int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
   TcConf& T = B.tc;
   std::vector<int> sig;
-  sig.reserve(3 + 2 * B.P.size());
-  sig.push_back(cs);
+  sig.reserve(2 + 2 * B.P.size());
   sig.push_back(nks);
   sig.push_back((int)B.P.size());
   for (const auto& p : B.P) {
     sig.push_back(p.n);
     sig.push_back(p.d);
   }
+  int rc;
   if (ctx->tcjobs.p && sig == ctx->tcjob_sig) {
     T.njobs_ext = ctx->tcjob_next;
     T.njobs_in = ctx->tcjob_nin;
     T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
     T.jobs_in = T.jobs_ext + T.njobs_ext;
-    T.cs = cs;
     T.nks = nks;
-    return PRONY_OK;
+  } else {
+    std::vector<ToeplitzJob> jobs;
+    auto add_jobs = [&](bool ext) {
+      for (int i = 0; i < (int)B.P.size(); ++i) {
+        const int tiles = ((ext ? B.P[i].Next : B.P[i].N) + 127) / 128;
+        const int nk = std::min(nks, std::max(1, (B.P[i].N + 31) / 32));
+        for (int mt = 0; mt < tiles; ++mt)
+          for (int ks = 0; ks < nk; ++ks) jobs.push_back({i, mt, ks, nk});
+      }
+    };
+    add_jobs(true);
+    T.njobs_ext = (int)jobs.size();
+    add_jobs(false);
+    T.njobs_in = (int)jobs.size() - T.njobs_ext;
+    if ((rc = ensure_tcjobs(ctx, sizeof(ToeplitzJob) * jobs.size()))) return rc;
+    CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ctx->tcjob_sig = std::move(sig);
+    ctx->tcjob_next = T.njobs_ext;
+    ctx->tcjob_nin = T.njobs_in;
+    T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
+    T.jobs_in = T.jobs_ext + T.njobs_ext;
+    T.nks = nks;
   }
-  std::vector<ToeplitzJob> jobs;
-  auto add_jobs = [&](bool ext) {
-    for (int i = 0; i < (int)B.P.size(); ++i) {
-      const int tiles = ((ext ? B.P[i].Next : B.P[i].N) + 127) / 128;
-      const int padded = (tiles + cs - 1) / cs * cs;
-      const int nk = std::min(nks, std::max(1, (B.P[i].N + 31) / 32));
-      for (int ks = 0; ks < nk; ++ks)
-        for (int mt = 0; mt < padded; ++mt) jobs.push_back({i, mt, ks, nk});
-    }
-  };
-  add_jobs(true);
-  T.njobs_ext = (int)jobs.size();
-  add_jobs(false);
-  T.njobs_in = (int)jobs.size() - T.njobs_ext;
-  int rc;
-  if ((rc = ensure_tcjobs(ctx, sizeof(ToeplitzJob) * jobs.size()))) return rc;
-  CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
-                     ctx->stream));
-  ctx->tcjob_sig = std::move(sig);
-  ctx->tcjob_next = T.njobs_ext;
-  ctx->tcjob_nin = T.njobs_in;
-  T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
-  T.jobs_in = T.jobs_ext + T.njobs_ext;
-  T.cs = cs;
-  T.nks = nks;
+  if (nks > 1)
+    return ensure_split_ws(ctx, B, (size_t)std::max(T.njobs_ext, T.njobs_in), sizeof(float) * tc_part_floats(T.ntbox));
   return PRONY_OK;
 }
 
@@ -331,34 +351,13 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   T.win_cap = win_cap_for(T.stages);
   T.nks_min = nks;
   T.prob_stride = tc_prob_stride(prec, T.ntbox, maxnc);
-  // Cluster sizes: the CTAs of a cluster share the B' stages of one problem and K range; tiles
-  // of a problem are padded to a multiple of the cluster with filler CTAs, so a size is a
-  // candidate only while the fillers stay below 1/8 of the CTAs.
-  int cs_max = 4;
-  if (const char* e = getenv("PRONY_TC_CLUSTER")) {
-    const int v = atoi(e);
-    cs_max = v >= 4 ? 4 : v >= 2 ? 2 : 1;
-  }
-  int cs = 1;
-  for (int c = cs_max; c > 1; c /= 2) {
-    long long real = 0, padded = 0;
-    for (const auto& p : B.P) {
-      const long long te = (p.Next + 127) / 128, ti = (p.N + 127) / 128;
-      real += te + ti;
-      padded += (te + c - 1) / c * c + (ti + c - 1) / c * c;
-    }
-    if (8 * (padded - real) <= padded) { cs = c; break; }
-  }
-  if (cs > 1) cs = tc_max_cluster(prec, cs, tc_smem_bytes(prec, T.ntbox, T.stages, T.win_cap));
-  T.cs_max = cs;
   // batch shape signature for the tuning cache
   T.key = std::to_string(prec) + ":" + std::to_string(B.P.size()) + ":" + std::to_string(maxw) + ":" +
           std::to_string(maxnc) + ":" + std::to_string(tiles_ext) + ":" + std::to_string(tiles_in) + ":" +
-          std::to_string(nks) + ":" + std::to_string(cs);
+          std::to_string(nks);
   auto hit = ctx->tc_tuned.find(T.key);
   T.tuned = hit != ctx->tc_tuned.end() || getenv("PRONY_TC_TUNE") != nullptr && atoi(getenv("PRONY_TC_TUNE")) == 0;
-  const int cs0 = hit != ctx->tc_tuned.end() ? hit->second.first : std::min(2, cs);
-  const int nks0 = hit != ctx->tc_tuned.end() ? hit->second.second : nks;
+  const int nks0 = hit != ctx->tc_tuned.end() ? hit->second : nks;
   int rc;
   long long twords = 64;                              // split-plane tables (+ slack for window rounding)
   for (const auto& p : B.P) twords = std::max(twords, p.toff + 6LL * p.Gd4 + 64);
@@ -370,7 +369,7 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   if ((rc = ensure(ctx->tcerr, 256))) return rc;
   CK(cudaMemsetAsync(ctx->tcerr.p, 0, sizeof(int), ctx->stream));
   T.err = (int*)ctx->tcerr.p;
-  return tc_set_jobs(ctx, B, cs0, nks0);
+  return tc_set_jobs(ctx, B, nks0);
 }
 
 // One Toeplitz block product for every live problem of the batch.
@@ -384,42 +383,37 @@ void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int
   } else if (B.tc.on) {
     const TcConf& T = B.tc;
     launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.kind, T.prob_stride, s);
-    cudaError_t e = launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, T.nks,
-                                       adjoint, wsel, ybuf, ext, T.kind, T.ntbox, T.win_cap, T.stages, T.cs,
-                                       ctx->xb.p, T.prob_stride, T.err, s);
+    cudaError_t e = launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, adjoint,
+                                       wsel, ybuf, ext, T.kind, T.ntbox, T.win_cap, T.stages, ctx->xb.p,
+                                       T.prob_stride, (float*)B.part, B.cnt, B.part_jobs, T.err, s);
     if (e != cudaSuccess && ctx->launch_err == cudaSuccess) ctx->launch_err = e;
   } else {
-    launch_toeplitz(D, ext ? B.jobs_ext : B.jobs_in, ext ? B.njobs_ext : B.njobs_in, B.nks, adjoint, xbuf, wsel, ybuf,
-                    ext, B.maxw, prec, s);
+    launch_toeplitz(D, ext ? B.jobs_ext : B.jobs_in, ext ? B.njobs_ext : B.njobs_in, adjoint, xbuf, wsel, ybuf, ext,
+                    B.maxw, B.part, B.cnt, B.part_jobs, s);
   }
 }
 
 // Autotuner of the tensor-core products: the first product of a batch shape not seen before is
 // timed (CUDA events on the context stream, one untimed and one timed launch per candidate)
-// for every cluster size up to cs_max and the K splits nks_min and 2 nks_min; the fastest
-// configuration is kept for the batch and cached in the context under the shape signature.
+// for the K splits nks_min and 2 nks_min; the faster one is kept for the batch and cached in the
+// context under the shape signature.
 int tc_autotune(prony_ctx* ctx, Batch& B, const Dev& D, int prec, cudaStream_t s) {
   TcConf& T = B.tc;
-  std::vector<std::pair<int, int>> cand;
-  for (int cs = 1; cs <= T.cs_max; cs *= 2)
-    for (int f = 1; f <= 2; ++f) {
-      const int nks = T.nks_min * f;
-      if (f == 2 && (nks > 16 || nks > T.nks_min + 8)) continue;
-      cand.push_back({cs, nks});
-    }
-  // room for the largest job list first, so that no candidate reallocates it
+  std::vector<int> cand = {T.nks_min};
+  if (2 * T.nks_min <= 16 && T.nks_min <= 8) cand.push_back(2 * T.nks_min);
+  // room for the largest job list and split workspace first, so that no candidate reallocates them
   size_t maxjobs = 0;
-  for (const auto& p : B.P)
-    maxjobs += (size_t)2 * T.nks_min * ((p.Next + 127) / 128 + 4 + (p.N + 127) / 128 + 4);
+  for (const auto& p : B.P) maxjobs += (size_t)2 * T.nks_min * ((p.Next + 127) / 128 + (p.N + 127) / 128);
   int rc;
   if ((rc = ensure_tcjobs(ctx, sizeof(ToeplitzJob) * maxjobs))) return rc;
+  if ((rc = ensure_split_ws(ctx, B, maxjobs, sizeof(float) * tc_part_floats(T.ntbox)))) return rc;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  std::pair<int, int> pick = {T.cs, T.nks};
-  for (const auto& c : cand) {
-    if ((rc = tc_set_jobs(ctx, B, c.first, c.second))) break;
+  int pick = T.nks;
+  for (const int c : cand) {
+    if ((rc = tc_set_jobs(ctx, B, c))) break;
     toeplitz_product(ctx, B, D, 1, BUF_V, W_V, BUF_Y, prec, s);
     cudaEventRecord(e0, s);
     toeplitz_product(ctx, B, D, 1, BUF_V, W_V, BUF_Y, prec, s);
@@ -445,7 +439,7 @@ int tc_autotune(prony_ctx* ctx, Batch& B, const Dev& D, int prec, cudaStream_t s
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  if ((rc = tc_set_jobs(ctx, B, pick.first, pick.second))) return rc;
+  if ((rc = tc_set_jobs(ctx, B, pick))) return rc;
   ctx->tc_tuned[T.key] = pick;
   T.tuned = true;
   return PRONY_OK;
@@ -583,8 +577,22 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
   D.small = (char*)ctx->small.p;
   D.L = L;
   D.vand = o.vandermonde ? 1 : 0;
+  // partials of the cross-block sums (Grams, norms, right-hand sides), one region per problem
+  D.red_stride = red_bytes_per_problem(D);
+  if ((rc = ensure(ctx->red, (size_t)D.red_stride * np))) return rc;
+  {
+    const size_t cap = ctx->rcnt.cap;
+    if ((rc = ensure(ctx->rcnt, sizeof(int) * np))) return rc;
+    if (ctx->rcnt.cap != cap) CK(cudaMemsetAsync(ctx->rcnt.p, 0, ctx->rcnt.cap, ctx->stream));
+  }
+  D.red = (char*)ctx->red.p;
+  D.rcnt = (int*)ctx->rcnt.p;
+  D.oob = (int*)ctx->oob.p;
   B.jobs_ext = (ToeplitzJob*)ctx->jobs.p;
   B.jobs_in = B.jobs_ext + B.njobs_ext;
+  if (simt && nks > 1 &&
+      (rc = ensure_split_ws(ctx, B, (size_t)std::max(B.njobs_ext, B.njobs_in), sizeof(float2) * simt_part_elems(B.maxw))))
+    return rc;
   if (o.precision == PRONY_FFT32) return setup_fft(ctx, B);
   if (is_tc(o.precision) && (rc = setup_tc(ctx, B, o.precision, maxR0))) return rc;
   if (o.svd_method == 1 && fft_fits(B)) {
@@ -626,7 +634,8 @@ std::string loop_graph_key(const Batch& B, const int* dflag, int cap, const doub
   put(&B.D, sizeof(Dev));
   put(B.P.data(), sizeof(ProbDesc) * B.P.size());
   const TcConf& T = B.tc;
-  const long long tc[] = {T.on, T.kind, T.ntbox, T.stages, T.win_cap, T.nks, T.cs, T.prob_stride, T.njobs_ext,
+  const long long tc[] = {T.on, T.kind, T.ntbox, T.stages, T.win_cap, T.nks, (long long)(size_t)B.part,
+                          (long long)(size_t)B.cnt, B.part_jobs, T.prob_stride, T.njobs_ext,
                           T.njobs_in, (long long)(size_t)T.jobs_ext, (long long)(size_t)T.jobs_in,
                           (long long)(size_t)T.err, B.fft.on, B.fft.lz, B.fft.maxpts, B.njobs_ext, B.njobs_in, B.nks,
                           B.maxw, (long long)(size_t)B.jobs_ext, (long long)(size_t)B.jobs_in,
@@ -636,22 +645,66 @@ std::string loop_graph_key(const Batch& B, const int* dflag, int cap, const doub
   return k;
 }
 
-// A loop on the device: a graph with a WHILE node whose body is one step (enqueued by `step`,
-// which leaves dflag nonzero once every problem has stopped) followed by the condition kernel,
-// capped at `cap` bodies.  Captured once per key into the context's slot, replayed after.
-template <typename Step>
-int device_loop(prony_ctx* ctx, int slot, const std::string& key, Step& step, int* dflag, int cap, cudaStream_t s) {
-  auto& L = ctx->loops[slot];
-  int* count = (int*)ctx->flag.p + 1 + slot;     // bodies run by this launch
-  if (!L.exec || key != L.key) {
-    if (L.exec) {
-      cudaGraphExecDestroy(L.exec);
-      L.exec = nullptr;
+// The whole solve as one CUDA graph, built from segments enqueued on the context stream: a
+// plain segment becomes a child graph node; a loop segment becomes a WHILE conditional node
+// (after a node that zeroes its body counter) whose body is the segment followed by the
+// condition kernel, which reads the device flag `dflag` (nonzero once every problem has stopped)
+// and caps the loop at `cap` bodies.  The handle's default value is 1: a loop runs at least once.
+// Segments run in order.  Captured once per key into the context, replayed after: one graph
+// launch per solve, no host round trip inside it.
+struct Seg {
+  bool loop;
+  std::function<int()> fn;
+  int cap;
+  int slot;          // loop body counter slot (0: power iterations, 1: Lanczos steps)
+};
+
+int build_solve_graph(prony_ctx* ctx, const std::vector<Seg>& segs, int* dflag, const std::string& key) {
+  auto& G = ctx->solve_graph;
+  cudaStream_t s = ctx->stream;
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+  }
+  G.key.clear();
+  G.fixed_launches = 0;
+  G.body_launches[0] = G.body_launches[1] = 0;
+  G.has_loop[0] = G.has_loop[1] = false;
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphNode_t prev = nullptr;
+  for (const Seg& seg : segs) {
+    const long long before = g_launches.load();
+    if (!seg.loop) {
+      cudaError_t be = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+      if (be != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(be, "cudaStreamBeginCapture");
+      }
+      const int rc = seg.fn();
+      cudaGraph_t child = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(s, &child);
+      const long long n = g_launches.load() - before;
+      note_launches(-n);
+      G.fixed_launches += n;
+      if (ce != cudaSuccess || rc) {
+        if (child) cudaGraphDestroy(child);
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : cuda_fail(ce, "cudaStreamEndCapture");
+      }
+      cudaGraphNode_t node;
+      const cudaError_t ae = cudaGraphAddChildGraphNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, child);
+      cudaGraphDestroy(child);
+      if (ae != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ae, "cudaGraphAddChildGraphNode");
+      }
+      prev = node;
+      continue;
     }
-    cudaGraph_t g;
-    CK(cudaGraphCreate(&g, 0));
+    int* count = (int*)ctx->flag.p + 1 + seg.slot;
     cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     cudaMemsetParams mp = {};
     mp.dst = count;
     mp.value = 0;
@@ -659,39 +712,65 @@ int device_loop(prony_ctx* ctx, int slot, const std::string& key, Step& step, in
     mp.width = 1;
     mp.height = 1;
     cudaGraphNode_t mnode, cnode;
-    CK(cudaGraphAddMemsetNode(&mnode, g, nullptr, 0, &mp));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    CK(cudaGraphAddNode(&cnode, g, &mnode, nullptr, 1, &cp));
-    const long long before = g_launches.load();
-    CK(cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                     cudaStreamCaptureModeRelaxed));
-    int rc = step();
-    launch_loop_cond(h, dflag, count, cap, s);
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&mnode, g, prev ? &prev : nullptr, prev ? 1 : 0, &mp);
+    if (e == cudaSuccess) {
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cnode, g, &mnode, nullptr, 1, &cp);
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "solve graph loop node");
+    }
+    const int rc = seg.fn();
+    launch_loop_cond(h, dflag, count, seg.cap, s);
     cudaGraph_t body;
     const cudaError_t ce = cudaStreamEndCapture(s, &body);
-    L.body_launches = (int)(g_launches.load() - before);
-    note_launches(-L.body_launches);               // counted when the bodies run (below)
-    if (rc || ce != cudaSuccess) {
-      cudaGraphDestroy(g);
+    const long long n = g_launches.load() - before;
+    note_launches(-n);
+    G.body_launches[seg.slot] = n;
+    G.has_loop[seg.slot] = true;
+    if (ce != cudaSuccess) {
+      // a launch inside the body failed and invalidated the capture: the parent graph (whose
+      // conditional body was the capture target) is not destroyed, since the driver may not
+      // handle that; it is left to the process exit
+      cudaGetLastError();
       return rc ? rc : cuda_fail(ce, "cudaStreamEndCapture");
     }
-    const cudaError_t ie = cudaGraphInstantiate(&L.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) {
-      L.exec = nullptr;
-      return cuda_fail(ie, "cudaGraphInstantiate");
+    if (rc) {
+      cudaGraphDestroy(g);
+      return rc;
     }
-    L.key = key;
+    prev = cnode;
   }
-  CK(cudaGraphLaunch(L.exec, s));
-  int runs = 0;
-  CK(cudaMemcpyAsync(&runs, count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  const cudaError_t ie = cudaGraphInstantiate(&G.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    G.exec = nullptr;
+    return cuda_fail(ie, "cudaGraphInstantiate");
+  }
+  G.key = key;
+  return PRONY_OK;
+}
+
+// One replay of the solve graph; the launch statistics count its bodies as they ran.
+int launch_solve_graph(prony_ctx* ctx) {
+  auto& G = ctx->solve_graph;
+  cudaStream_t s = ctx->stream;
+  CK(cudaGraphLaunch(G.exec, s));
+  CK(cudaMemcpyAsync(ctx->h_flag + 1, (int*)ctx->flag.p + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  note_launches((long long)runs * L.body_launches);
+  long long n = G.fixed_launches;
+  for (int k = 0; k < 2; ++k)
+    if (G.has_loop[k]) n += (long long)ctx->h_flag[1 + k] * G.body_launches[k];
+  note_launches(n);
   return PRONY_OK;
 }
 
@@ -727,78 +806,67 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     if (ctx->prof) CK(cudaEventRecord(ctx->events[ev + 1], s));
     return PRONY_OK;
   };
-  int rc;
+  int rc = PRONY_OK;
   if (ctx->prof) {
     ctx->trecs.clear();
     ctx->snaps.clear();
   }
-  launch_prep(D, s);
-  if (B.tc.on) launch_split_tables(D, B.tc.kind, s);
-  if (B.fft.on || B.fft.lz) launch_fft_tables(D, B.fft.maxpts, s);
-  launch_init_v0(D, o.seed, s);
   int* dflag = (int*)ctx->flag.p;
-  if (o.svd_method == 1) {
-    // Algorithm 2: Lanczos bidiagonalisation from the first start column, full
-    // reorthogonalisation (classical Gram-Schmidt twice); its right vectors start the power loop
-    const int cap = std::max(1, D.maxR0);
-    launch_lz_start(D, s);
-    auto reorth = [&](int basis, int wsel) {
-      for (int pass = 0; pass < 2; ++pass) {
-        launch_zero_small(D, D.L.work1, 16LL * D.L.LDR * D.L.LDM, s);
-        launch_gram(D, basis, -1, wsel, BUF_B2, -1, W_ONE, D.L.work1, D.L.LDM, s);
-        launch_apply(D, basis, wsel, W_ONE, D.L.work1, 1, BUF_B2, BUF_B2, 0, s);
-      }
-    };
-    auto lz_product = [&](int adjoint) {                         // B2 = T B1 or T^* B1, one column
-      if (B.fft.lz) launch_toeplitz_fft(D, B.fft.maxpts, 1, adjoint, BUF_B1, W_ONE, BUF_B2, 0, s);
-      else toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, adjoint);
-    };
-    auto lz_step = [&]() -> int {
-      launch_lz_load(D, 0, s);                                       // v_k
-      lz_product(0);                                                 // T v_k
-      launch_lz_axpy(D, 0, s);                                       // - beta_k u_{k-1}
-      reorth(BUF_U, W_LK);
-      launch_lz_accept(D, 0, tol_lanczos, cap, s);                   // alpha_k, u_k
-      launch_lz_load(D, 1, s);                                       // u_k
-      lz_product(1);                                                 // T^* u_k
-      launch_lz_axpy(D, 1, s);                                       // - alpha_k v_k
-      reorth(BUF_V, W_LK1);
-      launch_lz_accept(D, 1, tol_lanczos, cap, s);                   // beta_{k+1}, v_{k+1}
-      CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
-      launch_lz_all_done(D, dflag, s);
-      return PRONY_OK;
-    };
-    if (ctx->prof) {
-      for (int step = 0; step < cap; ++step) {
-        if ((rc = lz_step())) return rc;
-        CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (*ctx->h_flag != 0) break;
-      }
-    } else {
-      // the steps as one CUDA graph with a device-side WHILE loop (no host round trip per step)
-      const double par[] = {tol_lanczos, (double)prec};
-      if ((rc = device_loop(ctx, 1, loop_graph_key(B, dflag, cap, par, 2), lz_step, dflag, cap, s))) return rc;
+  const bool lanczos = o.svd_method == 1;
+  const int lz_cap = std::max(1, D.maxR0);
+
+  // ---- the steps of a solve, each enqueued on the context stream
+  // grid copies and tables, the Philox start block (Algorithm 3: V_0)
+  auto prefix = [&]() -> int {
+    launch_prep(D, s);
+    if (B.tc.on) launch_split_tables(D, B.tc.kind, s);
+    if (B.fft.on || B.fft.lz) launch_fft_tables(D, B.fft.maxpts, s);
+    launch_init_v0(D, o.seed, s);
+    if (lanczos) launch_lz_start(D, s);
+    return PRONY_OK;
+  };
+  // Algorithm 2: one Lanczos step from the first start column, full reorthogonalisation (classical
+  // Gram-Schmidt twice); its right vectors start the power loop
+  auto reorth = [&](int basis, int wsel) {
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_zero_small(D, D.L.work1, 16LL * D.L.LDR * D.L.LDM, s);
+      launch_gram(D, basis, -1, wsel, BUF_B2, -1, W_ONE, D.L.work1, D.L.LDM, s);
+      launch_apply(D, basis, wsel, W_ONE, D.L.work1, 1, BUF_B2, BUF_B2, 0, s);
     }
-    launch_lz_finish(D, s);
-  } else {
-    tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
-  }
-  if (B.tc.on && !B.tc.tuned && (rc = tc_autotune(ctx, B, D, prec, s))) return rc;
-  if ((rc = toeplitz(0, 1))) return rc;
-  if (ctx->prof) {
-    ctx->snaps.emplace_back(D.nprob);
-    CK(cudaMemcpyAsync(ctx->snaps.back().data(), D.st, sizeof(ProbState) * D.nprob, cudaMemcpyDeviceToHost, s));
-  }
+  };
+  auto lz_product = [&](int adjoint) {                         // B2 = T B1 or T^* B1, one column
+    if (B.fft.lz) launch_toeplitz_fft(D, B.fft.maxpts, 1, adjoint, BUF_B1, W_ONE, BUF_B2, 0, s);
+    else toeplitz_product(ctx, B, D, 0, BUF_B1, W_ONE, BUF_B2, prec, s, adjoint);
+  };
+  auto lz_step = [&]() -> int {
+    launch_lz_load(D, 0, s);                                       // v_k
+    lz_product(0);                                                 // T v_k
+    launch_lz_axpy(D, 0, s);                                       // - beta_k u_{k-1}
+    reorth(BUF_U, W_LK);
+    launch_lz_accept(D, 0, tol_lanczos, lz_cap, s);                // alpha_k, u_k
+    launch_lz_load(D, 1, s);                                       // u_k
+    lz_product(1);                                                 // T^* u_k
+    launch_lz_axpy(D, 1, s);                                       // - alpha_k v_k
+    reorth(BUF_V, W_LK1);
+    launch_lz_accept(D, 1, tol_lanczos, lz_cap, s);                // beta_{k+1}, v_{k+1}
+    CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
+    launch_lz_all_done(D, dflag, s);
+    return PRONY_OK;
+  };
+  // V_0 orthonormal (or the Lanczos right vectors), then Y = T V_0
+  auto start = [&]() -> int {
+    if (lanczos) launch_lz_finish(D, s);
+    else tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+    return toeplitz(0, 1);
+  };
   // one power iteration (Algorithm 3); dflag ends nonzero when every problem has stopped
   auto iteration = [&](int it) -> int {
     // U = qr(T V_{k-1})  (rows I_n of Y)
     tall_qr(B, BUF_Y, W_V, W_U, QR_DROP, tol_drop, 0, BUF_U, s);
     // Vbar = T^* U
     if ((rc = toeplitz(it, 0))) return rc;
-    // V = qr(Vbar), column pivoting and rank on the first iteration
-    if (it == 1) tall_qr(B, BUF_B2, W_U, W_V, QR_RANK, tol_rank, o.rank_mode, BUF_V, s);
-    else tall_qr(B, BUF_B2, W_U, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+    // V = qr(Vbar), column pivoting and the rank test on a problem's first iteration
+    tall_qr(B, BUF_B2, W_U, W_V, QR_AUTO, tol_rank, o.rank_mode, BUF_V, s);
     // Y = T V over the box {0..n+1}^d
     if ((rc = toeplitz(it, 1))) return rc;
     // Q = U^* (T V), ||T V - U Q||_F
@@ -809,6 +877,68 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     launch_check(D, tol_power, max_iter, dflag, s);
     return PRONY_OK;
   };
+  // finishing steps, for every problem that has not failed
+  auto finish = [&]() -> int {
+    launch_reset_done(D, s);
+    // M_l = U^* Y_l  with Y_l the rows k + e_l of the last product Y = T V
+    launch_zero_small(D, D.L.mproj, 16LL * D.maxD * D.L.LDR * D.L.LDM, s);
+    for (int l = 0; l < D.maxD; ++l)
+      launch_gram(D, BUF_U, -1, W_U, BUF_Y, l, W_V, D.L.mproj + 16LL * l * D.L.LDR * D.L.LDM, D.L.LDM, s);
+    launch_svd_S(D, s);
+    if (ro.want_S) {
+      // phase-canonical basis: argmax over V V_Q, then rotate U_Q, V_Q, S_l
+      launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);
+      launch_zero_small(D, D.L.argmx, 8LL * D.L.LDM, s);
+      launch_argmax(D, BUF_B1, s);
+      launch_canon(D, s);
+      launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);   // V_final
+      launch_apply(D, BUF_U, W_U, W_V, D.L.uq, 1, -1, BUF_B2, 0, s);   // U_final
+    }
+    launch_eig_t(D, o.seed, s);
+    launch_zero_small(D, D.L.rhs, 16LL * D.L.LDM, s);
+    launch_rhs(D, 0, s);
+    launch_solve_c(D, s);
+    launch_rhs(D, 1, s);
+    return PRONY_OK;
+  };
+
+  // ---- as one graph (the usual case), or step by step from the host: with profiling (events
+  // around every product) and on the first call for a batch shape (the product autotuner times
+  // candidates between the start block and the first product)
+  const bool graph = !ctx->prof && !(B.tc.on && !B.tc.tuned);
+  if (graph) {
+    const double par[] = {tol_rank, tol_power, tol_drop, (double)max_iter, (double)prec, (double)o.svd_method,
+                          (double)o.rank_mode, (double)o.vandermonde, (double)ro.want_S};
+    std::string key = loop_graph_key(B, dflag, max_iter, par, (int)(sizeof(par) / sizeof(par[0])));
+    key.append((const char*)&o.seed, sizeof(o.seed));
+    if (!ctx->solve_graph.exec || key != ctx->solve_graph.key) {
+      std::vector<Seg> segs;
+      segs.push_back({false, prefix, 0, 0});
+      if (lanczos) segs.push_back({true, lz_step, lz_cap, 1});
+      segs.push_back({false, start, 0, 0});
+      segs.push_back({true, [&]() { return iteration(1); }, max_iter, 0});
+      segs.push_back({false, finish, 0, 0});
+      if ((rc = build_solve_graph(ctx, segs, dflag, key))) return rc;
+    }
+    if ((rc = launch_solve_graph(ctx))) return rc;
+    CK(cudaGetLastError());
+    return check_tc_error(ctx, B);
+  }
+  prefix();
+  if (lanczos) {
+    for (int step = 0; step < lz_cap; ++step) {
+      if ((rc = lz_step())) return rc;
+      CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*ctx->h_flag != 0) break;
+    }
+  }
+  if (B.tc.on && !B.tc.tuned && (rc = tc_autotune(ctx, B, D, prec, s))) return rc;
+  if ((rc = start())) return rc;
+  if (ctx->prof) {
+    ctx->snaps.emplace_back(D.nprob);
+    CK(cudaMemcpyAsync(ctx->snaps.back().data(), D.st, sizeof(ProbState) * D.nprob, cudaMemcpyDeviceToHost, s));
+  }
   for (int it = 1; it <= max_iter; ++it) {
     if ((rc = iteration(it))) return rc;
     CK(cudaMemcpyAsync(ctx->h_flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -818,15 +948,6 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     }
     CK(cudaStreamSynchronize(s));
     if (*ctx->h_flag != 0) break;
-    if (it == 1 && !ctx->prof && max_iter > 1) {
-      // iterations 2.. as one CUDA graph: a WHILE node whose body is one iteration and whose
-      // condition kernel reads dflag on the device -- no host round trip per iteration
-      const double par[] = {tol_drop, tol_power, (double)prec};
-      auto body = [&]() -> int { return iteration(2); };
-      if ((rc = device_loop(ctx, 0, loop_graph_key(B, dflag, max_iter - 1, par, 3), body, dflag, max_iter - 1, s)))
-        return rc;
-      break;
-    }
   }
   if (ctx->prof) {
     // accumulate durations and algorithmic work of the Toeplitz launches of this solve
@@ -857,7 +978,6 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
           by += 8.0 * q.Gd + 8.0 * q.N * w + 8.0 * rows * w;
         }
       }
-      ctx->stats.tc_cluster = B.tc.on ? B.tc.cs : 0;
       ctx->stats.tc_ksplit = B.tc.on ? B.tc.nks : 0;
       ctx->stats.tc_bstages = B.tc.on ? B.tc.stages : 0;
       ctx->stats.toeplitz_launches += 1;
@@ -866,27 +986,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
       ctx->stats.toeplitz_bytes += by;
     }
   }
-  // finishing steps run for every problem that has not failed
-  launch_reset_done(D, s);
-  // M_l = U^* Y_l  with Y_l the rows k + e_l of the last product Y = T V
-  launch_zero_small(D, D.L.mproj, 16LL * D.maxD * D.L.LDR * D.L.LDM, s);
-  for (int l = 0; l < D.maxD; ++l)
-    launch_gram(D, BUF_U, -1, W_U, BUF_Y, l, W_V, D.L.mproj + 16LL * l * D.L.LDR * D.L.LDM, D.L.LDM, s);
-  launch_svd_S(D, s);
-  if (ro.want_S) {
-    // phase-canonical basis: argmax over V V_Q, then rotate U_Q, V_Q, S_l
-    launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);
-    launch_zero_small(D, D.L.argmx, 8LL * D.L.LDM, s);
-    launch_argmax(D, BUF_B1, s);
-    launch_canon(D, s);
-    launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);   // V_final
-    launch_apply(D, BUF_U, W_U, W_V, D.L.uq, 1, -1, BUF_B2, 0, s);   // U_final
-  }
-  launch_eig_t(D, o.seed, s);
-  launch_zero_small(D, D.L.rhs, 16LL * D.L.LDM, s);
-  launch_rhs(D, 0, s);
-  launch_solve_c(D, s);
-  launch_rhs(D, 1, s);
+  finish();
   CK(cudaGetLastError());
   return check_tc_error(ctx, B);
 }
@@ -928,8 +1028,21 @@ int check_precision(int prec) {
   return (prec == PRONY_FP32 || prec == PRONY_FFT32 || is_tc(prec)) ? PRONY_OK : PRONY_EINVAL;
 }
 
-// Error flag of the tensor-core kernels (bounded waits that gave up, window overflow).
+// Error flags of the kernels: a failed workspace bound check (any kernel; the access was skipped,
+// the split-K and cross-block counters are cleared for the next call) and the tensor-core kernels'
+// bounded waits or window overflow.
 int check_tc_error(prony_ctx* ctx, const Batch& B) {
+  int oob = 0;
+  CK(cudaMemcpyAsync(&oob, ctx->oob.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (oob) {
+    CK(cudaMemsetAsync(ctx->oob.p, 0, sizeof(int), ctx->stream));
+    if (ctx->cnt.p) CK(cudaMemsetAsync(ctx->cnt.p, 0, ctx->cnt.cap, ctx->stream));
+    if (ctx->rcnt.p) CK(cudaMemsetAsync(ctx->rcnt.p, 0, ctx->rcnt.cap, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    g_err = "internal workspace bound check failed at site " + std::to_string(oob);
+    return PRONY_ECUDA;
+  }
   if (!B.tc.on) return PRONY_OK;
   if (ctx->launch_err != cudaSuccess) {
     const cudaError_t e = ctx->launch_err;
@@ -1011,6 +1124,13 @@ int prony_ctx_create(prony_ctx** out, int device) {
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreate"); }
   e = cudaMallocHost(&c->h_flag, 256);
   if (e != cudaSuccess) { cudaStreamDestroy(c->stream); delete c; return cuda_fail(e, "cudaMallocHost"); }
+  if (ensure(c->oob, 256) != PRONY_OK || cudaMemsetAsync(c->oob.p, 0, 256, c->stream) != cudaSuccess) {
+    if (c->oob.p) cudaFree(c->oob.p);
+    cudaFreeHost(c->h_flag);
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return PRONY_ENOMEM;
+  }
   *out = c;
   return PRONY_OK;
 }
@@ -1021,10 +1141,10 @@ int prony_ctx_destroy(prony_ctx* c) {
   cudaStreamSynchronize(c->stream);
   DBuf* bufs[] = {&c->grid64, &c->gF, &c->gH, &c->V, &c->U, &c->B1, &c->B2, &c->Y, &c->small, &c->P,
                   &c->st, &c->jobs, &c->flag, &c->tout, &c->cout, &c->misc, &c->misc2, &c->misc3,
-                  &c->xb, &c->tabF, &c->tabH, &c->tcjobs, &c->tcerr, &c->lmws};
+                  &c->xb, &c->tabF, &c->tabH, &c->tcjobs, &c->tcerr, &c->lmws, &c->part, &c->cnt, &c->red,
+                  &c->rcnt, &c->oob};
   if (c->lm_exec) cudaGraphExecDestroy(c->lm_exec);
-  for (auto& l : c->loops)
-    if (l.exec) cudaGraphExecDestroy(l.exec);
+  if (c->solve_graph.exec) cudaGraphExecDestroy(c->solve_graph.exec);
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->h_flag) cudaFreeHost(c->h_flag);
@@ -1180,6 +1300,82 @@ int prony_build_S(prony_ctx* ctx, const prony_c128* samples, int d, int n, int m
       }
   for (int i = 0; i < m; ++i) sigma_out[i] = i < w ? sg[i] : 0.0;
   return worst;
+}
+
+int prony_small_steps(prony_ctx* ctx, int d, int m, int a, const prony_c128* Q, const prony_c128* M,
+                      unsigned long long seed, int jacobi_cap, int eigqr_cap, double* sigma_out, prony_c128* S_out,
+                      prony_c128* z_out, double* t_out, int* status_out) {
+  if (!ctx || !Q || !M || !sigma_out || !S_out || !z_out || !t_out || d < 1 || d > PRONY_DMAX || m < 1 ||
+      m > PRONY_MMAX || a < m || a > PRONY_RMAX)
+    return PRONY_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  // one problem whose power loop has "ended" with U of width a and V of width m: the state and
+  // the small workspace are written directly, no tall block or product is involved
+  ProbDesc pd{};
+  pd.d = d;
+  pd.m = m;
+  pd.r0 = a;
+  pd.n = 1;
+  pd.N = a;
+  ProbState st{};
+  st.wu = a;
+  st.wv = m;
+  st.rank_used = m;
+  st.rank_det = m;
+  const SmallLay L = make_small_lay((a + 1) / 2 * 2, m, d);
+  int rc;
+  if ((rc = ensure(ctx->small, (size_t)L.bytes))) return rc;
+  if ((rc = ensure(ctx->P, sizeof(ProbDesc)))) return rc;
+  if ((rc = ensure(ctx->st, sizeof(ProbState)))) return rc;
+  CK(cudaMemsetAsync(ctx->small.p, 0, (size_t)L.bytes, s));
+  CK(cudaMemcpyAsync(ctx->P.p, &pd, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->st.p, &st, sizeof(ProbState), cudaMemcpyHostToDevice, s));
+  char* sb = (char*)ctx->small.p;
+  // Q (a x m) and U^* T_l V (a x m each), row-major with leading dimension LDM
+  CK(cudaMemcpy2DAsync(sb + L.q, sizeof(double2) * L.LDM, Q, sizeof(prony_c128) * m, sizeof(prony_c128) * m, a,
+                       cudaMemcpyHostToDevice, s));
+  for (int l = 0; l < d; ++l)
+    CK(cudaMemcpy2DAsync(sb + L.mproj + 16LL * l * L.LDR * L.LDM, sizeof(double2) * L.LDM, M + (size_t)l * a * m,
+                         sizeof(prony_c128) * m, sizeof(prony_c128) * m, a, cudaMemcpyHostToDevice, s));
+  Dev D{};
+  D.P = (const ProbDesc*)ctx->P.p;
+  D.st = (ProbState*)ctx->st.p;
+  D.nprob = 1;
+  D.maxN = a;
+  D.maxR0 = a;
+  D.maxM = m;
+  D.maxD = d;
+  D.small = sb;
+  D.L = L;
+  D.cap_jacobi = jacobi_cap;
+  D.cap_eigqr = eigqr_cap;
+  launch_svd_S(D, s);
+  launch_eig_t(D, seed, s);
+  CK(cudaGetLastError());
+  std::vector<char> h(L.bytes);
+  CK(cudaMemcpyAsync(h.data(), sb, L.bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&st, ctx->st.p, sizeof(ProbState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double* sg = (const double*)(h.data() + L.sigma);
+  const double2* S = (const double2*)(h.data() + L.S);
+  const double2* z = (const double2*)(h.data() + L.zraw);
+  const double* t = (const double*)(h.data() + L.t);
+  for (int i = 0; i < m; ++i) sigma_out[i] = sg[i];
+  for (int l = 0; l < d; ++l)
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        const double2 v = S[(size_t)l * L.LDM * L.LDM + (size_t)i * L.LDM + j];
+        S_out[((size_t)l * m + i) * m + j] = {v.x, v.y};
+      }
+  for (int j = 0; j < m; ++j)
+    for (int l = 0; l < d; ++l) {
+      const double2 v = z[j * PRONY_DMAX + l];
+      z_out[(size_t)j * d + l] = {v.x, v.y};
+      t_out[(size_t)j * d + l] = t[j * PRONY_DMAX + l];
+    }
+  if (status_out) *status_out = st.status;
+  return PRONY_OK;
 }
 
 int prony_eval(prony_ctx* ctx, const double* t, const prony_c128* c, int m, int d, const int* k, int K,

@@ -10,38 +10,47 @@
 //
 // The array is a static device symbol: every GPU that loads the library holds it
 // (PRONY_STATIC_SCRATCH_BYTES) until the process exits.  In host code its name stands
-// for a host-side shadow, not a device address, so its device address is looked up
-// once per device with cudaGetSymbolAddress (the first call on each device does this,
-// so that first call should come before any stream capture).  All calls share the one
-// array: calls that overlap on the GPU (for example on two streams) race on it.
+// for a host-side shadow, not a device address, so every call looks up its device address
+// on the current device with cudaGetSymbolAddress (a cheap lookup once the module is loaded;
+// nothing is cached, so a reset device or another context never sees a stale address).  The
+// first call on a device loads the library's module there and reserves the array, which may
+// synchronise: make it once as a warm-up, outside latency-critical loops and before any stream
+// capture.  All calls share the one array: calls that overlap on the GPU (for example on two
+// streams) race on it.
+//
+// The product runs without a K split (one CTA per row tile), so it needs no partial-sum
+// workspace and its sums have one fixed order.
 #include "common.cuh"
 #include "../../include/prony.h"
 
 #include <algorithm>
-#include <mutex>
 
 namespace {
 
-constexpr long long kMaxJobs = 65536;
+constexpr long long kMaxJobs = 65536 - 128;
 constexpr long long kOffDesc = 0;
 constexpr long long kOffState = 256;
 constexpr long long kOffJobs = 512;
-constexpr long long kOffGrid = kOffJobs + kMaxJobs * (long long)sizeof(ToeplitzJob);   // 256-aligned
+// block sums of the grid preparation (at most 64 blocks of two doubles) and their counter
+constexpr long long kOffRed = kOffJobs + kMaxJobs * (long long)sizeof(ToeplitzJob);
+constexpr long long kOffRcnt = kOffRed + 64 * 16;
+constexpr long long kOffGrid = kOffJobs + 65536LL * (long long)sizeof(ToeplitzJob);   // 256-aligned
 constexpr long long kScratchBytes = kOffGrid + 2LL * 8LL * PRONY_STATIC_MAX_GRID;
 
 static_assert(sizeof(ProbDesc) <= 256 && sizeof(ProbState) <= 256, "scratch header too small");
 static_assert(kOffGrid % 256 == 0, "grid planes must stay 256-byte aligned");
+static_assert(kOffRcnt + 16 <= kOffGrid, "reduction slots must fit below the grid planes");
 static_assert(kScratchBytes == PRONY_STATIC_SCRATCH_BYTES, "scratch size must match the documented one");
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_addr[256] = {};      // device address of g_scratch, per device ordinal
-
 // Descriptor and job list written on the device (no host-to-device copy, no allocation).
 __global__ void k_static_setup(ProbDesc desc, int tiles, int nks) {
   unsigned char* base = g_scratch;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *(ProbDesc*)(base + kOffDesc) = desc;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *(ProbDesc*)(base + kOffDesc) = desc;
+    *(int*)(base + kOffRcnt) = 0;
+  }
   ToeplitzJob* jobs = (ToeplitzJob*)(base + kOffJobs);
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tiles * nks; q += gridDim.x * blockDim.x)
     jobs[q] = ToeplitzJob{0, q / nks, q % nks, nks};
@@ -64,32 +73,21 @@ extern "C" int prony_toeplitz_mm_static(const prony_c128* grid_dev, int d, int n
       return PRONY_EINVAL;
     }
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 256) {
-    set_last_error("prony_toeplitz_mm_static: no current CUDA device");
-    return PRONY_ECUDA;
+  if (r > N) {                                 // as prony_toeplitz_mm_dev: at most N columns
+    set_last_error("prony_toeplitz_mm_static: r exceeds (n+1)^d");
+    return PRONY_EINVAL;
   }
+  // the device address of the array on the current device, looked up on every call
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_scratch);
-      if (e != cudaSuccess || !p) {
-        set_last_error("prony_toeplitz_mm_static: cudaGetSymbolAddress of the scratch array failed");
-        return PRONY_ECUDA;
-      }
-      g_addr[dev] = p;
-    }
-    base = g_addr[dev];
+  cudaError_t e = cudaGetSymbolAddress(&base, g_scratch);
+  if (e != cudaSuccess || !base) {
+    set_last_error("prony_toeplitz_mm_static: cudaGetSymbolAddress of the scratch array failed");
+    return PRONY_ECUDA;
   }
   cudaStream_t s = (cudaStream_t)stream;
   const long long rows = (L == n + 2) ? Next : N;
   const int tiles = (int)((rows + 63) / 64);
-  int nks = (int)std::max<long long>(1, std::min<long long>(304 / std::max(1, tiles), 16));
-  nks = (int)std::min<long long>(nks, std::max<long long>(1, N / 64));
-  nks = (int)std::min<long long>(nks, std::max<long long>(1, kMaxJobs / tiles));
+  const int nks = 1;
   if ((long long)tiles * nks > kMaxJobs) return PRONY_EINVAL;
 
   ProbDesc desc{};
@@ -127,11 +125,14 @@ extern "C" int prony_toeplitz_mm_static(const prony_c128* grid_dev, int d, int n
   D.Y = (float2*)Y_dev;
   D.B2 = (float2*)Y_dev;
   D.small = nullptr;
+  D.red = (char*)(b + kOffRed);
+  D.red_stride = 64 * 16;
+  D.rcnt = (int*)(b + kOffRcnt);
   // state (widths, flags) is rewritten by the first kernel; gF / gH are overwritten whole
   launch_prep(D, s);
   const ToeplitzJob* jobs = (const ToeplitzJob*)(b + kOffJobs);
   const int ext = (L == n + 2);
-  launch_toeplitz(D, jobs, tiles * nks, nks, adjoint, BUF_V, W_R0, ext ? BUF_Y : BUF_B2, ext, r, PRONY_FP32, s);
+  launch_toeplitz(D, jobs, tiles * nks, adjoint, BUF_V, W_R0, ext ? BUF_Y : BUF_B2, ext, r, nullptr, nullptr, 0, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));

@@ -616,12 +616,12 @@ def test_full_size_C2_batch152(ctx):
 
 @pytest.mark.parametrize("env,expect", [
     ({"PRONY_TC_BSTAGES": "4"}, {"tc_bstages": 4}), ({"PRONY_TC_BSTAGES": "2"}, {"tc_bstages": 2}),
-    ({"PRONY_TC_CLUSTER": "1"}, {"tc_cluster": 1}), ({"PRONY_TC_TUNE": "0"}, {}),
+    ({"PRONY_TC_TUNE": "0"}, {}),
 ])
 def test_tensor_core_sizing_overrides(ctx, monkeypatch, env, expect):
-    """Every launch configuration of the tensor-core products (B stages, cluster size, K split,
-    with or without the autotuner) solves the same C2 problems to the same forward error as the
-    default one (different FP32 summation orders only), and the statistics report the override."""
+    """Every launch configuration of the tensor-core products (B stages, K split, with or without
+    the autotuner) solves the same C2 problems to the same forward error as the default one
+    (different FP32 summation orders only), and the statistics report the override."""
     from paper_2012_11430_gb300 import default_opts
     probs = [W.config_problem("C2", seed_offset=i) for i in range(12)]
     args = ([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs], [p.m for p in probs],
@@ -640,7 +640,7 @@ def test_tensor_core_sizing_overrides(ctx, monkeypatch, env, expect):
     assert rc == 0
     for k, v in expect.items():
         assert st[k] == v, (k, st)
-    assert st["tc_bstages"] >= 1 and st["tc_ksplit"] >= 1 and st["tc_cluster"] >= 1, st
+    assert st["tc_bstages"] >= 1 and st["tc_ksplit"] >= 1, st
     for p, a, b in zip(probs, base, outs):
         assert b.info["status"] == 0 and b.info["rank_used"] == p.m, b.info
         te_a, ce_a = W.match_to_truth(a.t, a.c, p.t, p.c)
@@ -712,3 +712,157 @@ def test_device_and_host_pointer_batches_agree(ctx):
             dt = np.abs(t_i - r.t)
             assert np.max(np.minimum(dt, 1.0 - dt)) <= 1e-6, (p.name, t_i, r.t)
             assert np.max(np.abs(c_x[o:o + p.m] - r.c)) <= 1e-5 * np.max(np.abs(r.c)), p.name
+
+
+# ------------------------------------------------------------------ deterministic split-K products
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16x2", "fp32"])
+@pytest.mark.parametrize("d,n,r,L_ext,adjoint", [(2, 63, 40, 1, 0), (2, 63, 20, 0, 1), (3, 19, 80, 1, 0)])
+def test_toeplitz_product_bit_identical_repeats(ctx, prec, d, n, r, L_ext, adjoint):
+    """Products whose K dimension is split over several CTAs add the partial sums in the order of
+    their K ranges, whatever order the CTAs finish in: two identical calls give bit-identical
+    results (and both stay within the product's error bound)."""
+    import torch
+    grid = _random_grid(d, n, 700 + d * 10 + n)
+    N = (n + 1) ** d
+    L = n + 2 if L_ext else n + 1
+    rng = np.random.Generator(np.random.PCG64(71 + r))
+    X = (rng.standard_normal((r, N)) + 1j * rng.standard_normal((r, N))).astype(np.complex64)
+    g_dev = torch.from_numpy(grid.reshape(-1).astype(np.complex128)).cuda()
+    X_dev = torch.from_numpy(X).cuda()
+    outs = []
+    for _ in range(2):
+        Y_dev = torch.full((r, L ** d), float("nan"), dtype=torch.complex64, device="cuda")
+        ctx.toeplitz_mm_dev(g_dev, d, n, X_dev, L, adjoint, prec, Y_dev)
+        outs.append(Y_dev.cpu().numpy())
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+    Y = outs[0].astype(np.complex128).T
+    T = _toeplitz_rows(grid, n, d, L, adjoint)
+    Xd = X.astype(np.complex128).T
+    rel = TC_REL[prec](N) if prec in TC_REL else (2 * N + 16) * U32
+    assert np.all(np.abs(Y - T @ Xd) <= rel * (np.abs(T) @ np.abs(Xd)) + 1e-30)
+
+
+# ------------------------------------------------------------------ S_l at full sizes, every arithmetic
+def _S_alignment(V_o, V):
+    ph = np.sum(V_o.conj() * V, axis=0)
+    return ph / np.abs(ph)
+
+
+@pytest.fixture(scope="module")
+def S_refs():
+    """Noise-free problems of the C2 shape (d=2, n=63, m=20) and the C3 shape (d=3, n=19, m=40)
+    with the oracle's S_l (Algorithm 3 in FP64, phase-canonical basis)."""
+    out = {}
+    for key, (d, n, m, seed) in {"C2": (2, 63, 20, 8101), "C3": (3, 19, 40, 8102)}.items():
+        P = W.make_problem(f"S_{key}", d, n, m, seed)
+        S_o, s_o, U_o, V_o = O.prony_S(P.grid, d, n, m, svd="power", tol_power=1e-13)
+        out[key] = (P, np.array(S_o), s_o, U_o, V_o)
+    return out
+
+
+# Relative Frobenius error bound of the S_l results.  1e-5 for the products that carry FP32
+# operands (three BF16 planes, 3xTF32, FP32 FMA, FP32 FFTs).  BF16x2 rounds each operand to 16
+# significant bits (|x - x0 - x1| <= 2^-17 |x|) and drops x1 y1: ~3 * 2^-16 per product term, so
+# its bound is 3 * 2^-16 ~ 4.6e-5.
+S_TOL = {"bf16x3": 1e-5, "tf32x3": 1e-5, "fp32": 1e-5, "fft32": 1e-5, "bf16x2": 3 * 2.0 ** -16}
+
+
+def projected_operator_error(U, S, sig, V, U_o, S_o, s_o, V_o):
+    """Relative Frobenius distance of the basis-free operators K_l = U S_l Sigma V^* = P_U T_l P_V
+    (N x N, rank m), from m x m Grams: ||K||^2 = ||S Sigma||^2 for orthonormal U, V and
+    <K, K_o> = tr((S Sigma)^* (U^* U_o) (S_o Sigma_o) (V_o^* V))."""
+    errs = []
+    Gu, Gv = U.conj().T @ U_o, V_o.conj().T @ V
+    Guu, Gvv = U.conj().T @ U, V.conj().T @ V        # the GPU's bases are orthonormal to FP32 only
+    Gou, Gov = U_o.conj().T @ U_o, V_o.conj().T @ V_o
+    for l in range(S.shape[0]):
+        A, A_o = S[l] * sig[None, :], S_o[l] * s_o[None, :]
+        n2 = np.trace(A.conj().T @ Guu @ A @ Gvv).real
+        n2o = np.trace(A_o.conj().T @ Gou @ A_o @ Gov).real
+        cross = np.trace(A.conj().T @ Gu @ A_o @ Gv).real
+        errs.append(np.sqrt(max(n2 + n2o - 2.0 * cross, 0.0) / n2o))
+    return max(errs)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "tf32x3", "fp32", "fft32"])
+@pytest.mark.parametrize("key", ["C2", "C3"])
+def test_build_S_full_size_every_precision(ctx, S_refs, key, prec):
+    """S_l = U^* T_l V Sigma^{-1} (Eq. generateSl) at the C2 and C3 sizes, where the products
+    split K over several CTAs and the row tiles cross grid lines, against the FP64 oracle:
+      * sigma within 1e-5 and the eigenvalues of every S_l (basis-free) within 1e-6;
+      * the basis-free operator U S_l Sigma V^* = P_U T_l P_V within S_TOL (relative Frobenius);
+      * S_l element by element after aligning the singular-vector phases within S_TOL at C2.
+    At C3 (m = 40 singular values within a factor 3, neighbours as close as ~0.2 %) single
+    singular vectors are ill-conditioned: an FP32-level perturbation rotates near-degenerate pairs
+    by ~error / gap, which changes S_l element by element (the basis) but not the operator or its
+    spectrum; the element-wise error is printed there and must stay below error / gap.  The FFT
+    products fit one CTA's shared memory only up to d=3, n=7, so C3 is refused there."""
+    from paper_2012_11430_gb300 import PronyError, PRONY_EINVAL, default_opts
+    P, S_o, s_o, U_o, V_o = S_refs[key]
+    opts = default_opts(precision=prec)
+    if prec == "fft32" and key == "C3":
+        with pytest.raises(PronyError) as e:
+            ctx.build_S(P.grid, P.d, P.n, P.m, opts)
+        assert e.value.code == PRONY_EINVAL
+        return
+    S, sig, U, V, info = ctx.build_S(P.grid, P.d, P.n, P.m, opts, want_uv=True)
+    assert info["status"] == 0, info
+    err_sig = np.max(np.abs(sig - s_o) / s_o)
+    assert err_sig <= 1e-5
+    ph = _S_alignment(V_o, V)
+    elem = max(np.linalg.norm(np.diag(ph) @ S[l] @ np.diag(ph.conj()) - S_o[l]) / np.linalg.norm(S_o[l])
+               for l in range(P.d))
+    proj = projected_operator_error(U, S, sig, V, U_o, S_o, s_o, V_o)
+    eig = 0.0
+    for l in range(P.d):
+        ev, ev_o = np.linalg.eigvals(S[l]), np.linalg.eigvals(S_o[l])
+        ev, ev_o = ev[np.argsort(np.angle(ev))], ev_o[np.argsort(np.angle(ev_o))]
+        eig = max(eig, float(np.max(np.abs(ev - ev_o))))
+    gap = float(np.min(-np.diff(s_o)) / s_o[0])
+    print(f"S_l {key} {prec}: projected {proj:.2e}, element-wise {elem:.2e}, eigenvalues {eig:.2e}, "
+          f"sigma {err_sig:.2e}, min gap {gap:.1e}")
+    assert eig <= 1e-6, eig
+    assert proj <= S_TOL[prec], proj
+    if key == "C2":
+        assert elem <= S_TOL[prec], elem
+    else:
+        assert elem <= S_TOL[prec] / gap, (elem, gap)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp32", "fft32"])
+def test_solve_bit_identical_repeats(ctx, prec):
+    """Every cross-block sum of the solver (split-K products, tall Grams, norms, right-hand sides)
+    adds its partials in a fixed order, so repeating a batched solve on the same inputs gives
+    bit-identical t and c (and the same iteration counts)."""
+    from paper_2012_11430_gb300 import default_opts
+    probs = W.batch_problems(6) + [W.config_problem("C2"), W.make_problem("rep3", 3, 5, 4, 43)]
+    args = ([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs], [p.m for p in probs],
+            default_opts(precision=prec))
+    a, rc_a = ctx.solve_batched(*args)
+    b, rc_b = ctx.solve_batched(*args)
+    assert rc_a == rc_b == 0
+    for p, x, y in zip(probs, a, b):
+        assert x.info == y.info, (p.name, x.info, y.info)
+        assert np.array_equal(x.t, y.t) and np.array_equal(x.c, y.c), p.name
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_graph_and_host_driven_solves_agree(ctx, prec):
+    """A solve runs as one CUDA graph (power loop as a device-side WHILE node); with profiling on
+    the same kernels are launched one by one from the host.  Both orders of the same kernels give
+    bit-identical results, and the graph is replayed, not rebuilt, for a repeated layout."""
+    from paper_2012_11430_gb300 import default_opts
+    probs = W.batch_problems(5) + [W.config_problem("C1"), W.make_problem("gh3", 3, 5, 4, 44)]
+    args = ([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs], [p.m for p in probs],
+            default_opts(precision=prec))
+    ctx.solve_batched(*args)                       # tuning cache filled, graph captured
+    a, rc_a = ctx.solve_batched(*args)             # graph replay
+    ctx.set_profiling(True)
+    try:
+        b, rc_b = ctx.solve_batched(*args)         # host-driven launches
+    finally:
+        ctx.set_profiling(False)
+    assert rc_a == rc_b == 0
+    for p, x, y in zip(probs, a, b):
+        assert x.info == y.info, (p.name, x.info, y.info)
+        assert np.array_equal(x.t, y.t) and np.array_equal(x.c, y.c), p.name
