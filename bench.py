@@ -2,7 +2,7 @@
 """Benchmark of the GPU Prony solver; default workload C3 (d=3, n=19, N=8000, m=40, 50 dB).
 
 One step = one pass of the whole hot path (Algorithm 1 with the block power SVD) over a batch
-of `--batch` independent synthetic problems (C3: 16, C1/C2: 152, C4: 4096).  Printed as one
+of `--batch` independent synthetic problems (C3: 32, C1/C2: 152, C4: 4096).  Printed as one
 JSON line:
 
   value     solves/s that pass the accuracy gate, inputs resident in HBM, CUDA events on
@@ -112,7 +112,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5"])
     ap.add_argument("--batch", type=int, default=None,
-                    help="problems per GPU (default: C3 16, C1 / C2 152, C4 4096)")
+                    help="problems per GPU (default: C3 32, C1 / C2 152, C4 4096)")
     ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--svd", default="power", choices=["power", "lanczos"],
                     help="subspace step: block power method (Algorithm 3) or Lanczos start (Algorithm 2)")
@@ -120,11 +120,14 @@ def parse():
                     help="comma-separated product arithmetics for the per-precision object "
                          "(default: C3 all four of bf16x3,tf32x3,bf16x2,fp32; other configs none)")
     ap.add_argument("--oracle-workers", type=int, default=4)
+    ap.add_argument("--launch-steps", type=int, default=0,
+                    help="run one warm-up step and this many steps with every kernel launched from the "
+                         "host (profiling mode), then exit: the command an ncu launch list is taken on")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
-DEFAULT_BATCH = {"C1": 152, "C2": 152, "C3": 16, "C4": 4096}
+DEFAULT_BATCH = {"C1": 152, "C2": 152, "C3": 32, "C4": 4096}
 GATE_FLOOR = 10 * 2.0 ** -24          # 10 u32: absolute floor of the noisy gate (6e-7)
 
 
@@ -517,6 +520,15 @@ def main():
         return lambda: ctx.solve_batched_dev(dev, ds, ns, ms, soff, ooff, t_dev, c_dev, o, stream.cuda_stream)
 
     step_dev = step_with(opts)
+    if args.launch_steps > 0:
+        step_dev()
+        ctx.set_profiling(True)                    # host-driven loop: every kernel is a plain launch
+        for _ in range(args.launch_steps):
+            step_dev()
+        torch.cuda.synchronize()
+        print(json.dumps({"launch_steps": args.launch_steps, "config": args.config, "batch": B,
+                          "precision": args.precision, "launches": ctx.stats()["launches"]}), flush=True)
+        return
     for _ in range(args.warmup):
         step_dev()
     # accuracy of this configuration (results of one untimed step)

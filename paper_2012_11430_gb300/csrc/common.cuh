@@ -342,6 +342,22 @@ void launch_toeplitz(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoi
                      int y_ext, int maxw, float2* part, int* cnt, long long part_jobs, cudaStream_t s);
 
 // kernels_tc.cu (tensor-core Toeplitz products: split BF16 planes or TF32 hi + lo)
+// Window of a product CTA in its split-plane tables, [lo, lo + len) in table entries, for the grid
+// indices [f_lo, f_hi] it reads.  TF32 tables hold one 32-bit entry per grid index x; BF16
+// tables hold 16-bit entries in reverse order (entry Gd4 - 1 - x holds sample x), so that two
+// consecutive input points on a grid line are two ascending entries (one 32-bit word, or two
+// joined by a funnel shift).  Starts are 16-byte aligned; a BF16 window carries 8 spare entries
+// (the word pairs of a line read up to two entries past its last point).
+__host__ __device__ inline void tc_window(bool bf16, int Gd4, int f_lo, int f_hi, int& lo, int& len) {
+  if (bf16) {
+    const int r_lo = (Gd4 - 1 - f_hi) & ~7, r_hi = Gd4 - 1 - f_lo;
+    lo = r_lo;
+    len = ((r_hi - r_lo + 1 + 7) & ~7) + 8;
+  } else {
+    lo = f_lo & ~3;
+    len = ((f_hi - lo + 1) + 3) & ~3;
+  }
+}
 int tc_planes(int kind);
 size_t tc_stage_bytes(int kind, int ntbox);
 size_t tc_elem_bytes(int kind);
@@ -351,11 +367,15 @@ long long tc_prob_stride(int kind, int ntbox, int maxnc);
 // counter per job.
 size_t tc_part_floats(int ntbox);
 void launch_split_tables(const Dev& D, int kind, cudaStream_t s);
-void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, long long prob_stride, cudaStream_t s);
+void launch_xb_prep(const Dev& D, int xbuf, int xshift, int wsel, void* xb, int kind, long long prob_stride,
+                    cudaStream_t s);
 cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int adjoint, int wsel, int ybuf,
                                int y_ext, int kind, int ntbox, int win_cap, int stages, const void* xb,
                                long long prob_stride, float* part, int* cnt, long long part_jobs, int* err,
                                cudaStream_t s);
+cudaError_t launch_gram_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int xbuf, int xshift, int xw, int zw,
+                           long long out_off, int out_ld, int ntbox, int stages, const void* xb, long long prob_stride,
+                           float* part, int* cnt, long long part_jobs, int* err, cudaStream_t s);
 
 // kernels_refine.cu (Levenberg-Marquardt refinement of (t, c))
 long long lm_workspace_bytes(int m, int d);

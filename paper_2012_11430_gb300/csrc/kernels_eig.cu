@@ -91,8 +91,8 @@ __device__ inline void rr_pair(int step, int k, int nb, int& pa, int& pb) {
 // consecutive matrices per problem), on the per-problem small workspace.  Matrices are row-major
 // complex FP64 at byte offsets of the problem's block; op = conjugate transpose when t* = 1.
 // One CTA computes a 16 x 16 tile of C: 256 threads, one entry each, K staged 16 at a time in
-// shared memory; four partial sums per entry (k mod 4) keep eight independent FP64 chains per
-// thread in flight.  Dimensions come from the problem's state (a = wu, b = wv).
+// shared memory; eight partial sums per entry (k mod 8) keep sixteen independent FP64 chains per
+// thread in flight (a dependent FP64 operation waits hundreds of cycles on this GPU).  Dimensions come from the problem's state (a = wu, b = wv).
 enum ZDim { ZD_A = 0, ZD_B = 1 };
 enum ZLive { ZL_SVD = 0, ZL_EIG = 1 };
 enum ZConv { ZC_ALL = 0, ZC_SKIP_CONV = 1, ZC_COPY_CONV = 2 };
@@ -136,7 +136,9 @@ __global__ void __launch_bounds__(256) k_zgemm(Dev D, ZG g) {
     if (g.conv == ZC_COPY_CONV && i < M && j < N) C[i * g.ldc + j] = A[i * g.lda + j];
     return;
   }
-  double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+  double2 acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = make_double2(0.0, 0.0);
   for (int k0 = 0; k0 < K; k0 += ZT) {
     {
       // A tile rows i0.., columns k0..; B tile rows k0.., columns j0..
@@ -152,9 +154,9 @@ __global__ void __launch_bounds__(256) k_zgemm(Dev D, ZG g) {
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < ZT; kk += 4) {
+    for (int kk = 0; kk < ZT; kk += 8) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const double2 a = As[ty][kk + u], b = Bs[kk + u][tx];
         acc[u].x = fma(a.x, b.x, acc[u].x);
         acc[u].y = fma(a.x, b.y, acc[u].y);
@@ -165,7 +167,8 @@ __global__ void __launch_bounds__(256) k_zgemm(Dev D, ZG g) {
     __syncthreads();
   }
   if (i >= M || j >= N) return;
-  double2 v = cscale(cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3])), g.alpha);
+  double2 v = cscale(cadd(cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3])), cadd(cadd(acc[4], acc[5]), cadd(acc[6], acc[7]))),
+                     g.alpha);
   if (g.colscale >= 0) {
     const double sj = ((const double*)(sb + g.colscale))[j];
     v = sj > 0.0 ? cscale(v, 1.0 / sj) : make_double2(0.0, 0.0);

@@ -151,14 +151,17 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
     }
     __syncthreads();
     for (int j = i + threadIdx.x; j < w; j += blockDim.x) A[j * LR + i] = lcol[j];   // column i of L
-    const int rem = w - i - 1;
-    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-      const int j = i + 1 + idx / rem, k = i + 1 + idx % rem;
-      const float2 lj = lcol[j], lk = lcol[k];
-      float2 a = A[j * LR + k];
-      a.x -= lj.x * lk.x + lj.y * lk.y;            // lj * conj(lk)
-      a.y -= lj.y * lk.x - lj.x * lk.y;
-      A[j * LR + k] = a;
+    // rank-1 update of the trailing block: a warp per row (stepping by the warps), its lanes
+    // over the columns (no index division)
+    for (int j = i + 1 + warp; j < w; j += (int)(blockDim.x >> 5)) {
+      const float2 lj = lcol[j];
+      for (int k = i + 1 + lane; k < w; k += 32) {
+        const float2 lk = lcol[k];
+        float2 a = A[j * LR + k];
+        a.x -= lj.x * lk.x + lj.y * lk.y;            // lj * conj(lk)
+        a.y -= lj.y * lk.x - lj.x * lk.y;
+        A[j * LR + k] = a;
+      }
     }
     __syncthreads();
   }
@@ -286,19 +289,45 @@ __global__ void __launch_bounds__(256) k_solve_c(Dev D) {
     __syncthreads();
   }
   __shared__ double2 cs_[PRONY_MMAX];
-  if (threadIdx.x == 0) {
-    // L y = b ; L^H c = y
+  if (threadIdx.x < 32) {
+    // L y = b, then L^H c = y, column by column on one warp: lane l keeps the running residuals
+    // r_j (j = l, l + 32); each step divides one residual by the diagonal and updates the
+    // residuals of the rows that remain, so a step costs a few dependent FP64 operations instead
+    // of a dot product of growing length
+    const int lane = threadIdx.x;
+    double2 r[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) r[q] = lane + 32 * q < m ? bb[lane + 32 * q] : make_double2(0.0, 0.0);
     for (int i = 0; i < m; ++i) {
-      double2 s = bb[i];
-      for (int k = 0; k < i; ++k) s = csub(s, cmul(G[i * LD + k], cs_[k]));
-      cs_[i] = cscale(s, 1.0 / G[i * LD + i].x);
+      const int q = i >> 5;
+      double2 ri = q ? r[1] : r[0];
+      ri.x = __shfl_sync(0xffffffffu, ri.x, i & 31);
+      ri.y = __shfl_sync(0xffffffffu, ri.y, i & 31);
+      const double2 yi = cscale(ri, 1.0 / G[i * LD + i].x);
+      if (lane == (i & 31)) cs_[i] = yi;
+#pragma unroll
+      for (int qq = 0; qq < 2; ++qq) {
+        const int j = lane + 32 * qq;
+        if (j > i && j < m) r[qq] = csub(r[qq], cmul(G[j * LD + i], yi));
+      }
     }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) r[q] = lane + 32 * q < m ? cs_[lane + 32 * q] : make_double2(0.0, 0.0);
     for (int i = m - 1; i >= 0; --i) {
-      double2 s = cs_[i];
-      for (int k = i + 1; k < m; ++k) s = csub(s, cmul(cconj(G[k * LD + i]), cs_[k]));
-      cs_[i] = cscale(s, 1.0 / G[i * LD + i].x);
+      const int q = i >> 5;
+      double2 ri = q ? r[1] : r[0];
+      ri.x = __shfl_sync(0xffffffffu, ri.x, i & 31);
+      ri.y = __shfl_sync(0xffffffffu, ri.y, i & 31);
+      const double2 ci = cscale(ri, 1.0 / G[i * LD + i].x);
+      if (lane == (i & 31)) cs_[i] = ci;
+#pragma unroll
+      for (int qq = 0; qq < 2; ++qq) {
+        const int j = lane + 32 * qq;
+        if (j < i) r[qq] = csub(r[qq], cmul(cconj(G[i * LD + j]), ci));
+      }
     }
-    if (s_bad) set_status(st, ST_ERANK);
+    if (lane == 0 && s_bad) set_status(st, ST_ERANK);
   }
   __syncthreads();
   // sort (t, c) lexicographically by t (and the raw eigenvalues with them)

@@ -332,19 +332,37 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
         }
     }
   }
-  // the blocks' partial Grams (one slot of a x b each) added in block order, in FP64
+  // the blocks' partial Grams (one slot of a x b each) added in FP64 in a fixed order: eight
+  // interleaved partial sums over the slots (k mod 8), so that eight loads are in flight, then
+  // combined pairwise
   const int nblk = (p.N + chunk - 1) / chunk;
   if (red_arrive(D, pi, nblk)) {
     const float2* slots = (const float2*)red_region(D, pi);
+    const size_t ss = (size_t)a * b;
     for (int e = threadIdx.x; e < a * b; e += blockDim.x) {
-      double sx = 0.0, sy = 0.0;
-      for (int k = 0; k < nblk; ++k) {
-        const float2 v = __ldcg(slots + (size_t)k * a * b + e);
-        sx += (double)v.x;
-        sy += (double)v.y;
+      double sx[8], sy[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sx[u] = sy[u] = 0.0;
+      int k = 0;
+      for (; k + 8 <= nblk; k += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(slots + (size_t)(k + u) * ss + e);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          sx[u] += (double)v[u].x;
+          sy[u] += (double)v[u].y;
+        }
       }
+      for (int u = 0; k < nblk; ++k, ++u) {
+        const float2 v = __ldcg(slots + (size_t)k * ss + e);
+        sx[u] += (double)v.x;
+        sy[u] += (double)v.y;
+      }
+      const double tx = ((sx[0] + sx[1]) + (sx[2] + sx[3])) + ((sx[4] + sx[5]) + (sx[6] + sx[7]));
+      const double ty = ((sy[0] + sy[1]) + (sy[2] + sy[3])) + ((sy[4] + sy[5]) + (sy[6] + sy[7]));
       double2* o = &out[(e / b) * out_ld + e % b];
-      *o = make_double2(o->x + sx, o->y + sy);
+      *o = make_double2(o->x + tx, o->y + ty);
     }
   }
 }
@@ -419,22 +437,26 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
 #pragma unroll
       for (int e = 0; e < 4; ++e)      // issued before the products so that their latency overlaps them
         zv[e] = (Z && j0 + e < b) ? Z[(long long)(j0 + e) * ldz + gz] : make_float2(0.f, 0.f);
-      float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      // x m as paired FP32 FMAs on M as stored: p1 += (Re x, Re x)(Re m, Im m),
+      // p2 += (Im x, Im x)(Re m, Im m); then x m = (p1.x - p2.y, p1.y + p2.x)
+      unsigned long long p1[4] = {0ull, 0ull, 0ull, 0ull}, p2[4] = {0ull, 0ull, 0ull, 0ull};
       for (int i = 0; i < a; ++i) {
         const float2 x = Xs[i * rows + rr];
-        const float2* mrow = Ms + i * ldm + j0;
+        const unsigned long long xr = pk2(x.x, x.x), xi = pk2(x.y, x.y);
+        const unsigned long long* mrow = (const unsigned long long*)(Ms + i * ldm + j0);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float2 mm = mrow[e];
-          acc[e].x += x.x * mm.x - x.y * mm.y;
-          acc[e].y += x.x * mm.y + x.y * mm.x;
+          const unsigned long long mm = mrow[e];
+          ffma2(p1[e], xr, mm);
+          ffma2(p2[e], xi, mm);
         }
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int j = j0 + e;
         if (j >= b) break;
-        float2 v = acc[e];
+        const float2 q1 = upk2(p1[e]), q2 = upk2(p2[e]);
+        float2 v = make_float2(q1.x - q2.y, q1.y + q2.x);
         if (Z) {
           v.x = zv[e].x - v.x;
           v.y = zv[e].y - v.y;
@@ -554,10 +576,13 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
   if (!resid) {
     const int tpi = blockDim.x / m;                 // threads per term (m <= 64: at least 4)
     const int i = threadIdx.x / tpi, q = threadIdx.x % tpi;
-    double2 acc = make_double2(0.0, 0.0);
-    if (i < m)
-      for (int rr = q; rr < nrows; rr += tpi) acc = cadd(acc, cmul(power(i, rr), sample(rr)));
-    part[threadIdx.x] = acc;
+    // four interleaved partial sums (FP64 additions have a long dependent latency), fixed order
+    double2 a4[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    if (i < m) {
+      int u = 0;
+      for (int rr = q; rr < nrows; rr += tpi, u = (u + 1) & 3) a4[u] = cadd(a4[u], cmul(power(i, rr), sample(rr)));
+    }
+    part[threadIdx.x] = cadd(cadd(a4[0], a4[1]), cadd(a4[2], a4[3]));
     __syncthreads();
     double2* b = (double2*)(D.small + p.soff + D.L.rhs);
     double2* slots = (double2*)red_region(D, pi);
@@ -578,9 +603,9 @@ __global__ void __launch_bounds__(256) k_rhs(Dev D, int resid) {
     double r2 = 0.0;
     for (int rr = threadIdx.x; rr < nrows; rr += blockDim.x) {
       const double2 f = sample(rr);
-      double2 v = make_double2(-f.x, -f.y);
-      for (int i = 0; i < m; ++i) v = cadd(v, cmul(c[i], power(i, rr)));
-      r2 += cabs2(v);
+      double2 v[2] = {make_double2(-f.x, -f.y), make_double2(0.0, 0.0)};   // two chains over the terms
+      for (int i = 0; i < m; ++i) v[i & 1] = cadd(v[i & 1], cmul(c[i], power(i, rr)));
+      r2 += cabs2(cadd(v[0], v[1]));
     }
     double tot = block_sum(r2, shr);
     double* slot = (double*)red_region(D, pi);
@@ -768,7 +793,8 @@ static void gram_geometry(const Dev& D, size_t& sm, int& chunk, int& nblk) {
     }
     it = slots_for.emplace(sm, std::max(1, occ) * sms).first;
   }
-  const int per_prob = std::max(1, it->second / std::max(1, D.nprob));
+  // at most 64 blocks per problem: the last block of a problem adds every block's partial Gram
+  const int per_prob = std::max(1, std::min(64, it->second / std::max(1, D.nprob)));
   chunk = std::max(RS, (D.maxN + per_prob - 1) / per_prob);
   chunk = (chunk + RS - 1) / RS * RS;
   nblk = (D.maxN + chunk - 1) / chunk;

@@ -31,6 +31,7 @@
 #include "../../include/prony.h"
 
 #include <algorithm>
+#include <type_traits>
 #include <climits>
 #include <cstring>
 
@@ -90,11 +91,6 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t* w) {
   }
 }
 
-// byte offset of BF16 element (row, k) of a K-major tile of 64-element rows, 128-byte swizzle
-__device__ __forceinline__ uint32_t sw128(int row, int k) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 3) ^ (row & 7)) << 4) | ((k & 7) << 1)));
-}
-
 // Split an FP32 value into TF32 hi + lo (round to nearest, ties away; both exactly TF32).
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
@@ -133,9 +129,10 @@ __device__ __forceinline__ void mma_ts(bool tf32, uint32_t d, uint32_t a, uint64
 // problem is one contiguous tile in the shared-memory image of a B stage: KHALVES segments of
 // NPL planes of NT rows of 128 bytes (BF16: 64 K per row; TF32: 32 K per row and segment), the
 // 16-byte groups of row R swizzled by R mod 8 (the 128-byte swizzle of the MMA descriptor).
-// One thread writes one 16-byte group of every plane.
+// One thread writes one 16-byte group of every plane.  Row h of X is row h of the buffer, or for
+// the box buffer Y the row of I_n point h shifted by e_xshift (xshift < 0: unshifted).
 template <int KIND>
-__global__ void k_xb_prep(Dev D, int xbuf, int wsel, unsigned char* xb, long long prob_stride) {
+__global__ void k_xb_prep(Dev D, int xbuf, int xshift, int wsel, unsigned char* xb, long long prob_stride) {
   using K = TcKind<KIND>;
   constexpr int NPL = K::NPL;
   constexpr int EPG = K::TF32 ? 4 : 8;               // elements per 16-byte group
@@ -166,7 +163,8 @@ __global__ void k_xb_prep(Dev D, int xbuf, int wsel, unsigned char* xb, long lon
 #pragma unroll
     for (int e = 0; e < EPG; ++e) {
       const int h = h0 + e;
-      const float2 x = (h < p.N && j < w) ? X[(long long)j * ldx + h] : make_float2(0.f, 0.f);
+      const int hr = (xbuf == BUF_Y && h < p.N) ? map_row(h, p.n, p.d, p.n + 2, xshift) : h;
+      const float2 x = (h < p.N && j < w) ? X[(long long)j * ldx + hr] : make_float2(0.f, 0.f);
       v[e] = (row & 1) == 0 ? (im_block ? -x.y : x.x) : (im_block ? x.x : x.y);
     }
     uint32_t pw[3][4];                                 // planes x 16 bytes
@@ -197,17 +195,20 @@ __global__ void k_xb_prep(Dev D, int xbuf, int wsel, unsigned char* xb, long lon
   }
 }
 
-// Split planes of the sample grid, table a = part * NPL + plane.  BF16: each word pairs entry x
-// (low half) with entry x - 1 (high half), so the A' operand of two consecutive input points on
-// a grid line is one word; TF32: one word per entry.  One pass per solve.
+// Split planes of the sample grid, table a = part * NPL + plane (part 0: Re, 1: Im), at word
+// offset toff + a * Gd4 of the problem.  TF32: one 32-bit word per grid index x.  BF16: 16-bit
+// entries in reverse order (entry Gd4 - 1 - x holds sample x; see tc_window), in the first half of
+// the table's word range.  One pass per solve.
+__device__ __forceinline__ uint16_t bf16_bits(float a) { return (uint16_t)(pack_bf16x2(a, 0.f) & 0xFFFFu); }
 __global__ void k_split_tables(Dev D, int tf32) {
   const int pi = blockIdx.y;
   const ProbDesc& p = D.P[pi];
-  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < p.Gd4; x += gridDim.x * blockDim.x) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.Gd4; j += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const float2* F = (side ? D.gH : D.gF) + p.grid;
       uint32_t* tab = (side ? D.tabH : D.tabF) + p.toff;
+      const int x = tf32 ? j : p.Gd4 - 1 - j;
       const float2 v = x < p.Gd ? F[x] : make_float2(0.f, 0.f);
       if (tf32) {
         uint32_t wr[2], wi[2];
@@ -219,14 +220,17 @@ __global__ void k_split_tables(Dev D, int tf32) {
           tab[(long long)(2 + pl) * p.Gd4 + x] = wi[pl];
         }
       } else {
-        const float2 v1 = (x >= 1 && x - 1 < p.Gd) ? F[x - 1] : make_float2(0.f, 0.f);
-        uint32_t wr[3], wi[3];
-        split_pair<3>(v.x, v1.x, wr);
-        split_pair<3>(v.y, v1.y, wi);
+        uint16_t* t16 = (uint16_t*)tab;
+        float r[2] = {v.x, v.y};
 #pragma unroll
-        for (int pl = 0; pl < 3; ++pl) {
-          tab[(long long)pl * p.Gd4 + x] = wr[pl];
-          tab[(long long)(3 + pl) * p.Gd4 + x] = wi[pl];
+        for (int part = 0; part < 2; ++part) {
+          float rest = r[part];
+#pragma unroll
+          for (int pl = 0; pl < 3; ++pl) {                // x = x0 + x1 + x2, exact for FP32
+            const uint16_t h = bf16_bits(rest);
+            t16[2LL * (part * 3 + pl) * p.Gd4 + j] = h;
+            rest -= __uint_as_float((uint32_t)h << 16);
+          }
         }
       }
     }
@@ -238,17 +242,27 @@ struct TcParams {
   long long prob_stride;          // bytes of B' tiles per problem
   int adjoint, wsel, ybuf, y_ext;
   int ntbox;                      // B' rows reserved per plane and problem (>= every NT)
-  int win_cap;                    // window capacity (words per table, a multiple of 4)
+  int win_cap;                    // window capacity (entries per table: BF16 a multiple of 8, TF32 of 4)
   int stages;                     // B stages in shared memory (A stages: from the TMEM left by D)
   float* part;                    // split K: one partial tile (ntbox columns x 128 rows) per job
   int* cnt;                       // split K: arrivals per row tile, indexed by its first job (zero between launches)
   long long part_jobs;            // split K: jobs the workspace holds
+  // Gram mode (X^* Z of the tall blocks): A' from X (buffer, row shift, width selector), the
+  // result into the FP64 small workspace at byte offset out_off, leading dimension out_ld
+  int xbuf, xshift, xw;
+  long long out_off;
+  int out_ld;
 };
 
 // Tensor-memory layout of a CTA whose B' tile has NT rows per plane.  With the planes stacked
-// along N (NPL * NT <= 256), one MMA per A plane a multiplies A_a by B_0..B_{NPL-1-a} at once and
-// D holds one NT-column block per B plane (summed in the epilogue); otherwise every product
-// A_a B_b is its own MMA into a single NT-column block.  The A stages follow D.
+// along N (NPL * NT <= 256), one MMA per A plane a multiplies A_a by B_0..B_{NPL-1-a} at once
+// into D blocks a..NPL-1 (NT columns each), so block k accumulates the products A_a B_b with
+// a + b = k: block 0 holds the leading product A_0 B_0 alone and blocks 1.. the corrections,
+// each 2^-8 (BF16) or 2^-11 (TF32) smaller than the block before.  The FP32 accumulator rounds
+// once per MMA relative to its own magnitude, so the leading block takes one rounding per K step
+// instead of NPL, and the corrections' roundings fall below the leading block's.  The epilogue
+// adds the blocks from the smallest up.  Otherwise (NPL * NT > 256) every product A_a B_b is its
+// own MMA into a single NT-column block.  The A stages follow D.
 struct TcLayout {
   bool stacked;
   int dcols, acol0, sa;
@@ -264,25 +278,30 @@ __device__ inline TcLayout tc_layout(int NT) {
   return t;
 }
 
-// 16 accumulator columns c0..c0+15 of this thread's TMEM lane, the per-plane blocks summed.
+// 16 accumulator columns c0..c0+15 of this thread's TMEM lane, the blocks summed from the
+// smallest (the last) to the leading one.
 template <int NPL>
 __device__ __forceinline__ void tc_load_acc(uint32_t taddr, bool stacked, int NT, float* v) {
   uint32_t u[16];
-  tmem_ld_x16(taddr, u);
+  const int top = stacked ? NPL - 1 : 0;
+  tmem_ld_x16(taddr + top * NT, u);
   tmem_ld_wait();
 #pragma unroll
   for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(u[e]);
-  if (stacked) {
-    for (int b = 1; b < NPL; ++b) {
-      tmem_ld_x16(taddr + b * NT, u);
-      tmem_ld_wait();
+  for (int b = top - 1; b >= 0; --b) {
+    tmem_ld_x16(taddr + b * NT, u);
+    tmem_ld_wait();
 #pragma unroll
-      for (int e = 0; e < 16; ++e) v[e] += __uint_as_float(u[e]);
-    }
+    for (int e = 0; e < 16; ++e) v[e] += __uint_as_float(u[e]);
   }
 }
 
-template <int KIND>
+// GRAM = true: the same pipeline computes the Gram X^* Z of two tall blocks (N rows, the K
+// dimension) on the tensor cores: A' row i = conj(X[:, i]) read from HBM by the producer warps
+// ([Re x | -Im x] per K chunk, split into planes like the samples), B' = Z by k_xb_prep, one row
+// tile (i < the width of X, at most 128), K split over CTAs as for the products; the result goes
+// to the per-problem FP64 small workspace.
+template <int KIND, bool GRAM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P, int* err) {
   using K = TcKind<KIND>;
@@ -304,8 +323,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (st.done) return;
   const int w = tc_width(st, p, P.wsel);
   if (w <= 0) return;
+  const int aw = GRAM ? tc_width(st, p, P.xw) : 0;   // Gram rows: the columns of X
+  if (GRAM && (aw <= 0 || aw > TC_BM)) return;
   const int L = P.y_ext ? p.n + 2 : p.n + 1;
-  const int rows_total = P.y_ext ? p.Next : p.N;
+  const int rows_total = GRAM ? aw : P.y_ext ? p.Next : p.N;
   const int row0 = job.mt * TC_BM;
   if (row0 >= rows_total) return;
   const int nc = (p.N + 31) / 32;
@@ -323,23 +344,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     return;
   }
 
-  // window of grid indices needed by this CTA: [gk(first row) - gh(last h), gk(last row) - gh(first h)]
+  // window of grid indices needed by this CTA: [gk(first row) - gh(last h), gk(last row) - gh(first h)],
+  // as table entries [wlo, wlo + wlen)
+  constexpr int EB = K::TF32 ? 4 : 2;           // bytes per table entry
   int wlo = 0, wlen = 0;
   bool idle = nchunks == 0;                     // an empty K range (a split wider than the problem)
-  if (!idle) {
+  if (!idle && !GRAM) {
     const int last_row = min(rows_total, row0 + TC_BM) - 1;
     const int h_first = 32 * c_begin, h_last = min(p.N, 32 * c_end) - 1;
-    wlo = grid_of_row(row0, L, p) - grid_of_h(h_last, p);
-    const int whi = grid_of_row(last_row, L, p) - grid_of_h(h_first, p);
-    wlo &= ~3;                                  // 16-byte aligned start (4 words)
-    wlen = ((whi - wlo + 1) + 3) & ~3;
+    const int f_lo = grid_of_row(row0, L, p) - grid_of_h(h_last, p);
+    const int f_hi = grid_of_row(last_row, L, p) - grid_of_h(h_first, p);
+    tc_window(!K::TF32, p.Gd4, f_lo, f_hi, wlo, wlen);
     if (wlen > P.win_cap) {
       if (threadIdx.x == 0) atomicExch(err, 3);
       idle = true;
     }
   }
   if (idle && job.nks == 1) return;             // no partial to contribute
-  const uint32_t* gtab = (P.adjoint ? D.tabH : D.tabF) + p.toff;
+  // table a of the problem starts at word toff + a * Gd4 (BF16: its first half, 16-bit entries)
+  const unsigned char* gtab = (const unsigned char*)((P.adjoint ? D.tabH : D.tabF) + p.toff);
 
   // shared memory: B stages (1024-aligned), then the window of the split-plane tables.  A B stage
   // holds KHALVES x NPL x NT rows of 128 bytes: for each 128-byte K segment the planes are
@@ -350,7 +373,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t stage_bytes = (uint32_t)(K::KHALVES * NPL * P.ntbox) * 128u;
   const uint32_t half_bytes = (uint32_t)(NPL * NT) * 128u;
   unsigned char* Bs = sm;
-  uint32_t* wtab = (uint32_t*)(sm + (size_t)P.stages * stage_bytes);   // table a at wtab + a * win_cap
+  unsigned char* wtab = sm + (size_t)P.stages * stage_bytes;   // table a at byte a * win_cap * EB
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -369,7 +392,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     fence_barrier_init();
   }
   // grid offset gh of the first of each 16 input points when all 16 lie on one grid line
-  for (int idx = threadIdx.x; idx < 2 * nchunks; idx += blockDim.x) {
+  for (int idx = threadIdx.x; !GRAM && idx < 2 * nchunks; idx += blockDim.x) {
     const int h0 = 32 * (c_begin + idx / 2) + 16 * (idx & 1);
     const bool line = h0 + 15 < p.N && (h0 % (p.n + 1)) + 15 <= p.n;
     ghalf[idx] = line ? grid_of_h(h0, p) : -1;
@@ -382,13 +405,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------- bulk copies: window and B' stages
     if (lane == 0 && !idle) {
-      mbar_arrive_expect_tx(&bar_win, (uint32_t)(K::NTAB * wlen) * 4u);
+      if (!GRAM) {
+        mbar_arrive_expect_tx(&bar_win, (uint32_t)(K::NTAB * wlen * EB));
 #pragma unroll
-      for (int part = 0; part < 2; ++part)
+        for (int part = 0; part < 2; ++part)
 #pragma unroll
-        for (int pl = 0; pl < NPL; ++pl)
-          tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap, gtab + (long long)(GPL * part + pl) * p.Gd4 + wlo,
-                      (uint32_t)wlen * 4u, &bar_win);
+          for (int pl = 0; pl < NPL; ++pl)
+            tma_load_1d(wtab + (size_t)(part * NPL + pl) * P.win_cap * EB,
+                        gtab + 4LL * (GPL * part + pl) * p.Gd4 + (long long)wlo * EB, (uint32_t)(wlen * EB), &bar_win);
+      }
       const uint32_t tile_bytes = (uint32_t)K::KHALVES * half_bytes;
       const unsigned char* src0 = P.xb + P.prob_stride * job.prob + (size_t)c_begin * tile_bytes;
       int issued = 0;
@@ -407,12 +432,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!s_err)
         for (int it = max(0, issued - S); it < issued; ++it)
           if (!mbar_wait_spin(&bar_empty[it % S], (it / S) & 1, TC_SPIN)) { s_err = 1; break; }
-      if (!mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
+      if (!GRAM && !mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
     if (lane == 0 && !idle) {
-      uint32_t idesc[NPL];                        // stacked: A_a times B_0..B_{NPL-1-a}
+      uint32_t idesc[NPL];                        // stacked: A_a times B_0..B_{NPL-1-a} into D blocks a..
 #pragma unroll
       for (int a = 0; a < NPL; ++a) {
         const int n = lay.stacked ? (NPL - a) * NT : NT;
@@ -437,7 +462,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (lay.stacked) {
 #pragma unroll
             for (int a = 0; a < NPL; ++a)
-              mma_ts(K::TF32, tb, a0 + a * K::PCOLS + 8 * kk, bdk, idesc[a], (a > 0) ? 1u : first);
+              mma_ts(K::TF32, tb + (uint32_t)(a * NT), a0 + a * K::PCOLS + 8 * kk, bdk, idesc[a],
+                     (a > 0) ? 1u : first);
           } else {
 #pragma unroll
             for (int pr = 0; pr < NPROD; ++pr) {
@@ -460,9 +486,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int i = 32 * q + lane;                // row within the tile
     const int row = row0 + i;
     const bool vrow = row < rows_total;
-    const int gk = vrow ? grid_of_row(row, L, p) - wlo : 0;
+    // window entry of grid index 0 for this row: TF32 entry of grid index g is gk - g... (descending
+    // with the input point), BF16 entry is gk + g (ascending, reversed tables)
+    const int gk = (GRAM || !vrow) ? 0 : K::TF32 ? grid_of_row(row, L, p) - wlo : p.Gd4 - 1 - grid_of_row(row, L, p) - wlo;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    bool ok = idle || __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
+    bool ok = idle || GRAM || __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
     if (!ok) s_err = 1;
     constexpr int NW = K::TF32 ? 16 : 8;          // words per part and plane: 16 points
     int s = 0;
@@ -473,24 +501,80 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       {
-        const int g0 = ghalf[2 * it + hh];
+        const int g0 = GRAM ? 0 : ghalf[2 * it + hh];
         // TMEM column of (plane pl, part, point j of this half): BF16 two points per column at
         // pl * 32 + part * 16 + hh * 8 + j / 2; TF32 one point per column at pl * 64 + part * 32 + hh * 16 + j
         const uint32_t a0 = tb + lane_off + lay.acol0 + (uint32_t)s * NPL * K::PCOLS + hh * NW;
         // all table words of the chunk are loaded before the first tensor-memory store (the
         // stores are compiler barriers), so the loads overlap
         uint32_t wv[2][NPL][NW];
-        if (g0 >= 0) {
-          // the 16 points lie on one grid line: F(k - h_j) sits at window index x - j; a BF16
-          // word pairs the points (2jp, 2jp + 1) at table entry x - 2jp
+        if (GRAM) {
+          // A'(i, r) = conj(X[r, i]) for the 16 rows r of this half chunk: parts Re x and -Im x
+          int ldx = 0;
+          const float2* X = tc_buf(D, P.xbuf, p, ldx);   // sets ldx: the column offset is added after
+          X += (long long)i * ldx;
+          const int r0c = 32 * (c_begin + it) + 16 * hh;
+          const bool box = P.xbuf == BUF_Y;
+          // on one line of I_n the rows of the box buffer are consecutive too
+          const bool line = r0c + 15 < p.N && (r0c % (p.n + 1)) + 15 <= p.n;
+          const int rb = (box && line && vrow) ? map_row(r0c, p.n, p.d, p.n + 2, P.xshift) : r0c;
+          float v[2][16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int r = r0c + jj;
+            float2 x = make_float2(0.f, 0.f);
+            if (vrow && r < p.N) x = X[(!box || line) ? rb + jj : map_row(r, p.n, p.d, p.n + 2, P.xshift)];
+            v[0][jj] = x.x;
+            v[1][jj] = -x.y;
+          }
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            if (K::TF32) {
+#pragma unroll
+              for (int e = 0; e < NW; ++e) {
+                uint32_t w2[2];
+                split_tf32(v[part][e], w2);
+                wv[part][0][e] = w2[0];
+                wv[part][NPL - 1][e] = w2[1];
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < NW; ++e) {
+                uint32_t w3[3];
+                split_pair<NPL>(v[part][2 * e], v[part][2 * e + 1], w3);
+#pragma unroll
+                for (int pl = 0; pl < NPL; ++pl) wv[part][pl][e] = w3[pl];
+              }
+            }
+          }
+        } else if (g0 >= 0 && K::TF32) {
+          // the 16 points lie on one grid line: F(k - h_j) sits at window entry x - j
           const int x = vrow ? gk - g0 : 16;      // rows past the end read nothing (any in-range x)
 #pragma unroll
           for (int part = 0; part < 2; ++part)
 #pragma unroll
             for (int pl = 0; pl < NPL; ++pl) {
-              const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap + x;
+              const uint32_t* T = (const uint32_t*)(wtab + (size_t)(part * NPL + pl) * P.win_cap * EB) + x;
 #pragma unroll
-              for (int e = 0; e < NW; ++e) wv[part][pl][e] = vrow ? T[-(16 / NW) * e] : 0u;
+              for (int e = 0; e < NW; ++e) wv[part][pl][e] = vrow ? T[-e] : 0u;
+            }
+        } else if (g0 >= 0) {
+          // the 16 points lie on one grid line: point j at window entry x + j (ascending), so the
+          // word of the points (2e, 2e + 1) is the 32-bit pair at entry x + 2e -- aligned when x is
+          // even, else joined from two aligned words by a 16-bit funnel shift
+          const int x = vrow ? gk + g0 : 0;
+          const int wb = x >> 1;
+          const uint32_t sh = (uint32_t)(x & 1) << 4;
+#pragma unroll
+          for (int part = 0; part < 2; ++part)
+#pragma unroll
+            for (int pl = 0; pl < NPL; ++pl) {
+              const uint32_t* T = (const uint32_t*)(wtab + (size_t)(part * NPL + pl) * P.win_cap * EB) + wb;
+              uint32_t w[NW + 1];
+#pragma unroll
+              for (int e = 0; e <= NW; ++e) w[e] = vrow ? T[e] : 0u;
+#pragma unroll
+              for (int e = 0; e < NW; ++e) wv[part][pl][e] = __funnelshift_r(w[e], w[e + 1], sh);
             }
         } else {
           // points on several grid lines: each point from its own table entry
@@ -500,20 +584,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int g = __shfl_sync(0xffffffffu, ghl, j);
-            xs[j] = (vrow && g != INT_MIN) ? gk - g : -1;
+            xs[j] = (vrow && g != INT_MIN) ? (K::TF32 ? gk - g : gk + g) : -1;
           }
 #pragma unroll
           for (int part = 0; part < 2; ++part)
 #pragma unroll
             for (int pl = 0; pl < NPL; ++pl) {
-              const uint32_t* T = wtab + (size_t)(part * NPL + pl) * P.win_cap;
+              const unsigned char* Tb = wtab + (size_t)(part * NPL + pl) * P.win_cap * EB;
 #pragma unroll
               for (int e = 0; e < NW; ++e) {
                 if (K::TF32) {
-                  wv[part][pl][e] = xs[e] >= 0 ? T[xs[e]] : 0u;
+                  wv[part][pl][e] = xs[e] >= 0 ? ((const uint32_t*)Tb)[xs[e]] : 0u;
                 } else {
-                  const uint32_t lo = xs[2 * e] >= 0 ? (T[xs[2 * e]] & 0xFFFFu) : 0u;
-                  const uint32_t hi = xs[2 * e + 1] >= 0 ? (T[xs[2 * e + 1]] << 16) : 0u;
+                  const uint16_t* T = (const uint16_t*)Tb;
+                  const uint32_t lo = xs[2 * e] >= 0 ? (uint32_t)T[xs[2 * e]] : 0u;
+                  const uint32_t hi = xs[2 * e + 1] >= 0 ? (uint32_t)T[xs[2 * e + 1]] << 16 : 0u;
                   wv[part][pl][e] = lo | hi;
                 }
               }
@@ -538,7 +623,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool dready = idle || __all_sync(0xffffffffu, mbar_wait(&bar_d, 0, TC_SPIN));
     if (!dready) s_err = 1;
     int ldy;
-    float2* Y = tc_buf(D, P.ybuf, p, ldy);
+    float2* Y = GRAM ? nullptr : tc_buf(D, P.ybuf, p, ldy);
+    double2* G = GRAM ? (double2*)(D.small + p.soff + P.out_off) : nullptr;
+    // output entry (row, column j): Y[j][row] of the product, or Gram entry (row, j) in FP64
+    auto store = [&](int j, float re, float im) {
+      if (GRAM) G[(long long)row * P.out_ld + j] = make_double2((double)re, (double)im);
+      else Y[(long long)j * ldy + row] = make_float2(re, im);
+    };
     if (job.nks == 1) {
       if (dready && !s_err) {
         tc_fence_after();
@@ -549,7 +640,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int j = c0 / 2 + e;
-              if (j < w) Y[(long long)j * ldy + row] = make_float2(v[2 * e], v[2 * e + 1]);
+              if (j < w) store(j, v[2 * e], v[2 * e + 1]);
             }
           }
         }
@@ -581,23 +672,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       named_bar_sync(1, 32 * TC_APROD);
       if (s_last) {
         // every other CTA of the tile has stored its partial (fence before its arrival): add the
-        // partials in the order of their K ranges
+        // partials in the order of their K ranges -- in FP32 for a product (at most 16 ranges;
+        // dependent FP64 additions are slow here), in FP64 for a Gram (up to hundreds of ranges)
         __threadfence();
         const float* base = P.part + (size_t)first_job * slot;
+        using Acc = typename std::conditional<GRAM, double, float>::type;
         for (int c0 = 16 * hh; c0 < NT; c0 += 32) {
-          float v[16];
+          Acc v[16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = __ldcg(base + (size_t)(c0 + e) * TC_BM + i);
+          for (int e = 0; e < 16; ++e) v[e] = (Acc)__ldcg(base + (size_t)(c0 + e) * TC_BM + i);
           for (int k = 1; k < job.nks; ++k) {
             const float* src = base + (size_t)k * slot + (size_t)c0 * TC_BM + i;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] += __ldcg(src + (size_t)e * TC_BM);
+            for (int e = 0; e < 16; ++e) v[e] += (Acc)__ldcg(src + (size_t)e * TC_BM);
           }
           if (vrow) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int j = c0 / 2 + e;
-              if (j < w) Y[(long long)j * ldy + row] = make_float2(v[2 * e], v[2 * e + 1]);
+              if (j < w) {
+                if (GRAM) G[(long long)row * P.out_ld + j] = make_double2(v[2 * e], v[2 * e + 1]);
+                else store(j, (float)v[2 * e], (float)v[2 * e + 1]);
+              }
             }
           }
         }
@@ -623,8 +719,9 @@ int tc_planes(int kind) { return kind == PRONY_BF16X3 ? 3 : 2; }
 size_t tc_stage_bytes(int kind, int ntbox) { return (size_t)(kind == PRONY_TF32X3 ? 2 : 1) * tc_planes(kind) * ntbox * 128; }
 size_t tc_elem_bytes(int kind) { return kind == PRONY_TF32X3 ? 4 : 2; }
 
+size_t tc_entry_bytes(int kind) { return kind == PRONY_TF32X3 ? 4 : 2; }
 size_t tc_smem_bytes(int kind, int ntbox, int stages, int win_cap) {
-  return 1024 + (size_t)stages * tc_stage_bytes(kind, ntbox) + (size_t)2 * tc_planes(kind) * win_cap * 4;
+  return 1024 + (size_t)stages * tc_stage_bytes(kind, ntbox) + (size_t)2 * tc_planes(kind) * win_cap * tc_entry_bytes(kind);
 }
 
 void launch_split_tables(const Dev& D, int kind, cudaStream_t s) {
@@ -636,30 +733,32 @@ void launch_split_tables(const Dev& D, int kind, cudaStream_t s) {
 // Bytes of B' tiles reserved per problem: every chunk at the widest tile of the batch.
 long long tc_prob_stride(int kind, int ntbox, int maxnc) { return (long long)maxnc * (long long)tc_stage_bytes(kind, ntbox); }
 
-void launch_xb_prep(const Dev& D, int xbuf, int wsel, void* xb, int kind, long long prob_stride, cudaStream_t s) {
+void launch_xb_prep(const Dev& D, int xbuf, int xshift, int wsel, void* xb, int kind, long long prob_stride,
+                    cudaStream_t s) {
   note_launch();
   // items (chunk, row, 16-byte group) of the largest problem, about four per thread
   const long long items = (long long)((D.maxN + 31) / 32) * (2 * D.maxR0 + 16) * 16;
   dim3 g((unsigned)std::max<long long>(1, std::min<long long>(1024, (items + 1023) / 1024)), D.nprob);
   unsigned char* b = (unsigned char*)xb;
   switch (kind) {
-    case PRONY_BF16X3: k_xb_prep<PRONY_BF16X3><<<g, 256, 0, s>>>(D, xbuf, wsel, b, prob_stride); break;
-    case PRONY_BF16X2: k_xb_prep<PRONY_BF16X2><<<g, 256, 0, s>>>(D, xbuf, wsel, b, prob_stride); break;
-    default: k_xb_prep<PRONY_TF32X3><<<g, 256, 0, s>>>(D, xbuf, wsel, b, prob_stride); break;
+    case PRONY_BF16X3: k_xb_prep<PRONY_BF16X3><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride); break;
+    case PRONY_BF16X2: k_xb_prep<PRONY_BF16X2><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride); break;
+    default: k_xb_prep<PRONY_TF32X3><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride); break;
   }
 }
 
-template <int KIND>
+template <int KIND, bool GRAM>
 static cudaError_t launch_tc_kind(const Dev& D, const ToeplitzJob* jobs, int njobs, const TcParams& P, int* err,
                                   size_t sm, cudaStream_t s) {
   static size_t set = 0;
   if (sm > set) {
     // the attribute must cover this launch's dynamic shared memory (static + dynamic <= 227 KB)
-    cudaError_t e = cudaFuncSetAttribute(k_toeplitz_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_toeplitz_tc<KIND, GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     set = sm;
   }
-  k_toeplitz_tc<KIND><<<njobs, TC_THREADS, sm, s>>>(D, jobs, P, err);
+  k_toeplitz_tc<KIND, GRAM><<<njobs, TC_THREADS, sm, s>>>(D, jobs, P, err);
   return cudaGetLastError();
 }
 
@@ -670,12 +769,24 @@ cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs,
                                long long prob_stride, float* part, int* cnt, long long part_jobs, int* err,
                                cudaStream_t s) {
   TcParams P{(const unsigned char*)xb, prob_stride, adjoint, wsel, ybuf, y_ext, ntbox, win_cap, stages, part, cnt,
-             part_jobs};
+             part_jobs, 0, -1, 0, 0, 0};
   const size_t sm = tc_smem_bytes(kind, ntbox, stages, win_cap);
   note_launch();
   switch (kind) {
-    case PRONY_BF16X3: return launch_tc_kind<PRONY_BF16X3>(D, jobs, njobs, P, err, sm, s);
-    case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2>(D, jobs, njobs, P, err, sm, s);
-    default: return launch_tc_kind<PRONY_TF32X3>(D, jobs, njobs, P, err, sm, s);
+    case PRONY_BF16X3: return launch_tc_kind<PRONY_BF16X3, false>(D, jobs, njobs, P, err, sm, s);
+    case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2, false>(D, jobs, njobs, P, err, sm, s);
+    default: return launch_tc_kind<PRONY_TF32X3, false>(D, jobs, njobs, P, err, sm, s);
   }
+}
+
+// The Gram X^* Z of two tall blocks on the tensor cores in three BF16 planes (B' tiles of Z from
+// k_xb_prep at `xb`), one CTA per problem and K range (jobs: row tile 0).
+cudaError_t launch_gram_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int xbuf, int xshift, int xw, int zw,
+                           long long out_off, int out_ld, int ntbox, int stages, const void* xb, long long prob_stride,
+                           float* part, int* cnt, long long part_jobs, int* err, cudaStream_t s) {
+  TcParams P{(const unsigned char*)xb, prob_stride, 0, zw, 0, 0, ntbox, 0, stages, part, cnt, part_jobs,
+             xbuf, xshift, xw, out_off, out_ld};
+  const size_t sm = tc_smem_bytes(PRONY_BF16X3, ntbox, stages, 0);
+  note_launch();
+  return launch_tc_kind<PRONY_BF16X3, true>(D, jobs, njobs, P, err, sm, s);
 }

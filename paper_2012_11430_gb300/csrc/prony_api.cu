@@ -89,7 +89,7 @@ struct prony_ctx {
   // the tensor-core job list on the device: (nks, P, then n and d of every problem) it was
   // built for, and its ext / in counts (a repeated batch layout skips the rebuild and the upload)
   std::vector<int> tcjob_sig;
-  int tcjob_next = 0, tcjob_nin = 0;
+  int tcjob_next = 0, tcjob_nin = 0, tcjob_ngram = 0;
   // refinement: workspace and the CUDA graph of the last argument set
   DBuf lmws;
   struct LmKey {
@@ -145,6 +145,11 @@ struct TcConf {
   ToeplitzJob* jobs_ext = nullptr;
   ToeplitzJob* jobs_in = nullptr;
   int* err = nullptr;
+  // tall-skinny Grams on the tensor cores (three BF16 planes): one CTA per problem and K range
+  bool gram = false;
+  int nks_gram = 1, gram_stages = 2, njobs_gram = 0;
+  long long gram_stride = 0;          // bytes of the Gram's B' tiles per problem
+  ToeplitzJob* jobs_gram = nullptr;
 };
 
 struct Batch {
@@ -189,8 +194,9 @@ int h_grid_of_h(int h, const ProbDesc& p) {
   }
   return g;
 }
-// largest window (table words) over the CTAs of a problem for a K split into nks ranges
-int max_window(const ProbDesc& p, int L, int nks) {
+// largest window (table entries, as the kernel sizes it: tc_window) over the CTAs of a problem
+// for a K split into nks ranges
+int max_window(const ProbDesc& p, int L, int nks, bool bf16) {
   const int rows = ipow(L, p.d) > 0 ? (int)ipow(L, p.d) : 0;
   const int nc = (p.N + 31) / 32, cper = (nc + nks - 1) / nks;
   int mx = 0;
@@ -200,9 +206,10 @@ int max_window(const ProbDesc& p, int L, int nks) {
       int cb = ks * cper, ce = std::min(nc, cb + cper);
       if (cb >= ce) continue;
       int hf = 32 * cb, hl = std::min(p.N, 32 * ce) - 1;
-      int lo = (h_grid_of_row(r0, L, p) - h_grid_of_h(hl, p)) & ~3;
-      int hi = h_grid_of_row(last, L, p) - h_grid_of_h(hf, p);
-      mx = std::max(mx, ((hi - lo + 1) + 3) & ~3);
+      int lo = 0, len = 0;
+      tc_window(bf16, p.Gd4, h_grid_of_row(r0, L, p) - h_grid_of_h(hl, p), h_grid_of_row(last, L, p) - h_grid_of_h(hf, p),
+                lo, len);
+      mx = std::max(mx, len);
     }
   }
   return mx;
@@ -235,8 +242,9 @@ static int ensure_tcjobs(prony_ctx* ctx, size_t bytes) {
 int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
   TcConf& T = B.tc;
   std::vector<int> sig;
-  sig.reserve(2 + 2 * B.P.size());
+  sig.reserve(3 + 2 * B.P.size());
   sig.push_back(nks);
+  sig.push_back(T.gram ? T.nks_gram : 0);
   sig.push_back((int)B.P.size());
   for (const auto& p : B.P) {
     sig.push_back(p.n);
@@ -246,8 +254,10 @@ int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
   if (ctx->tcjobs.p && sig == ctx->tcjob_sig) {
     T.njobs_ext = ctx->tcjob_next;
     T.njobs_in = ctx->tcjob_nin;
+    T.njobs_gram = ctx->tcjob_ngram;
     T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
     T.jobs_in = T.jobs_ext + T.njobs_ext;
+    T.jobs_gram = T.jobs_in + T.njobs_in;
     T.nks = nks;
   } else {
     std::vector<ToeplitzJob> jobs;
@@ -263,18 +273,27 @@ int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
     T.njobs_ext = (int)jobs.size();
     add_jobs(false);
     T.njobs_in = (int)jobs.size() - T.njobs_ext;
+    // Grams: one row tile per problem, its K (the N rows of the tall blocks) in nks_gram ranges
+    for (int i = 0; T.gram && i < (int)B.P.size(); ++i) {
+      const int nk = std::min(T.nks_gram, std::max(1, (B.P[i].N + 31) / 32));
+      for (int ks = 0; ks < nk; ++ks) jobs.push_back({i, 0, ks, nk});
+    }
+    T.njobs_gram = (int)jobs.size() - T.njobs_ext - T.njobs_in;
     if ((rc = ensure_tcjobs(ctx, sizeof(ToeplitzJob) * jobs.size()))) return rc;
     CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
                        ctx->stream));
     ctx->tcjob_sig = std::move(sig);
     ctx->tcjob_next = T.njobs_ext;
     ctx->tcjob_nin = T.njobs_in;
+    ctx->tcjob_ngram = T.njobs_gram;
     T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
     T.jobs_in = T.jobs_ext + T.njobs_ext;
+    T.jobs_gram = T.jobs_in + T.njobs_in;
     T.nks = nks;
   }
-  if (nks > 1)
-    return ensure_split_ws(ctx, B, (size_t)std::max(T.njobs_ext, T.njobs_in), sizeof(float) * tc_part_floats(T.ntbox));
+  if (nks > 1 || (T.gram && T.nks_gram > 1))
+    return ensure_split_ws(ctx, B, (size_t)std::max(std::max(T.njobs_ext, T.njobs_in), T.njobs_gram),
+                           sizeof(float) * tc_part_floats(T.ntbox));
   return PRONY_OK;
 }
 
@@ -298,10 +317,17 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   if (T.ntbox > 256) return PRONY_EINVAL;
   int st_max = 4;
   while (st_max > 1 && 1024 + st_max * stage + 64 * 1024 > avail) --st_max;
-  auto win_cap_for = [&](int st) { return (int)((avail - 1024 - st * stage) / (8 * npl)) & ~3; };
-  // split K: enough CTAs to fill the GPU, and every window within the shared-memory capacity
+  // window entries per table: BF16 tables hold 2-byte entries (multiples of 8), TF32 4-byte (of 4)
+  const bool bf16 = prec != PRONY_TF32X3;
+  auto win_cap_for = [&](int st) {
+    return (int)((avail - 1024 - st * stage) / (2 * npl * (bf16 ? 2 : 4))) & (bf16 ? ~7 : ~3);
+  };
+  // split K: enough CTAs to fill the GPU, every window within the shared-memory capacity, and at
+  // most 64 K chunks per CTA: the FP32 accumulator in tensor memory takes one rounding per MMA
+  // (12 per chunk for three planes), and longer chains raise the products' rounding floor above
+  // the power iteration's default tolerance
   int nks_lo = std::max(1, std::min(16, (2 * 152 + tiles_in - 1) / std::max(1, tiles_in)));
-  nks_lo = std::max(nks_lo, (maxnc + 511) / 512);  // at most 512 K chunks per CTA
+  nks_lo = std::max(nks_lo, (maxnc + 63) / 64);
   // largest window of a problem shape (it depends on n, d and the split only), computed once per
   // shape of the batch
   std::map<std::pair<int, int>, int> shapes;          // (n, d) -> a problem of that shape
@@ -312,7 +338,7 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     auto it = wmemo.find(key);
     if (it != wmemo.end()) return it->second;
     const ProbDesc& p = B.P[i];
-    const int wl = max_window(p, ext ? p.n + 2 : p.n + 1, nks);
+    const int wl = max_window(p, ext ? p.n + 2 : p.n + 1, nks, bf16);
     wmemo.emplace(key, wl);
     return wl;
   };
@@ -351,13 +377,35 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   T.win_cap = win_cap_for(T.stages);
   T.nks_min = nks;
   T.prob_stride = tc_prob_stride(prec, T.ntbox, maxnc);
+  // Grams of the tall blocks on the tensor cores, on request only (PRONY_TC_GRAM=1): the FP32
+  // accumulator in tensor memory rounds once per MMA, and the Grams of CholeskyQR2, of Q = U^* T V
+  // and of U^* T_l V need FP32-level accuracy: with them on the tensor cores the power iteration's
+  // residual floor rises above its tolerance and C2 / C3 solves take one more iteration, which
+  // costs more than the faster Grams save.  Default: the FP32 CUDA-core kernel.  Sizing when on:
+  // enough CTAs to fill the GPU twice, at most 64 K chunks each; B stages as shared memory holds
+  // (no window), at most 4
+  {
+    const char* e = getenv("PRONY_TC_GRAM");
+    T.gram = e && atoi(e) == 1;
+    const int np = (int)B.P.size();
+    T.nks_gram = std::max(1, std::min(maxnc, (2 * 152 + np - 1) / np));
+    T.nks_gram = std::max(T.nks_gram, (maxnc + 63) / 64);       // at most 64 K chunks per CTA
+    const size_t gstage = tc_stage_bytes(PRONY_BF16X3, T.ntbox);
+    T.gram_stages = (int)std::max<size_t>(1, std::min<size_t>(4, (avail - 1024) / gstage));
+    T.gram_stride = tc_prob_stride(PRONY_BF16X3, T.ntbox, maxnc);
+  }
   // batch shape signature for the tuning cache
   T.key = std::to_string(prec) + ":" + std::to_string(B.P.size()) + ":" + std::to_string(maxw) + ":" +
           std::to_string(maxnc) + ":" + std::to_string(tiles_ext) + ":" + std::to_string(tiles_in) + ":" +
           std::to_string(nks);
   auto hit = ctx->tc_tuned.find(T.key);
   T.tuned = hit != ctx->tc_tuned.end() || getenv("PRONY_TC_TUNE") != nullptr && atoi(getenv("PRONY_TC_TUNE")) == 0;
-  const int nks0 = hit != ctx->tc_tuned.end() ? hit->second : nks;
+  int nks0 = hit != ctx->tc_tuned.end() ? hit->second : nks;
+  if (const char* e = getenv("PRONY_TC_KSPLIT")) {    // tuning override: at least this K split
+    const int v = atoi(e);
+    if (v > nks0) nks0 = std::min(v, maxnc);
+    T.tuned = true;
+  }
   int rc;
   long long twords = 64;                              // split-plane tables (+ slack for window rounding)
   for (const auto& p : B.P) twords = std::max(twords, p.toff + 6LL * p.Gd4 + 64);
@@ -365,7 +413,9 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   if ((rc = ensure(ctx->tabH, 4 * (size_t)twords))) return rc;
   B.D.tabF = (uint32_t*)ctx->tabF.p;
   B.D.tabH = (uint32_t*)ctx->tabH.p;
-  if ((rc = ensure(ctx->xb, (size_t)B.P.size() * (size_t)T.prob_stride))) return rc;
+  // B' tiles of the products and (three BF16 planes) of the Grams share one buffer
+  if ((rc = ensure(ctx->xb, (size_t)B.P.size() * (size_t)std::max(T.prob_stride, T.gram ? T.gram_stride : 0LL))))
+    return rc;
   if ((rc = ensure(ctx->tcerr, 256))) return rc;
   CK(cudaMemsetAsync(ctx->tcerr.p, 0, sizeof(int), ctx->stream));
   T.err = (int*)ctx->tcerr.p;
@@ -375,6 +425,22 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
 // One Toeplitz block product for every live problem of the batch.
 int check_tc_error(prony_ctx* ctx, const Batch& B);
 
+// The Gram X^* Z of two tall blocks (N rows) for every live problem: out (FP64, small workspace at
+// out_off, leading dimension out_ld) = sum over the rows r in I_n of conj(X[r, a]) Z[r, b]; on the
+// tensor cores when the batch uses them, else the FP32 CUDA-core kernel.
+void gram(prony_ctx* ctx, const Batch& B, const Dev& D, int xbuf, int xshift, int xw, int zbuf, int zshift, int zw,
+          long long out_off, int out_ld, cudaStream_t s) {
+  const TcConf& T = B.tc;
+  if (T.on && T.gram) {
+    launch_xb_prep(D, zbuf, zshift, zw, ctx->xb.p, PRONY_BF16X3, T.gram_stride, s);
+    cudaError_t e = launch_gram_tc(D, T.jobs_gram, T.njobs_gram, xbuf, xshift, xw, zw, out_off, out_ld, T.ntbox,
+                                   T.gram_stages, ctx->xb.p, T.gram_stride, (float*)B.part, B.cnt, B.part_jobs, T.err, s);
+    if (e != cudaSuccess && ctx->launch_err == cudaSuccess) ctx->launch_err = e;
+  } else {
+    launch_gram(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld, s);
+  }
+}
+
 void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int xbuf, int wsel, int ybuf, int prec,
                       cudaStream_t s, int adjoint = -1) {
   if (adjoint < 0) adjoint = ext ? 0 : 1;
@@ -382,7 +448,7 @@ void toeplitz_product(prony_ctx* ctx, const Batch& B, const Dev& D, int ext, int
     launch_toeplitz_fft(D, B.fft.maxpts, wsel == W_ONE ? 1 : B.maxw, adjoint, xbuf, wsel, ybuf, ext, s);
   } else if (B.tc.on) {
     const TcConf& T = B.tc;
-    launch_xb_prep(D, xbuf, wsel, ctx->xb.p, T.kind, T.prob_stride, s);
+    launch_xb_prep(D, xbuf, -1, wsel, ctx->xb.p, T.kind, T.prob_stride, s);
     cudaError_t e = launch_toeplitz_tc(D, ext ? T.jobs_ext : T.jobs_in, ext ? T.njobs_ext : T.njobs_in, adjoint,
                                        wsel, ybuf, ext, T.kind, T.ntbox, T.win_cap, T.stages, ctx->xb.p,
                                        T.prob_stride, (float*)B.part, B.cnt, B.part_jobs, T.err, s);
@@ -609,15 +675,15 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
 
 // CholeskyQR2 of the tall block in `xbuf` (width selector xw) into `outbuf`, through B1.
 // mode: QR_PLAIN / QR_DROP / QR_RANK for the first pass; the second pass is plain.
-void tall_qr(const Batch& B, int xbuf, int xw, int target, int mode, double tol, int rank_mode, int outbuf,
-             cudaStream_t s) {
+void tall_qr(prony_ctx* ctx, const Batch& B, int xbuf, int xw, int target, int mode, double tol, int rank_mode,
+             int outbuf, cudaStream_t s) {
   const Dev& D = B.D;
   launch_zero_small(D, D.L.gram, 16LL * D.L.LDR * D.L.LDR, s);
-  launch_gram(D, xbuf, -1, xw, xbuf, -1, xw, D.L.gram, D.L.LDR, s);
+  gram(ctx, B, D, xbuf, -1, xw, xbuf, -1, xw, D.L.gram, D.L.LDR, s);
   launch_chol(D, xw, target, mode, tol, rank_mode, s);
   launch_apply(D, xbuf, W_IN, W_OUT, D.L.mapm, 0, -1, BUF_B1, 0, s);
   launch_zero_small(D, D.L.gram, 16LL * D.L.LDR * D.L.LDR, s);
-  launch_gram(D, BUF_B1, -1, target, BUF_B1, -1, target, D.L.gram, D.L.LDR, s);
+  gram(ctx, B, D, BUF_B1, -1, target, BUF_B1, -1, target, D.L.gram, D.L.LDR, s);
   launch_chol(D, target, target, QR_PLAIN, 0.0, 0, s);
   launch_apply(D, BUF_B1, W_IN, W_OUT, D.L.mapm, 0, -1, outbuf, 0, s);
 }
@@ -830,7 +896,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   auto reorth = [&](int basis, int wsel) {
     for (int pass = 0; pass < 2; ++pass) {
       launch_zero_small(D, D.L.work1, 16LL * D.L.LDR * D.L.LDM, s);
-      launch_gram(D, basis, -1, wsel, BUF_B2, -1, W_ONE, D.L.work1, D.L.LDM, s);
+      gram(ctx, B, D, basis, -1, wsel, BUF_B2, -1, W_ONE, D.L.work1, D.L.LDM, s);
       launch_apply(D, basis, wsel, W_ONE, D.L.work1, 1, BUF_B2, BUF_B2, 0, s);
     }
   };
@@ -856,22 +922,22 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   // V_0 orthonormal (or the Lanczos right vectors), then Y = T V_0
   auto start = [&]() -> int {
     if (lanczos) launch_lz_finish(D, s);
-    else tall_qr(B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+    else tall_qr(ctx, B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
     return toeplitz(0, 1);
   };
   // one power iteration (Algorithm 3); dflag ends nonzero when every problem has stopped
   auto iteration = [&](int it) -> int {
     // U = qr(T V_{k-1})  (rows I_n of Y)
-    tall_qr(B, BUF_Y, W_V, W_U, QR_DROP, tol_drop, 0, BUF_U, s);
+    tall_qr(ctx, B, BUF_Y, W_V, W_U, QR_DROP, tol_drop, 0, BUF_U, s);
     // Vbar = T^* U
     if ((rc = toeplitz(it, 0))) return rc;
     // V = qr(Vbar), column pivoting and the rank test on a problem's first iteration
-    tall_qr(B, BUF_B2, W_U, W_V, QR_AUTO, tol_rank, o.rank_mode, BUF_V, s);
+    tall_qr(ctx, B, BUF_B2, W_U, W_V, QR_AUTO, tol_rank, o.rank_mode, BUF_V, s);
     // Y = T V over the box {0..n+1}^d
     if ((rc = toeplitz(it, 1))) return rc;
     // Q = U^* (T V), ||T V - U Q||_F
     launch_zero_small(D, D.L.q, 16LL * D.L.LDR * D.L.LDM, s);
-    launch_gram(D, BUF_U, -1, W_U, BUF_Y, -1, W_V, D.L.q, D.L.LDM, s);
+    gram(ctx, B, D, BUF_U, -1, W_U, BUF_Y, -1, W_V, D.L.q, D.L.LDM, s);
     launch_apply(D, BUF_U, W_U, W_V, D.L.q, 1, BUF_Y, -1, 1, s);
     CK(cudaMemsetAsync(dflag, 0xFF, sizeof(int), s));
     launch_check(D, tol_power, max_iter, dflag, s);
@@ -883,7 +949,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     // M_l = U^* Y_l  with Y_l the rows k + e_l of the last product Y = T V
     launch_zero_small(D, D.L.mproj, 16LL * D.maxD * D.L.LDR * D.L.LDM, s);
     for (int l = 0; l < D.maxD; ++l)
-      launch_gram(D, BUF_U, -1, W_U, BUF_Y, l, W_V, D.L.mproj + 16LL * l * D.L.LDR * D.L.LDM, D.L.LDM, s);
+      gram(ctx, B, D, BUF_U, -1, W_U, BUF_Y, l, W_V, D.L.mproj + 16LL * l * D.L.LDR * D.L.LDM, D.L.LDM, s);
     launch_svd_S(D, s);
     if (ro.want_S) {
       // phase-canonical basis: argmax over V V_Q, then rotate U_Q, V_Q, S_l

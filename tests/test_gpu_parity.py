@@ -5,7 +5,8 @@ Tolerances (FP32 Toeplitz products, FP64 small steps):
     floating-point dot-product bound gamma_N |a||b| plus the rounding of the FP64 samples to FP32.
   * Prony results, noise-free: torus distance of t <= 1e-6, relative 2-norm error of c <= 1e-5,
     relative Frobenius error of the S_l (phase-aligned) <= 1e-5.
-  * Noisy data: the forward error of the GPU result is at most 1.5x the oracle's, plus 1e-6 absolute.
+  * Noisy data: the forward error of the GPU result is at most 1.5x the oracle's, plus an absolute
+    floor of 10 u32 (6e-7).
 """
 import numpy as np
 import pytest
@@ -16,6 +17,7 @@ from oracle import prony_oracle as O
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
+FLOOR = 10 * U32          # absolute floor of the noisy gate
 
 
 @pytest.fixture(scope="module")
@@ -147,8 +149,8 @@ def test_solve_noisy_C2_forward_error_within_oracle(ctx):
     t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
     te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
     te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
-    assert te_g <= 1.5 * te_o + 1e-6, (te_g, te_o, res.info)
-    assert ce_g <= 1.5 * ce_o + 1e-6, (ce_g, ce_o, res.info)
+    assert te_g <= 1.5 * te_o + FLOOR, (te_g, te_o, res.info)
+    assert ce_g <= 1.5 * ce_o + FLOOR, (ce_g, ce_o, res.info)
 
 
 def test_nonfinite_input_reports_enan(ctx):
@@ -301,8 +303,8 @@ def test_solve_noisy_C2_tensor_core(ctx, prec):
     t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
     te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
     te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
-    assert te_g <= 1.5 * te_o + 1e-6, (te_g, te_o, res.info)
-    assert ce_g <= 1.5 * ce_o + 1e-6, (ce_g, ce_o, res.info)
+    assert te_g <= 1.5 * te_o + FLOOR, (te_g, te_o, res.info)
+    assert ce_g <= 1.5 * ce_o + FLOOR, (ce_g, ce_o, res.info)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -341,7 +343,7 @@ def test_precision_study_C3(ctx, c3_problem, prec):
     print(f"C3 {prec}: t error {te_g:.3e} (oracle {te_o:.3e}), c error {ce_g:.3e} (oracle {ce_o:.3e}), "
           f"iterations {res.info['power_iters']}")
     assert res.info["status"] == 0, res.info
-    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6
+    assert te_g <= 1.5 * te_o + FLOOR and ce_g <= 1.5 * ce_o + FLOOR
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -377,7 +379,7 @@ def test_raw_z_vandermonde(ctx, prec):
     t_o, c_o, info_o = O.prony(Pn.grid, Pn.d, Pn.n, Pn.m, svd="power", tol_power=1e-13, vandermonde_from="z")
     te_g, ce_g = W.match_to_truth(res.t, res.c, Pn.t, Pn.c)
     te_o, ce_o = W.match_to_truth(t_o, c_o, Pn.t, Pn.c)
-    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (te_g, te_o, ce_g, ce_o)
+    assert te_g <= 1.5 * te_o + FLOOR and ce_g <= 1.5 * ce_o + FLOOR, (te_g, te_o, ce_g, ce_o)
     assert abs(res.info["ls_resid"] - info_o["ls_resid"]) <= 1e-3 * info_o["ls_resid"]
 
 
@@ -429,7 +431,7 @@ def test_lanczos_start_noisy_C2(ctx, prec):
     t_o, c_o, _ = O.prony(P.grid, P.d, P.n, P.m, svd="power", tol_power=1e-13)
     te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
     te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
-    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (te_g, te_o, ce_g, ce_o)
+    assert te_g <= 1.5 * te_o + FLOOR and ce_g <= 1.5 * ce_o + FLOOR, (te_g, te_o, ce_g, ce_o)
 
 
 def test_lanczos_start_batched_and_rank_detect(ctx):
@@ -516,7 +518,7 @@ def test_solve_noisy_C2_fft(ctx):
     te_g, ce_g = W.match_to_truth(res.t, res.c, P.t, P.c)
     te_o, ce_o = W.match_to_truth(t_o, c_o, P.t, P.c)
     assert res.info["status"] == 0, res.info
-    assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (te_g, te_o, ce_g, ce_o)
+    assert te_g <= 1.5 * te_o + FLOOR and ce_g <= 1.5 * ce_o + FLOOR, (te_g, te_o, ce_g, ce_o)
 
 
 def test_fft_batched_uneven_and_limits(ctx):
@@ -555,16 +557,18 @@ def test_table_accuracy_noise_sweep_gpu(ctx):
     floor (eps = 1e-3) the residual matches the printed value within 20% and the t and c errors
     are of the printed order of magnitude (the bands of the oracle's pin of the same table); the
     residual scales linearly from eps = 1e-4 to 1e-3 and the errors grow with it; at
-    eps = 1e-6 the GPU stays within twice the printed residual; at eps = 1e-3 with tol = eps the
-    detected rank is 4, the failure the text after the table reports."""
+    eps = 1e-6, where perturbation and FP32 floor are of the same size, the residual stays within
+    twice the printed one plus the GPU's noise-free residual (its floor, measured here); at
+    eps = 1e-3 with tol = eps the detected rank is 4, the failure the text after the table
+    reports."""
     from paper_2012_11430_gb300 import PRONY_ERANK, default_opts
     from test_oracle_pins import _paper_noise, _table
     tab = _table()
     P = W.paper_efficiency_problem(3, 5, n=20)
     opts = default_opts(precision="bf16x3", tol_rank=3e-4)
     out = {}
-    for eps in (1e-6, 1e-4, 1e-3):
-        res = ctx.solve(_paper_noise(P, eps), 3, 20, 5, opts)
+    for eps in (0.0, 1e-6, 1e-4, 1e-3):
+        res = ctx.solve(_paper_noise(P, eps) if eps else P.grid, 3, 20, 5, opts)
         assert res.info["status"] == 0 and res.info["rank_used"] == 5, (eps, res.info)
         out[eps] = (res.info["ls_resid"],) + W.match_to_truth(res.t, res.c, P.t, P.c)
     r_p, t_p, c_p = tab["1e-3"]
@@ -576,7 +580,7 @@ def test_table_accuracy_noise_sweep_gpu(ctx):
     assert 8 < out[1e-3][0] / out[1e-4][0] < 12, (out[1e-4], out[1e-3])
     assert out[1e-3][1] / out[1e-4][1] > 4 and out[1e-3][2] / out[1e-4][2] > 3, (out[1e-4], out[1e-3])
     r6, t6, c6 = tab["1e-6"]
-    assert out[1e-6][0] < 2 * r6 and out[1e-6][1] < 1e-6, (out[1e-6], tab["1e-6"])
+    assert out[1e-6][0] < 2 * r6 + out[0.0][0] and out[1e-6][1] < 1e-6, (out[1e-6], out[0.0], tab["1e-6"])
     res = ctx.solve(_paper_noise(P, 1e-3), 3, 20, 5, default_opts(precision="bf16x3", tol_rank=1e-3),
                     allow=(PRONY_ERANK,))
     assert res.info["rank_detected"] == tab["rank_eps1e-3_tol1e-3"] == 4 and res.info["status"] == PRONY_ERANK
@@ -585,9 +589,11 @@ def test_table_accuracy_noise_sweep_gpu(ctx):
 # ------------------------------------------------------------------ full sizes, bench launch configuration
 def _full_batch_check(ctx, probs, sample, snr_db):
     """One batched call at full size (the launch configuration the bench times); the sampled
-    problems against the FP64 oracle (forward error within 1.5x + 1e-6), every problem against
-    properties that hold at any size: status OK, m terms, and a least-squares residual no worse
-    than twice the noise amplitude (a misplaced node leaves a residual of the order of |c|)."""
+    problems against the FP64 oracle, each within 1.5x its own oracle forward error + 10 u32 (the
+    oracle in spawned worker processes), every problem against properties that hold at any size:
+    status OK, m terms, and a least-squares residual no worse than twice the noise amplitude (a
+    misplaced node leaves a residual of the order of |c|)."""
+    import bench
     from paper_2012_11430_gb300 import default_opts
     outs, rc = ctx.solve_batched([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs],
                                  [p.m for p in probs], default_opts())
@@ -596,22 +602,24 @@ def _full_batch_check(ctx, probs, sample, snr_db):
     for p, r in zip(probs, outs):
         assert r.info["status"] == 0 and r.info["rank_used"] == p.m, (p.name, r.info)
         assert r.info["ls_resid"] <= 2.0 * amp, (p.name, r.info["ls_resid"], amp)
-    for i in sample:
+    sample = list(sample)
+    oerr, _, _, _ = bench.oracle_errors([probs[i] for i in sample], 4)
+    for i, (te_o, ce_o) in zip(sample, oerr):
         p, r = probs[i], outs[i]
-        t_o, c_o, _ = O.prony(p.grid, p.d, p.n, p.m, svd="power", tol_power=1e-13)
         te_g, ce_g = W.match_to_truth(r.t, r.c, p.t, p.c)
-        te_o, ce_o = W.match_to_truth(t_o, c_o, p.t, p.c)
-        assert te_g <= 1.5 * te_o + 1e-6 and ce_g <= 1.5 * ce_o + 1e-6, (p.name, te_g, te_o, ce_g, ce_o)
+        assert te_g <= 1.5 * te_o + FLOOR and ce_g <= 1.5 * ce_o + FLOOR, (p.name, te_g, te_o, ce_g, ce_o)
 
 
 def test_full_size_C4_batch(ctx):
+    """4096 uneven problems; every 8th (512) checked against its own oracle run."""
     probs = W.batch_problems(4096)
-    _full_batch_check(ctx, probs, sample=range(0, 4096, 512), snr_db=30.0)
+    _full_batch_check(ctx, probs, sample=range(0, 4096, 8), snr_db=30.0)
 
 
 def test_full_size_C2_batch152(ctx):
+    """152 C2 problems, every one checked against its own oracle run."""
     probs = [W.config_problem("C2", seed_offset=i) for i in range(152)]
-    _full_batch_check(ctx, probs, sample=(0, 151), snr_db=40.0)
+    _full_batch_check(ctx, probs, sample=range(152), snr_db=40.0)
 
 
 @pytest.mark.parametrize("env,expect", [
@@ -645,7 +653,7 @@ def test_tensor_core_sizing_overrides(ctx, monkeypatch, env, expect):
         assert b.info["status"] == 0 and b.info["rank_used"] == p.m, b.info
         te_a, ce_a = W.match_to_truth(a.t, a.c, p.t, p.c)
         te_b, ce_b = W.match_to_truth(b.t, b.c, p.t, p.c)
-        assert te_b <= 1.5 * te_a + 1e-6 and ce_b <= 1.5 * ce_a + 1e-6, (p.name, te_a, te_b, ce_a, ce_b)
+        assert te_b <= 1.5 * te_a + FLOOR and ce_b <= 1.5 * ce_a + FLOOR, (p.name, te_a, te_b, ce_a, ce_b)
 
 
 # ------------------------------------------------------------------ maximum sizes
