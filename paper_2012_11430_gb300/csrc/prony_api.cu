@@ -323,11 +323,13 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     return (int)((avail - 1024 - st * stage) / (2 * npl * (bf16 ? 2 : 4))) & (bf16 ? ~7 : ~3);
   };
   // split K: enough CTAs to fill the GPU, every window within the shared-memory capacity, and at
-  // most 64 K chunks per CTA: the FP32 accumulator in tensor memory takes one rounding per MMA
-  // (12 per chunk for three planes), and longer chains raise the products' rounding floor above
-  // the power iteration's default tolerance
+  // most 512 roundings of the leading accumulator block per CTA: the FP32 accumulator in tensor
+  // memory rounds once per MMA into it, one per K step (4 per chunk for BF16 planes, 8 for TF32),
+  // and longer chains raise the products' rounding floor above the power iteration's default
+  // tolerance.  So at most 128 K chunks per CTA for BF16 planes, 64 for TF32.
+  const int max_chunks = bf16 ? 128 : 64;
   int nks_lo = std::max(1, std::min(16, (2 * 152 + tiles_in - 1) / std::max(1, tiles_in)));
-  nks_lo = std::max(nks_lo, (maxnc + 63) / 64);
+  nks_lo = std::max(nks_lo, (maxnc + max_chunks - 1) / max_chunks);
   // largest window of a problem shape (it depends on n, d and the split only), computed once per
   // shape of the batch
   std::map<std::pair<int, int>, int> shapes;          // (n, d) -> a problem of that shape
