@@ -376,6 +376,11 @@ cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs,
 cudaError_t launch_gram_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int xbuf, int xshift, int xw, int zw,
                            long long out_off, int out_ld, int ntbox, int stages, const void* xb, long long prob_stride,
                            float* part, int* cnt, long long part_jobs, int* err, cudaStream_t s);
+// OUT = X M (as launch_apply without Z and norm) on the tensor cores, three BF16 planes; jobs: one
+// per row tile of the N rows, nks = 1; OUT is not the box buffer Y.
+cudaError_t launch_apply_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int xbuf, int xw, int outw,
+                            long long m_off, int m_double, int outbuf, int ntbox, int stages, void* xb,
+                            long long prob_stride, int* err, cudaStream_t s);
 
 // kernels_refine.cu (Levenberg-Marquardt refinement of (t, c))
 long long lm_workspace_bytes(int m, int d);

@@ -43,6 +43,7 @@ constexpr int TC_MAXSTAGE = 8;
 constexpr int TC_APROD = 8;                 // A' warps (two per TMEM lane quadrant)
 constexpr int TC_THREADS = 32 * (2 + TC_APROD);
 constexpr int TC_MAXCH = 512;               // K chunks per CTA (host splits K to stay below)
+enum TcMode { TC_PRODUCT = 0, TC_GRAM = 1, TC_APPLY = 2 };
 
 __device__ inline int tc_width(const ProbState& s, const ProbDesc& p, int sel) { return sel_width(s, p, sel); }
 
@@ -131,8 +132,13 @@ __device__ __forceinline__ void mma_ts(bool tf32, uint32_t d, uint32_t a, uint64
 // 16-byte groups of row R swizzled by R mod 8 (the 128-byte swizzle of the MMA descriptor).
 // One thread writes one 16-byte group of every plane.  Row h of X is row h of the buffer, or for
 // the box buffer Y the row of I_n point h shifted by e_xshift (xshift < 0: unshifted).
+// With m_off >= 0 the source is instead the matrix M of an X M product (TC_APPLY): "row" h is
+// row h < a of M (a = the width selected by asel), read from the problem's small workspace at
+// byte offset m_off -- complex64 with leading dimension LDR, or complex128 (m_double, rounded to
+// complex64) with leading dimension LDM.
 template <int KIND>
-__global__ void k_xb_prep(Dev D, int xbuf, int xshift, int wsel, unsigned char* xb, long long prob_stride) {
+__global__ void k_xb_prep(Dev D, int xbuf, int xshift, int wsel, unsigned char* xb, long long prob_stride,
+                          long long m_off, int m_double, int asel) {
   using K = TcKind<KIND>;
   constexpr int NPL = K::NPL;
   constexpr int EPG = K::TF32 ? 4 : 8;               // elements per 16-byte group
@@ -143,10 +149,13 @@ __global__ void k_xb_prep(Dev D, int xbuf, int xshift, int wsel, unsigned char* 
   if (s.done) return;
   const int w = tc_width(s, p, wsel);
   const int NT = ((2 * w + 15) / 16) * 16;
-  const int nc = (p.N + 31) / 32;
+  const bool msrc = m_off >= 0;
+  const int hmax = msrc ? tc_width(s, p, asel) : p.N;   // rows of the source
+  const int nc = (hmax + 31) / 32;
   const size_t tile_bytes = (size_t)K::KHALVES * NPL * NT * 128;
-  int ldx;
-  const float2* X = tc_buf(D, xbuf, p, ldx);
+  int ldx = 0;
+  const float2* X = msrc ? nullptr : tc_buf(D, xbuf, p, ldx);
+  const unsigned char* Mb = (const unsigned char*)D.small + p.soff + (msrc ? m_off : 0);
   unsigned char* out = xb + prob_stride * pi;
   const long long total = (long long)nc * NT * GPC;   // (chunk, row, group)
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
@@ -163,8 +172,20 @@ __global__ void k_xb_prep(Dev D, int xbuf, int xshift, int wsel, unsigned char* 
 #pragma unroll
     for (int e = 0; e < EPG; ++e) {
       const int h = h0 + e;
-      const int hr = (xbuf == BUF_Y && h < p.N) ? map_row(h, p.n, p.d, p.n + 2, xshift) : h;
-      const float2 x = (h < p.N && j < w) ? X[(long long)j * ldx + hr] : make_float2(0.f, 0.f);
+      float2 x = make_float2(0.f, 0.f);
+      if (h < hmax && j < w) {
+        if (msrc) {
+          if (m_double) {
+            const double2 dv = ((const double2*)Mb)[(long long)h * D.L.LDM + j];
+            x = make_float2((float)dv.x, (float)dv.y);
+          } else {
+            x = ((const float2*)Mb)[(long long)h * D.L.LDR + j];
+          }
+        } else {
+          const int hr = xbuf == BUF_Y ? map_row(h, p.n, p.d, p.n + 2, xshift) : h;
+          x = X[(long long)j * ldx + hr];
+        }
+      }
       v[e] = (row & 1) == 0 ? (im_block ? -x.y : x.x) : (im_block ? x.x : x.y);
     }
     uint32_t pw[3][4];                                 // planes x 16 bytes
@@ -296,15 +317,23 @@ __device__ __forceinline__ void tc_load_acc(uint32_t taddr, bool stacked, int NT
   }
 }
 
-// GRAM = true: the same pipeline computes the Gram X^* Z of two tall blocks (N rows, the K
-// dimension) on the tensor cores: A' row i = conj(X[:, i]) read from HBM by the producer warps
-// ([Re x | -Im x] per K chunk, split into planes like the samples), B' = Z by k_xb_prep, one row
-// tile (i < the width of X, at most 128), K split over CTAs as for the products; the result goes
-// to the per-problem FP64 small workspace.
-template <int KIND, bool GRAM>
+// MODE selects what A' is:
+//   TC_PRODUCT  the Toeplitz tiles generated from the sample window (above);
+//   TC_GRAM     the Gram X^* Z of two tall blocks (N rows, the K dimension): A' row i = conj(X[:, i])
+//               read from HBM by the producer warps ([Re x | -Im x] per K chunk, split into planes
+//               like the samples), B' = Z by k_xb_prep, one row tile (i < the width of X, at most
+//               128), K split over CTAs as for the products; the result goes to the per-problem FP64
+//               small workspace;
+//   TC_APPLY    the product OUT = X M of a tall block X (N rows, a <= 128 columns, the K dimension)
+//               and an a x b matrix M of the small workspace: A' row r = X[r, :] read from HBM
+//               ([Re x | Im x] per chunk of 32 columns), B' = M by k_xb_prep, one CTA per row tile
+//               and the whole K range (no split), OUT stored like a product.
+template <int KIND, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_toeplitz_tc(Dev D, const ToeplitzJob* jobs, TcParams P, int* err) {
   using K = TcKind<KIND>;
+  constexpr bool GRAM = MODE == TC_GRAM, APPLY = MODE == TC_APPLY;
+  constexpr bool HBMA = GRAM || APPLY;              // A' read from a tall block in HBM, no window
   constexpr int NPL = K::NPL;
   constexpr int NPROD = K::NPROD;
   constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
@@ -323,13 +352,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (st.done) return;
   const int w = tc_width(st, p, P.wsel);
   if (w <= 0) return;
-  const int aw = GRAM ? tc_width(st, p, P.xw) : 0;   // Gram rows: the columns of X
+  const int aw = HBMA ? tc_width(st, p, P.xw) : 0;   // Gram rows / X M inner dimension: the columns of X
   if (GRAM && (aw <= 0 || aw > TC_BM)) return;
   const int L = P.y_ext ? p.n + 2 : p.n + 1;
-  const int rows_total = GRAM ? aw : P.y_ext ? p.Next : p.N;
+  const int rows_total = GRAM ? aw : (P.y_ext ? p.Next : p.N);
   const int row0 = job.mt * TC_BM;
   if (row0 >= rows_total) return;
-  const int nc = (p.N + 31) / 32;
+  if (APPLY && aw <= 0) {                           // X M with an empty X: OUT = 0
+    int ldo;
+    float2* O = tc_buf(D, P.ybuf, p, ldo);
+    const int nr = min(TC_BM, rows_total - row0);
+    for (int e = threadIdx.x; e < nr * w; e += blockDim.x) O[(long long)(e / nr) * ldo + row0 + e % nr] = make_float2(0.f, 0.f);
+    return;
+  }
+  const int nc = APPLY ? (aw + 31) / 32 : (p.N + 31) / 32;
   const int cper = (nc + job.nks - 1) / job.nks;
   const int c_begin = job.ks * cper, c_end = min(nc, c_begin + cper);
   const int nchunks = max(0, c_end - c_begin);
@@ -349,7 +385,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr int EB = K::TF32 ? 4 : 2;           // bytes per table entry
   int wlo = 0, wlen = 0;
   bool idle = nchunks == 0;                     // an empty K range (a split wider than the problem)
-  if (!idle && !GRAM) {
+  if (!idle && !HBMA) {
     const int last_row = min(rows_total, row0 + TC_BM) - 1;
     const int h_first = 32 * c_begin, h_last = min(p.N, 32 * c_end) - 1;
     const int f_lo = grid_of_row(row0, L, p) - grid_of_h(h_last, p);
@@ -392,7 +428,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     fence_barrier_init();
   }
   // grid offset gh of the first of each 16 input points when all 16 lie on one grid line
-  for (int idx = threadIdx.x; !GRAM && idx < 2 * nchunks; idx += blockDim.x) {
+  for (int idx = threadIdx.x; !HBMA && idx < 2 * nchunks; idx += blockDim.x) {
     const int h0 = 32 * (c_begin + idx / 2) + 16 * (idx & 1);
     const bool line = h0 + 15 < p.N && (h0 % (p.n + 1)) + 15 <= p.n;
     ghalf[idx] = line ? grid_of_h(h0, p) : -1;
@@ -405,7 +441,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------- bulk copies: window and B' stages
     if (lane == 0 && !idle) {
-      if (!GRAM) {
+      if (!HBMA) {
         mbar_arrive_expect_tx(&bar_win, (uint32_t)(K::NTAB * wlen * EB));
 #pragma unroll
         for (int part = 0; part < 2; ++part)
@@ -432,7 +468,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!s_err)
         for (int it = max(0, issued - S); it < issued; ++it)
           if (!mbar_wait_spin(&bar_empty[it % S], (it / S) & 1, TC_SPIN)) { s_err = 1; break; }
-      if (!GRAM && !mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
+      if (!HBMA && !mbar_wait(&bar_win, 0, TC_SPIN)) s_err = 1;
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
@@ -488,11 +524,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool vrow = row < rows_total;
     // window entry of grid index 0 for this row: TF32 entry of grid index g is gk - g... (descending
     // with the input point), BF16 entry is gk + g (ascending, reversed tables)
-    const int gk = (GRAM || !vrow) ? 0 : K::TF32 ? grid_of_row(row, L, p) - wlo : p.Gd4 - 1 - grid_of_row(row, L, p) - wlo;
+    const int gk = (HBMA || !vrow) ? 0 : K::TF32 ? grid_of_row(row, L, p) - wlo : p.Gd4 - 1 - grid_of_row(row, L, p) - wlo;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    bool ok = idle || GRAM || __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
+    bool ok = idle || HBMA || __all_sync(0xffffffffu, mbar_wait(&bar_win, 0, TC_SPIN));
     if (!ok) s_err = 1;
     constexpr int NW = K::TF32 ? 16 : 8;          // words per part and plane: 16 points
+    // X M: this lane's row of X (row r of I_n; the box buffer Y holds it at its box row)
+    int ldx_a = 0;
+    const float2* xrow = nullptr;
+    if (APPLY) {
+      xrow = tc_buf(D, P.xbuf, p, ldx_a);
+      if (vrow) xrow += P.xbuf == BUF_Y ? map_row(row, p.n, p.d, p.n + 2, -1) : row;
+    }
     int s = 0;
     uint32_t ph = 0;
     for (int it = 0; ok && it < nchunks; ++it) {
@@ -501,14 +544,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       {
-        const int g0 = GRAM ? 0 : ghalf[2 * it + hh];
+        const int g0 = HBMA ? 0 : ghalf[2 * it + hh];
         // TMEM column of (plane pl, part, point j of this half): BF16 two points per column at
         // pl * 32 + part * 16 + hh * 8 + j / 2; TF32 one point per column at pl * 64 + part * 32 + hh * 16 + j
         const uint32_t a0 = tb + lane_off + lay.acol0 + (uint32_t)s * NPL * K::PCOLS + hh * NW;
         // all table words of the chunk are loaded before the first tensor-memory store (the
         // stores are compiler barriers), so the loads overlap
         uint32_t wv[2][NPL][NW];
-        if (GRAM) {
+        if (APPLY) {
+          // A'(r, i) = X[r, i] for the 16 columns i of this half chunk: parts Re x and Im x
+          const int i0 = 32 * (c_begin + it) + 16 * hh;
+          float v[2][16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const float2 x = (vrow && i0 + jj < aw) ? xrow[(long long)(i0 + jj) * ldx_a] : make_float2(0.f, 0.f);
+            v[0][jj] = x.x;
+            v[1][jj] = x.y;
+          }
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            if (K::TF32) {
+#pragma unroll
+              for (int e = 0; e < NW; ++e) {
+                uint32_t w2[2];
+                split_tf32(v[part][e], w2);
+                wv[part][0][e] = w2[0];
+                wv[part][NPL - 1][e] = w2[1];
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < NW; ++e) {
+                uint32_t w3[3];
+                split_pair<NPL>(v[part][2 * e], v[part][2 * e + 1], w3);
+#pragma unroll
+                for (int pl = 0; pl < NPL; ++pl) wv[part][pl][e] = w3[pl];
+              }
+            }
+          }
+        } else if (GRAM) {
           // A'(i, r) = conj(X[r, i]) for the 16 rows r of this half chunk: parts Re x and -Im x
           int ldx = 0;
           const float2* X = tc_buf(D, P.xbuf, p, ldx);   // sets ldx: the column offset is added after
@@ -733,32 +806,43 @@ void launch_split_tables(const Dev& D, int kind, cudaStream_t s) {
 // Bytes of B' tiles reserved per problem: every chunk at the widest tile of the batch.
 long long tc_prob_stride(int kind, int ntbox, int maxnc) { return (long long)maxnc * (long long)tc_stage_bytes(kind, ntbox); }
 
-void launch_xb_prep(const Dev& D, int xbuf, int xshift, int wsel, void* xb, int kind, long long prob_stride,
-                    cudaStream_t s) {
+static void xb_prep(const Dev& D, int xbuf, int xshift, int wsel, void* xb, int kind, long long prob_stride,
+                    long long m_off, int m_double, int asel, long long src_rows, cudaStream_t s) {
   note_launch();
   // items (chunk, row, 16-byte group) of the largest problem, about four per thread
-  const long long items = (long long)((D.maxN + 31) / 32) * (2 * D.maxR0 + 16) * 16;
+  const long long items = (long long)((src_rows + 31) / 32) * (2 * D.maxR0 + 16) * 16;
   dim3 g((unsigned)std::max<long long>(1, std::min<long long>(1024, (items + 1023) / 1024)), D.nprob);
   unsigned char* b = (unsigned char*)xb;
   switch (kind) {
-    case PRONY_BF16X3: k_xb_prep<PRONY_BF16X3><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride); break;
-    case PRONY_BF16X2: k_xb_prep<PRONY_BF16X2><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride); break;
-    default: k_xb_prep<PRONY_TF32X3><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride); break;
+    case PRONY_BF16X3:
+      k_xb_prep<PRONY_BF16X3><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride, m_off, m_double, asel);
+      break;
+    case PRONY_BF16X2:
+      k_xb_prep<PRONY_BF16X2><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride, m_off, m_double, asel);
+      break;
+    default:
+      k_xb_prep<PRONY_TF32X3><<<g, 256, 0, s>>>(D, xbuf, xshift, wsel, b, prob_stride, m_off, m_double, asel);
+      break;
   }
 }
 
-template <int KIND, bool GRAM>
+void launch_xb_prep(const Dev& D, int xbuf, int xshift, int wsel, void* xb, int kind, long long prob_stride,
+                    cudaStream_t s) {
+  xb_prep(D, xbuf, xshift, wsel, xb, kind, prob_stride, -1, 0, 0, D.maxN, s);
+}
+
+template <int KIND, int MODE>
 static cudaError_t launch_tc_kind(const Dev& D, const ToeplitzJob* jobs, int njobs, const TcParams& P, int* err,
                                   size_t sm, cudaStream_t s) {
   static size_t set = 0;
   if (sm > set) {
     // the attribute must cover this launch's dynamic shared memory (static + dynamic <= 227 KB)
     cudaError_t e =
-        cudaFuncSetAttribute(k_toeplitz_tc<KIND, GRAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_toeplitz_tc<KIND, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     set = sm;
   }
-  k_toeplitz_tc<KIND, GRAM><<<njobs, TC_THREADS, sm, s>>>(D, jobs, P, err);
+  k_toeplitz_tc<KIND, MODE><<<njobs, TC_THREADS, sm, s>>>(D, jobs, P, err);
   return cudaGetLastError();
 }
 
@@ -773,9 +857,9 @@ cudaError_t launch_toeplitz_tc(const Dev& D, const ToeplitzJob* jobs, int njobs,
   const size_t sm = tc_smem_bytes(kind, ntbox, stages, win_cap);
   note_launch();
   switch (kind) {
-    case PRONY_BF16X3: return launch_tc_kind<PRONY_BF16X3, false>(D, jobs, njobs, P, err, sm, s);
-    case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2, false>(D, jobs, njobs, P, err, sm, s);
-    default: return launch_tc_kind<PRONY_TF32X3, false>(D, jobs, njobs, P, err, sm, s);
+    case PRONY_BF16X3: return launch_tc_kind<PRONY_BF16X3, TC_PRODUCT>(D, jobs, njobs, P, err, sm, s);
+    case PRONY_BF16X2: return launch_tc_kind<PRONY_BF16X2, TC_PRODUCT>(D, jobs, njobs, P, err, sm, s);
+    default: return launch_tc_kind<PRONY_TF32X3, TC_PRODUCT>(D, jobs, njobs, P, err, sm, s);
   }
 }
 
@@ -788,5 +872,20 @@ cudaError_t launch_gram_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int
              xbuf, xshift, xw, out_off, out_ld};
   const size_t sm = tc_smem_bytes(PRONY_BF16X3, ntbox, stages, 0);
   note_launch();
-  return launch_tc_kind<PRONY_BF16X3, true>(D, jobs, njobs, P, err, sm, s);
+  return launch_tc_kind<PRONY_BF16X3, TC_GRAM>(D, jobs, njobs, P, err, sm, s);
+}
+
+// OUT = X M for every live problem on the tensor cores in three BF16 planes: B' tiles of M (small
+// workspace at m_off) by k_xb_prep, then one CTA per row tile of N rows (jobs with nks = 1).
+cudaError_t launch_apply_tc(const Dev& D, const ToeplitzJob* jobs, int njobs, int xbuf, int xw, int outw,
+                            long long m_off, int m_double, int outbuf, int ntbox, int stages, void* xb,
+                            long long prob_stride, int* err, cudaStream_t s) {
+  xb_prep(D, -1, -1, outw, xb, PRONY_BF16X3, prob_stride, m_off, m_double, xw, D.maxR0, s);
+  TcParams P{(const unsigned char*)xb, prob_stride, 0, outw, outbuf, 0, ntbox, 0, stages, nullptr, nullptr, 0,
+             xbuf, -1, xw, 0, 0};
+  // at least half the shared memory of an SM, so that one CTA holds an SM (and all of its tensor
+  // memory) at a time
+  const size_t sm = std::max<size_t>(tc_smem_bytes(PRONY_BF16X3, ntbox, stages, 0), 116 * 1024);
+  note_launch();
+  return launch_tc_kind<PRONY_BF16X3, TC_APPLY>(D, jobs, njobs, P, err, sm, s);
 }

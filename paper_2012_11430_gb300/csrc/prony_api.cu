@@ -89,7 +89,7 @@ struct prony_ctx {
   // the tensor-core job list on the device: (nks, P, then n and d of every problem) it was
   // built for, and its ext / in counts (a repeated batch layout skips the rebuild and the upload)
   std::vector<int> tcjob_sig;
-  int tcjob_next = 0, tcjob_nin = 0, tcjob_ngram = 0;
+  int tcjob_next = 0, tcjob_nin = 0, tcjob_ngram = 0, tcjob_napply = 0;
   // refinement: workspace and the CUDA graph of the last argument set
   DBuf lmws;
   struct LmKey {
@@ -150,6 +150,11 @@ struct TcConf {
   int nks_gram = 1, gram_stages = 2, njobs_gram = 0;
   long long gram_stride = 0;          // bytes of the Gram's B' tiles per problem
   ToeplitzJob* jobs_gram = nullptr;
+  // X M products of the tall blocks on the tensor cores (three BF16 planes): one CTA per row tile
+  bool apply = false;
+  int apply_stages = 2, njobs_apply = 0;
+  long long apply_stride = 0;         // bytes of the B' tiles of M per problem
+  ToeplitzJob* jobs_apply = nullptr;
 };
 
 struct Batch {
@@ -245,6 +250,7 @@ int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
   sig.reserve(3 + 2 * B.P.size());
   sig.push_back(nks);
   sig.push_back(T.gram ? T.nks_gram : 0);
+  sig.push_back(T.apply ? 1 : 0);
   sig.push_back((int)B.P.size());
   for (const auto& p : B.P) {
     sig.push_back(p.n);
@@ -255,9 +261,11 @@ int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
     T.njobs_ext = ctx->tcjob_next;
     T.njobs_in = ctx->tcjob_nin;
     T.njobs_gram = ctx->tcjob_ngram;
+    T.njobs_apply = ctx->tcjob_napply;
     T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
     T.jobs_in = T.jobs_ext + T.njobs_ext;
     T.jobs_gram = T.jobs_in + T.njobs_in;
+    T.jobs_apply = T.jobs_gram + T.njobs_gram;
     T.nks = nks;
   } else {
     std::vector<ToeplitzJob> jobs;
@@ -279,6 +287,10 @@ int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
       for (int ks = 0; ks < nk; ++ks) jobs.push_back({i, 0, ks, nk});
     }
     T.njobs_gram = (int)jobs.size() - T.njobs_ext - T.njobs_in;
+    // X M products: every row tile of the N rows, the whole inner dimension in one CTA
+    for (int i = 0; T.apply && i < (int)B.P.size(); ++i)
+      for (int mt = 0; mt < (B.P[i].N + 127) / 128; ++mt) jobs.push_back({i, mt, 0, 1});
+    T.njobs_apply = (int)jobs.size() - T.njobs_ext - T.njobs_in - T.njobs_gram;
     if ((rc = ensure_tcjobs(ctx, sizeof(ToeplitzJob) * jobs.size()))) return rc;
     CK(cudaMemcpyAsync(ctx->tcjobs.p, jobs.data(), sizeof(ToeplitzJob) * jobs.size(), cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -286,9 +298,11 @@ int tc_set_jobs(prony_ctx* ctx, Batch& B, int nks) {
     ctx->tcjob_next = T.njobs_ext;
     ctx->tcjob_nin = T.njobs_in;
     ctx->tcjob_ngram = T.njobs_gram;
+    ctx->tcjob_napply = T.njobs_apply;
     T.jobs_ext = (ToeplitzJob*)ctx->tcjobs.p;
     T.jobs_in = T.jobs_ext + T.njobs_ext;
     T.jobs_gram = T.jobs_in + T.njobs_in;
+    T.jobs_apply = T.jobs_gram + T.njobs_gram;
     T.nks = nks;
   }
   if (nks > 1 || (T.gram && T.nks_gram > 1))
@@ -396,6 +410,18 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
     T.gram_stages = (int)std::max<size_t>(1, std::min<size_t>(4, (avail - 1024) / gstage));
     T.gram_stride = tc_prob_stride(PRONY_BF16X3, T.ntbox, maxnc);
   }
+  // X M products of the tall blocks (CholeskyQR2, the final U and V) on the tensor cores in three
+  // BF16 planes, FP32-exact operands: the inner dimension is at most r0 <= 128 (four K chunks), so
+  // the FP32 accumulator takes at most 16 roundings per product and plane pair.  Off with
+  // PRONY_TC_APPLY=0 (the FP32 CUDA-core kernel).  B stages: up to one per K chunk of the widest X.
+  {
+    const char* e = getenv("PRONY_TC_APPLY");
+    T.apply = !(e && atoi(e) == 0);
+    const int maxac = (maxw + 31) / 32;
+    const size_t astage = tc_stage_bytes(PRONY_BF16X3, T.ntbox);
+    T.apply_stages = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(4, maxac), (avail - 1024) / astage));
+    T.apply_stride = tc_prob_stride(PRONY_BF16X3, T.ntbox, maxac);
+  }
   // batch shape signature for the tuning cache
   T.key = std::to_string(prec) + ":" + std::to_string(B.P.size()) + ":" + std::to_string(maxw) + ":" +
           std::to_string(maxnc) + ":" + std::to_string(tiles_ext) + ":" + std::to_string(tiles_in) + ":" +
@@ -416,7 +442,8 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   B.D.tabF = (uint32_t*)ctx->tabF.p;
   B.D.tabH = (uint32_t*)ctx->tabH.p;
   // B' tiles of the products and (three BF16 planes) of the Grams share one buffer
-  if ((rc = ensure(ctx->xb, (size_t)B.P.size() * (size_t)std::max(T.prob_stride, T.gram ? T.gram_stride : 0LL))))
+  if ((rc = ensure(ctx->xb, (size_t)B.P.size() * (size_t)std::max(std::max(T.prob_stride, T.gram ? T.gram_stride : 0LL),
+                                                                    T.apply ? T.apply_stride : 0LL))))
     return rc;
   if ((rc = ensure(ctx->tcerr, 256))) return rc;
   CK(cudaMemsetAsync(ctx->tcerr.p, 0, sizeof(int), ctx->stream));
@@ -440,6 +467,21 @@ void gram(prony_ctx* ctx, const Batch& B, const Dev& D, int xbuf, int xshift, in
     if (e != cudaSuccess && ctx->launch_err == cudaSuccess) ctx->launch_err = e;
   } else {
     launch_gram(D, xbuf, xshift, xw, zbuf, zshift, zw, out_off, out_ld, s);
+  }
+}
+
+// OUT = X M (X in xbuf, M in the small workspace) for every live problem: on the tensor cores when
+// the batch's products use them, else the FP32 CUDA-core kernel (which also serves Z - X M and the
+// residual norm).
+void apply(prony_ctx* ctx, const Batch& B, const Dev& D, int xbuf, int xw, int outw, long long m_off, int m_double,
+           int outbuf, cudaStream_t s) {
+  const TcConf& T = B.tc;
+  if (T.on && T.apply && outbuf != BUF_Y) {
+    cudaError_t e = launch_apply_tc(D, T.jobs_apply, T.njobs_apply, xbuf, xw, outw, m_off, m_double, outbuf, T.ntbox,
+                                    T.apply_stages, ctx->xb.p, T.apply_stride, T.err, s);
+    if (e != cudaSuccess && ctx->launch_err == cudaSuccess) ctx->launch_err = e;
+  } else {
+    launch_apply(D, xbuf, xw, outw, m_off, m_double, -1, outbuf, 0, s);
   }
 }
 
@@ -683,11 +725,11 @@ void tall_qr(prony_ctx* ctx, const Batch& B, int xbuf, int xw, int target, int m
   launch_zero_small(D, D.L.gram, 16LL * D.L.LDR * D.L.LDR, s);
   gram(ctx, B, D, xbuf, -1, xw, xbuf, -1, xw, D.L.gram, D.L.LDR, s);
   launch_chol(D, xw, target, mode, tol, rank_mode, s);
-  launch_apply(D, xbuf, W_IN, W_OUT, D.L.mapm, 0, -1, BUF_B1, 0, s);
+  apply(ctx, B, D, xbuf, W_IN, W_OUT, D.L.mapm, 0, BUF_B1, s);
   launch_zero_small(D, D.L.gram, 16LL * D.L.LDR * D.L.LDR, s);
   gram(ctx, B, D, BUF_B1, -1, target, BUF_B1, -1, target, D.L.gram, D.L.LDR, s);
   launch_chol(D, target, target, QR_PLAIN, 0.0, 0, s);
-  launch_apply(D, BUF_B1, W_IN, W_OUT, D.L.mapm, 0, -1, outbuf, 0, s);
+  apply(ctx, B, D, BUF_B1, W_IN, W_OUT, D.L.mapm, 0, outbuf, s);
 }
 
 struct RunOut {
@@ -955,12 +997,12 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
     launch_svd_S(D, s);
     if (ro.want_S) {
       // phase-canonical basis: argmax over V V_Q, then rotate U_Q, V_Q, S_l
-      launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);
+      apply(ctx, B, D, BUF_V, W_V, W_V, D.L.vq, 1, BUF_B1, s);
       launch_zero_small(D, D.L.argmx, 8LL * D.L.LDM, s);
       launch_argmax(D, BUF_B1, s);
       launch_canon(D, s);
-      launch_apply(D, BUF_V, W_V, W_V, D.L.vq, 1, -1, BUF_B1, 0, s);   // V_final
-      launch_apply(D, BUF_U, W_U, W_V, D.L.uq, 1, -1, BUF_B2, 0, s);   // U_final
+      apply(ctx, B, D, BUF_V, W_V, W_V, D.L.vq, 1, BUF_B1, s);   // V_final
+      apply(ctx, B, D, BUF_U, W_U, W_V, D.L.uq, 1, BUF_B2, s);   // U_final
     }
     launch_eig_t(D, o.seed, s);
     launch_zero_small(D, D.L.rhs, 16LL * D.L.LDM, s);
