@@ -249,8 +249,12 @@ typedef struct {
 /* Tuning overrides of the tensor-core products, read from the environment at every call:
  *   PRONY_TC_BSTAGES=s   exactly s B' stages in shared memory (default: the most stages, from
  *                        4 down to 2, that reach the smallest K split whose windows fit)
+ *   PRONY_TC_KSPLIT=k    a K split of at least k (no autotuning)
  *   PRONY_TC_TUNE=0      no autotuning: the smallest K split
- * They change launch configurations only, never the arithmetic beyond FP32 summation order.
+ *   PRONY_TC_APPLY=0     the X M products of the tall blocks (CholeskyQR2, the final U and V) on
+ *                        the FP32 CUDA cores instead of the tensor cores (three BF16 planes)
+ * The first three change launch configurations only, never the arithmetic beyond FP32 summation
+ * order; the fourth changes how the X M products are rounded (both are FP32-accurate).
  * For a given launch configuration every product is deterministic: split-K partial sums are
  * added in the order of their K ranges, whatever order the CTAs finish in. */
 int prony_set_profiling(prony_ctx* ctx, int enable);   /* also resets the statistics */

@@ -143,9 +143,9 @@ __global__ void k_zero_small(Dev D, long long off, long long bytes) {
 // so that the batch gives a few blocks per SM: few blocks per problem means few FP64 atomics on
 // the same output entries).
 //
-// Rows are staged RS at a time (32, or 16 / 8 for wide blocks) in two alternating shared-memory
-// buffers: each thread loads the next rows' values into registers while the current ones are
-// multiplied, then stores them.  A thread stages one row (its row index is computed once per
+// Rows are staged RS at a time in two alternating shared-memory buffers (RS = 64 down to 8: the
+// most that the staged columns of this problem leave room for): each thread loads the next rows'
+// values into registers while the current ones are multiplied, then stores them.  A thread stages one row (its row index is computed once per
 // pass) and several columns; the values are stored column-major with a row pitch of RS + 1 and
 // pre-arranged for paired FP32 FMAs (fma.rn.f32x2): x as (Re x, Re x, Im x, Im x) and z as
 // (Re z, Im z, Im z, -Re z), so that conj(x) z is two paired FMAs on (re, im) accumulators.
@@ -153,12 +153,22 @@ __global__ void k_zero_small(Dev D, long long off, long long bytes) {
 // i, j < 4, so the threads of a warp read consecutive columns (different banks) or the same one
 // (broadcast).  When there are fewer 4x4 tiles than threads, threads split the staged rows into
 // row groups whose partial sums are added in shared memory; when there are more, the tiles are
-// processed in batches (every batch re-stages the rows).  Each block adds its totals to the FP64
-// output with one atomic per entry.
+// processed in batches (every batch re-stages the rows).  Each block stores its partial Gram; the
+// last block of the problem adds the partials (FP32, a fixed order) into the FP64 output.
 constexpr int GRAM_T = 4;           // register tile (GRAM_T x GRAM_T complex accumulators)
 constexpr int GRAM_KMAX = 10;       // staged values per thread and pass: (a + b) RS <= 256 GRAM_KMAX
 
 __host__ __device__ inline int gram_rows(int LR) { return LR <= 40 ? 32 : LR <= 80 ? 16 : 8; }
+// float4 entries of one staging buffer (sized by the widest blocks of the batch, LR columns)
+__host__ __device__ inline int gram_buf_elems(int LR) { return 2 * LR * (gram_rows(LR) + 1); }
+// Rows staged per pass for a block of `cols` staged columns (float4 each) of which `loaded` are
+// read from HBM: the most (64, 32, 16, 8) that fit the buffer and the staging registers.
+__device__ inline int gram_rows_for(int cols, int loaded, int LR) {
+  const int cap = gram_buf_elems(LR);
+  int rs = 64;
+  while (rs > 8 && (cols * (rs + 1) > cap || loaded * rs > 256 * 10)) rs >>= 1;
+  return rs;
+}
 
 __device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
   unsigned long long r;
@@ -186,16 +196,18 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
   if (r_begin >= p.N || a <= 0 || b <= 0) return;
   const int r_end = min(p.N, r_begin + chunk);
   const int LR = D.L.LDR;
-  const int RS = gram_rows(LR), PR = RS + 1;
-  const size_t buf_elems = (size_t)2 * LR * PR;   // X then Z, column-major with row pitch PR
+  // X^* X (same buffer, shift and width): the rows are loaded once and only the tiles on and
+  // above the diagonal are computed, the others written as their conjugate mirrors
+  const bool sym = xbuf == zbuf && xshift == zshift && a == b;
+  // staged columns: a of X, then b of Z (for X^* X the second form of the same a columns)
+  const int ZC = a;                                // first staged column of Z
+  const int RS = gram_rows_for(a + b, sym ? a : a + b, LR), PR = RS + 1;
+  const size_t buf_elems = (size_t)gram_buf_elems(LR);   // X then Z, column-major with row pitch PR
   // [RG-1][per_batch][16] packed partial sums, over the staging buffers once the rows are done
   unsigned long long* red = (unsigned long long*)smem4;
   int ldx, ldz;
   const float2* X = buf_base(D, xbuf, p, ldx);
   const float2* Z = buf_base(D, zbuf, p, ldz);
-  // X^* X (same buffer, shift and width): the rows are loaded once and only the tiles on and
-  // above the diagonal are computed, the others written as their conjugate mirrors
-  const bool sym = xbuf == zbuf && xshift == zshift && a == b;
   const int NA = (a + GRAM_T - 1) / GRAM_T, NB = (b + GRAM_T - 1) / GRAM_T;
   const int ntile = sym ? NA * (NA + 1) / 2 : NA * NB;
   const int nthr = blockDim.x;
@@ -227,12 +239,12 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
     for (int k = 0; k < GRAM_KMAX; ++k) {
       const int col = c0 + k * cstep;
       const float2 v = held[k];
-      // X and Z regions are contiguous: Z column c sits at column LR + c of the buffer
+      // X and Z regions are contiguous: Z column c sits at column ZC + c of the buffer
       if (col < a) {
         Xs[col * PR + my_rr] = make_float4(v.x, v.x, v.y, v.y);
-        if (sym) Xs[(col + LR) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
+        if (sym) Xs[(col + ZC) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
       } else if (!sym && col < a + b) {
-        Xs[(col - a + LR) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
+        Xs[(col - a + ZC) * PR + my_rr] = make_float4(v.x, v.y, v.y, -v.x);
       }
     }
   };
@@ -255,7 +267,7 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
 #pragma unroll
     for (int i = 0; i < GRAM_T; ++i) {
       xo[i] = min(ti + NA * i, a - 1) * PR;
-      zo[i] = (min(tj + NB * i, b - 1) + LR) * PR;
+      zo[i] = (min(tj + NB * i, b - 1) + ZC) * PR;
     }
     unsigned long long acc[GRAM_T][GRAM_T];
 #pragma unroll
@@ -332,37 +344,63 @@ __global__ void __launch_bounds__(256, 2) k_gram(Dev D, int xbuf, int xshift, in
         }
     }
   }
-  // the blocks' partial Grams (one slot of a x b each) added in FP64 in a fixed order: eight
-  // interleaved partial sums over the slots (k mod 8), so that eight loads are in flight, then
-  // combined pairwise
+  // The blocks' partial Grams (one slot of a x b each) added in FP32 in a fixed order: slot k
+  // goes to the partial sum k mod 4 of its entry, and the four are combined pairwise.  Each thread
+  // takes GR entries at a time, so that 4 GR loads are in flight.  (FP32 sums of at most 64
+  // partials add less rounding than each partial already carries from its own rows; FP64
+  // additions, at a small fraction of the FP32 rate here, made this one block per problem the
+  // longest part of the launch.)
   const int nblk = (p.N + chunk - 1) / chunk;
   if (red_arrive(D, pi, nblk)) {
+    constexpr int GR = 2;
     const float2* slots = (const float2*)red_region(D, pi);
-    const size_t ss = (size_t)a * b;
-    for (int e = threadIdx.x; e < a * b; e += blockDim.x) {
-      double sx[8], sy[8];
+    const int ss = a * b;
+    for (int e0 = threadIdx.x; e0 < ss; e0 += GR * blockDim.x) {
+      float2 acc[GR][4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) sx[u] = sy[u] = 0.0;
+      for (int g = 0; g < GR; ++g)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[g][u] = make_float2(0.f, 0.f);
       int k = 0;
-      for (; k + 8 <= nblk; k += 8) {
-        float2 v[8];
+      for (; k + 4 <= nblk; k += 4) {
+        float2 v[GR][4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcg(slots + (size_t)(k + u) * ss + e);
+        for (int g = 0; g < GR; ++g)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          sx[u] += (double)v[u].x;
-          sy[u] += (double)v[u].y;
+          for (int u = 0; u < 4; ++u) {
+            const int e = e0 + g * blockDim.x;
+            v[g][u] = e < ss ? __ldcg(slots + (size_t)(k + u) * ss + e) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+        for (int g = 0; g < GR; ++g)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            acc[g][u].x += v[g][u].x;
+            acc[g][u].y += v[g][u].y;
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {                 // the last nblk mod 4 slots
+        if (k + u < nblk) {
+#pragma unroll
+          for (int g = 0; g < GR; ++g) {
+            const int e = e0 + g * blockDim.x;
+            const float2 v = e < ss ? __ldcg(slots + (size_t)(k + u) * ss + e) : make_float2(0.f, 0.f);
+            acc[g][u].x += v.x;
+            acc[g][u].y += v.y;
+          }
         }
       }
-      for (int u = 0; k < nblk; ++k, ++u) {
-        const float2 v = __ldcg(slots + (size_t)k * ss + e);
-        sx[u] += (double)v.x;
-        sy[u] += (double)v.y;
+#pragma unroll
+      for (int g = 0; g < GR; ++g) {
+        const int e = e0 + g * blockDim.x;
+        if (e < ss) {
+          const float tx = (acc[g][0].x + acc[g][1].x) + (acc[g][2].x + acc[g][3].x);
+          const float ty = (acc[g][0].y + acc[g][1].y) + (acc[g][2].y + acc[g][3].y);
+          double2* o = &out[(e / b) * out_ld + e % b];
+          *o = make_double2(o->x + (double)tx, o->y + (double)ty);
+        }
       }
-      const double tx = ((sx[0] + sx[1]) + (sx[2] + sx[3])) + ((sx[4] + sx[5]) + (sx[6] + sx[7]));
-      const double ty = ((sy[0] + sy[1]) + (sy[2] + sy[3])) + ((sy[4] + sy[5]) + (sy[6] + sy[7]));
-      double2* o = &out[(e / b) * out_ld + e % b];
-      *o = make_double2(o->x + tx, o->y + ty);
     }
   }
 }
@@ -428,7 +466,8 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
   int ldz = 0, ldo = 0;
   const float2* Z = zbuf >= 0 ? buf_base(D, zbuf, p, ldz) : nullptr;
   float2* O = norm_only ? nullptr : buf_base(D, outbuf, p, ldo);
-  double nrm = 0.0;
+  // squares of a row summed in FP32 (the entries are FP32 values; b <= 128 terms), blocks in FP64
+  float nrm = 0.f;
   if (r < p.N) {
     const int gz = Z ? buf_row(zbuf, p, r, -1) : 0;
     const int go = O ? buf_row(outbuf, p, r, -1) : 0;
@@ -461,20 +500,22 @@ __global__ void __launch_bounds__(256) k_apply(Dev D, int xbuf, int xw, int outw
           v.x = zv[e].x - v.x;
           v.y = zv[e].y - v.y;
         }
-        if (norm_only) nrm += (double)v.x * v.x + (double)v.y * v.y;
+        if (norm_only) nrm = fmaf(v.x, v.x, fmaf(v.y, v.y, nrm));
         else O[(long long)j * ldo + go] = v;
       }
     }
   }
   if (norm_only) {
-    double t = block_sum(nrm, shr);
+    double t = block_sum((double)nrm, shr);
     double* slot = (double*)red_region(D, pi);
     if (threadIdx.x == 0 && ws_ok(D, 8LL * (blockIdx.x + 1) <= D.red_stride, 13)) slot[blockIdx.x] = t;
     const int nblk = (p.N + rows - 1) / rows;
-    if (red_arrive(D, pi, nblk) && threadIdx.x == 0) {
+    if (red_arrive(D, pi, nblk)) {
+      // the block sums in a fixed order: thread i adds slots i, i + 256, ..., then a block sum
       double r2 = 0.0;
-      for (int k = 0; k < nblk; ++k) r2 += __ldcg(slot + k);
-      s.resid2 = r2;
+      for (int k = threadIdx.x; k < nblk; k += blockDim.x) r2 += __ldcg(slot + k);
+      r2 = block_sum(r2, shr);
+      if (threadIdx.x == 0) s.resid2 = r2;
     }
   }
 }
