@@ -86,24 +86,26 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   int limit = w;  // columns that may be accepted (never more than m after the rank step)
   if (mode == QR_RANK) limit = min(w, p.m);
   for (int i = 0; i < w; ++i) {
-    if (warp == 0) {                    // pivot search and trailing trace
+    if (warp == 0) {                    // pivot search and trailing trace (no search without pivoting)
       float best = -1.f, tr = 0.f;
       int bi = i;
-      for (int j = i + lane; j < w; j += 32) {
-        const float dd = A[j * LR + j].x;
-        tr += fmaxf(dd, 0.f);
-        if (dd > best) {
-          best = dd;
-          bi = j;
+      if (mode != QR_PLAIN) {
+        for (int j = i + lane; j < w; j += 32) {
+          const float dd = A[j * LR + j].x;
+          tr += fmaxf(dd, 0.f);
+          if (dd > best) {
+            best = dd;
+            bi = j;
+          }
         }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        tr += __shfl_xor_sync(0xffffffffu, tr, o);
-        const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (b2 > best || (b2 == best && i2 < bi)) {
-          best = b2;
-          bi = i2;
+        for (int o = 16; o > 0; o >>= 1) {
+          tr += __shfl_xor_sync(0xffffffffu, tr, o);
+          const float b2 = __shfl_xor_sync(0xffffffffu, best, o);
+          const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (b2 > best || (b2 == best && i2 < bi)) {
+            best = b2;
+            bi = i2;
+          }
         }
       }
       if (lane == 0) {
@@ -155,12 +157,16 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
     // over the columns (no index division)
     for (int j = i + 1 + warp; j < w; j += (int)(blockDim.x >> 5)) {
       const float2 lj = lcol[j];
-      for (int k = i + 1 + lane; k < w; k += 32) {
-        const float2 lk = lcol[k];
-        float2 a = A[j * LR + k];
-        a.x -= lj.x * lk.x + lj.y * lk.y;            // lj * conj(lk)
-        a.y -= lj.y * lk.x - lj.x * lk.y;
-        A[j * LR + k] = a;
+#pragma unroll
+      for (int q = 0; q < PRONY_RMAX / 32; ++q) {      // unrolled: the row's loads are issued together
+        const int k = i + 1 + lane + 32 * q;
+        if (k < w) {
+          const float2 lk = lcol[k];
+          float2 a = A[j * LR + k];
+          a.x -= lj.x * lk.x + lj.y * lk.y;          // lj * conj(lk)
+          a.y -= lj.y * lk.x - lj.x * lk.y;
+          A[j * LR + k] = a;
+        }
       }
     }
     __syncthreads();
@@ -172,6 +178,12 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
   // spread over the lanes of one warp (a = lane + 32 q).
   float2* M = (float2*)(D.small + p.soff + D.L.mapm);
   const int nwarp = blockDim.x >> 5;
+  // reciprocals of the diagonal once (each column's substitution would otherwise divide at every
+  // step of its dependent chain)
+  __shared__ float rinv[PRONY_RMAX];
+  for (int k = threadIdx.x; k < rho; k += blockDim.x) rinv[k] = 1.f / A[k * LR + k].x;
+  __syncthreads();
+  const int nq = (rho + 31) >> 5;
   for (int b = warp; b < rho; b += nwarp) {
     float2 sv[PRONY_RMAX / 32];
 #pragma unroll
@@ -182,10 +194,11 @@ __global__ void __launch_bounds__(256) k_chol(Dev D, int wsel, int target, int m
 #pragma unroll
       for (int q = 0; q < PRONY_RMAX / 32; ++q)
         if (q == kq) mine = sv[q];
-      const float rkk = A[k * LR + k].x;
-      float2 xk = make_float2(__shfl_sync(0xffffffffu, mine.x, ko) / rkk, __shfl_sync(0xffffffffu, mine.y, ko) / rkk);
+      const float rk = rinv[k];
+      const float2 xk = make_float2(__shfl_sync(0xffffffffu, mine.x, ko) * rk, __shfl_sync(0xffffffffu, mine.y, ko) * rk);
 #pragma unroll
       for (int q = 0; q < PRONY_RMAX / 32; ++q) {
+        if (q >= nq) break;
         const int a = lane + 32 * q;
         if (a == k) sv[q] = xk;
         else if (a < k) {

@@ -414,9 +414,12 @@ int setup_tc(prony_ctx* ctx, Batch& B, int prec, int maxw) {
   // BF16 planes, FP32-exact operands: the inner dimension is at most r0 <= 128 (four K chunks), so
   // the FP32 accumulator takes at most 16 roundings per product and plane pair.  Off with
   // PRONY_TC_APPLY=0 (the FP32 CUDA-core kernel).  B stages: up to one per K chunk of the widest X.
+  // Batches whose blocks are all narrower than 32 columns keep the CUDA-core kernel: there a CTA's
+  // fixed costs (tensor memory, barriers, an SM of its own) outweigh its one K chunk of MMAs (the
+  // 4096 small problems of C4: 6.8 ms of tensor-core X M per step against 2.4 ms on the FP32 pipe).
   {
     const char* e = getenv("PRONY_TC_APPLY");
-    T.apply = !(e && atoi(e) == 0);
+    T.apply = !(e && atoi(e) == 0) && maxw >= 32;
     const int maxac = (maxw + 31) / 32;
     const size_t astage = tc_stage_bytes(PRONY_BF16X3, T.ntbox);
     T.apply_stages = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(4, maxac), (avail - 1024) / astage));

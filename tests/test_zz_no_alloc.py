@@ -7,6 +7,8 @@ array shared by all calls, so two calls in a row must each give the right answer
 
 This file is collected last on purpose: a failure here leaves every other test run.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -116,11 +118,13 @@ def test_static_call_leaves_device_memory_unchanged(lib):
     stream = torch.cuda.current_stream()
     lib.toeplitz_mm_static(g_dev, d, n, X_dev, n + 2, 0, Y_dev, stream.cuda_stream)   # warm-up
     torch.cuda.synchronize()
+    gc.collect()                       # tensors of earlier tests must not be freed in between
     free0, _ = torch.cuda.mem_get_info()
     alloc0 = torch.cuda.memory_allocated()
     for _ in range(3):
         lib.toeplitz_mm_static(g_dev, d, n, X_dev, n + 2, 0, Y_dev, stream.cuda_stream)
     torch.cuda.synchronize()
+    gc.collect()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
     assert torch.cuda.memory_allocated() == alloc0
