@@ -283,6 +283,14 @@ __device__ inline float centred_phase(const uint64_t* T, const int* k, int d) {
 // Every kernel launch of the library goes through a launcher that calls note_launch()
 // (a process-wide counter, read with prony_get_stats).
 void note_launch();
+// Blocks per problem of a grid-stride kernel over every problem of a batch: `want` (sized for the
+// largest problem), fewer for large batches, so that a launch holds at most ~16k blocks (with
+// thousands of small problems, most blocks of a larger grid start, find no work and retire).
+inline int blocks_per_problem(long long want, int nprob) {
+  const long long cap = 16384LL / (nprob > 0 ? nprob : 1);
+  const long long b = want < cap ? want : cap;
+  return (int)(b > 1 ? b : 1);
+}
 // Message returned by prony_last_error() on this host thread.
 void set_last_error(const char* msg);
 

@@ -786,19 +786,19 @@ inline int blocks_for(long long n, int per) { return (int)std::min<long long>((n
 void launch_prep(const Dev& D, cudaStream_t s) {
   note_launch();
   k_state_init<<<(D.nprob + 127) / 128, 128, 0, s>>>(D);
-  dim3 g(std::max(1, std::min((D.maxGd + 255) / 256, 64)), D.nprob);
+  dim3 g(blocks_per_problem(std::min((D.maxGd + 255) / 256, 64), D.nprob), D.nprob);
   note_launch();
   k_prep<<<g, 256, 0, s>>>(D);
 }
 
 void launch_init_v0(const Dev& D, unsigned long long seed, cudaStream_t s) {
-  dim3 g(std::max(1, std::min((D.maxN + 255) / 256, 256)), D.nprob);
+  dim3 g(blocks_per_problem(std::min((D.maxN + 255) / 256, 256), D.nprob), D.nprob);
   note_launch();
   k_init_v0<<<g, 256, 0, s>>>(D, seed);
 }
 
 void launch_zero_small(const Dev& D, long long off, long long bytes, cudaStream_t s) {
-  dim3 g(std::max<int>(1, std::min<int>((int)((bytes / 4 + 255) / 256), 32)), D.nprob);
+  dim3 g(blocks_per_problem(std::min<long long>((bytes / 4 + 255) / 256, 32), D.nprob), D.nprob);
   note_launch();
   k_zero_small<<<g, 256, 0, s>>>(D, off, bytes);
 }

@@ -808,7 +808,7 @@ size_t tc_smem_bytes(int kind, int ntbox, int stages, int win_cap) {
 
 void launch_split_tables(const Dev& D, int kind, cudaStream_t s) {
   note_launch();
-  dim3 g(std::max(1, std::min((D.maxGd + 3) / 4 / 256 + 1, 64)), D.nprob);
+  dim3 g(blocks_per_problem(std::min((D.maxGd + 3) / 4 / 256 + 1, 64), D.nprob), D.nprob);
   k_split_tables<<<g, 256, 0, s>>>(D, kind == PRONY_TF32X3 ? 1 : 0);
 }
 
@@ -820,7 +820,7 @@ static void xb_prep(const Dev& D, int xbuf, int xshift, int wsel, void* xb, int 
   note_launch();
   // items (chunk, row, 16-byte group) of the largest problem, about four per thread
   const long long items = (long long)((src_rows + 31) / 32) * (2 * D.maxR0 + 16) * 16;
-  dim3 g((unsigned)std::max<long long>(1, std::min<long long>(1024, (items + 1023) / 1024)), D.nprob);
+  dim3 g(blocks_per_problem(std::min<long long>(1024, (items + 1023) / 1024), D.nprob), D.nprob);
   unsigned char* b = (unsigned char*)xb;
   switch (kind) {
     case PRONY_BF16X3:

@@ -752,7 +752,11 @@ std::string loop_graph_key(const Batch& B, const int* dflag, int cap, const doub
                           T.njobs_in, (long long)(size_t)T.jobs_ext, (long long)(size_t)T.jobs_in,
                           (long long)(size_t)T.err, B.fft.on, B.fft.lz, B.fft.maxpts, B.njobs_ext, B.njobs_in, B.nks,
                           B.maxw, (long long)(size_t)B.jobs_ext, (long long)(size_t)B.jobs_in,
-                          (long long)(size_t)dflag, cap};
+                          (long long)(size_t)dflag, cap,
+                          // the Gram and X M modes of the tensor-core pipeline (environment switches)
+                          T.gram, T.nks_gram, T.gram_stages, T.njobs_gram, T.gram_stride,
+                          (long long)(size_t)T.jobs_gram, T.apply, T.apply_stages, T.njobs_apply,
+                          T.apply_stride, (long long)(size_t)T.jobs_apply};
   put(tc, sizeof(tc));
   put(params, sizeof(double) * nparams);
   return k;

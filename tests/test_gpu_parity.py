@@ -624,7 +624,7 @@ def test_full_size_C2_batch152(ctx):
 
 @pytest.mark.parametrize("env,expect", [
     ({"PRONY_TC_BSTAGES": "4"}, {"tc_bstages": 4}), ({"PRONY_TC_BSTAGES": "2"}, {"tc_bstages": 2}),
-    ({"PRONY_TC_TUNE": "0"}, {}),
+    ({"PRONY_TC_TUNE": "0"}, {}), ({"PRONY_TC_APPLY": "0"}, {}),
 ])
 def test_tensor_core_sizing_overrides(ctx, monkeypatch, env, expect):
     """Every launch configuration of the tensor-core products (B stages, K split, with or without
@@ -852,6 +852,36 @@ def test_solve_bit_identical_repeats(ctx, prec):
     for p, x, y in zip(probs, a, b):
         assert x.info == y.info, (p.name, x.info, y.info)
         assert np.array_equal(x.t, y.t) and np.array_equal(x.c, y.c), p.name
+
+
+def test_x_m_product_switch_rebuilds_the_solve_graph(ctx, monkeypatch):
+    """The X M products of CholeskyQR2 run on the tensor cores for 40- and 80-column blocks
+    (C2 and C3 shapes) and on the FP32 CUDA cores with PRONY_TC_APPLY=0.  Both reach the same
+    forward error, and switching between them between two graph-launched solves of the same layout
+    takes effect: the graph replayed afterwards gives exactly what the host-driven launches of
+    the same mode give."""
+    from paper_2012_11430_gb300 import default_opts
+    probs = [W.config_problem("C2", seed_offset=i) for i in range(3)] + [W.config_problem("C3")]
+    args = ([p.grid for p in probs], [p.d for p in probs], [p.n for p in probs], [p.m for p in probs],
+            default_opts(precision="bf16x3"))
+    ctx.solve_batched(*args)
+    tc, rc = ctx.solve_batched(*args)              # graph replay, tensor-core X M
+    assert rc == 0
+    with monkeypatch.context() as mp:
+        mp.setenv("PRONY_TC_APPLY", "0")
+        simt, rc_s = ctx.solve_batched(*args)      # same layout: the graph must be rebuilt
+        ctx.set_profiling(True)
+        try:
+            simt_host, rc_h = ctx.solve_batched(*args)
+        finally:
+            ctx.set_profiling(False)
+    assert rc_s == rc_h == 0
+    for p, a, b, h in zip(probs, tc, simt, simt_host):
+        assert np.array_equal(b.t, h.t) and np.array_equal(b.c, h.c), p.name
+        te_a, ce_a = W.match_to_truth(a.t, a.c, p.t, p.c)
+        te_b, ce_b = W.match_to_truth(b.t, b.c, p.t, p.c)
+        assert te_a <= 1.5 * te_b + FLOOR and ce_a <= 1.5 * ce_b + FLOOR, (p.name, te_a, te_b, ce_a, ce_b)
+        assert te_b <= 1.5 * te_a + FLOOR and ce_b <= 1.5 * ce_a + FLOOR, (p.name, te_a, te_b, ce_a, ce_b)
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
