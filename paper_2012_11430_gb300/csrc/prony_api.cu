@@ -722,6 +722,17 @@ int setup_batch(prony_ctx* ctx, const std::vector<HostProb>& hp, const prony_opt
 
 // CholeskyQR2 of the tall block in `xbuf` (width selector xw) into `outbuf`, through B1.
 // mode: QR_PLAIN / QR_DROP / QR_RANK for the first pass; the second pass is plain.
+// One pass only (plain CholeskyQR, in place) for a well-conditioned block such as the Gaussian
+// start block V_0 (condition ~ (sqrt N + sqrt r0) / (sqrt N - sqrt r0), so its columns come out
+// orthonormal to a few u32 after one pass).
+void tall_qr1(prony_ctx* ctx, const Batch& B, int xbuf, int xw, int target, cudaStream_t s) {
+  const Dev& D = B.D;
+  launch_zero_small(D, D.L.gram, 16LL * D.L.LDR * D.L.LDR, s);
+  gram(ctx, B, D, xbuf, -1, xw, xbuf, -1, xw, D.L.gram, D.L.LDR, s);
+  launch_chol(D, xw, target, QR_PLAIN, 0.0, 0, s);
+  apply(ctx, B, D, xbuf, W_IN, W_OUT, D.L.mapm, 0, xbuf, s);
+}
+
 void tall_qr(prony_ctx* ctx, const Batch& B, int xbuf, int xw, int target, int mode, double tol, int rank_mode,
              int outbuf, cudaStream_t s) {
   const Dev& D = B.D;
@@ -973,7 +984,7 @@ int run_batch(prony_ctx* ctx, Batch& B, const prony_opts& o, const RunOut& ro) {
   // V_0 orthonormal (or the Lanczos right vectors), then Y = T V_0
   auto start = [&]() -> int {
     if (lanczos) launch_lz_finish(D, s);
-    else tall_qr(ctx, B, BUF_V, W_R0, W_V, QR_PLAIN, 0.0, 0, BUF_V, s);
+    else tall_qr1(ctx, B, BUF_V, W_R0, W_V, s);
     return toeplitz(0, 1);
   };
   // one power iteration (Algorithm 3); dflag ends nonzero when every problem has stopped
