@@ -78,6 +78,25 @@ def measured_peaks() -> dict:
     return {"bf16": 1900.0, "src": "of fallback (1.9 PFLOP/s bf16 burst)"}
 
 
+def committed_counters(config: str, precision: str):
+    """ncu counters of the current product kernel committed in profiles/traffic.txt (lines
+    `toeplitz <config> <precision> <DRAM bytes per launch>` and `tensor_pipe <config> <precision>
+    <% of active cycles, time-weighted over a solve's products>`): (traffic, pipe) or None."""
+    traffic = pipe = None
+    tf = os.path.join(ROOT, "profiles", "traffic.txt")
+    if os.path.exists(tf):
+        for line in open(tf):
+            parts = line.split()
+            if len(parts) == 4 and parts[1] == config and parts[2] == precision:
+                if parts[0] == "toeplitz":
+                    traffic = float(parts[3])
+                elif parts[0] == "tensor_pipe":
+                    pipe = {"value": float(parts[3]), "unit": "% of active cycles",
+                            "source": "ncu sm__pipe_tensor_cycles_active, time-weighted over the products of a "
+                                      "solve (profiles/toeplitz_tc_C3_batch8_bf16x3.md)"}
+    return traffic, pipe
+
+
 def roofline(prec, achieved, traffic, launches, stats, total_ms) -> dict:
     """Toeplitz block products.  `achieved` counts useful flops (8 per complex multiply-add);
     split BF16 runs `SPLIT_PRODUCTS` tensor-core products per useful product, so its peak is
@@ -651,13 +670,7 @@ def main():
                                                    "c_max": max(e[1] for e in errs[:count])}}
     launches = stats["toeplitz_launches"]
     achieved = stats["toeplitz_flops"] / (stats["toeplitz_ms"] / 1e3) / 1e12 if stats["toeplitz_ms"] > 0 else 0.0
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.txt")
-    if os.path.exists(tf):
-        for line in open(tf):
-            parts = line.split()
-            if len(parts) == 4 and parts[0] == "toeplitz" and parts[1] == args.config and parts[2] == args.precision:
-                traffic = float(parts[3])
+    traffic, pipe = committed_counters(args.config, args.precision)
     oracle_ratio = None
     if gate is not None and noisy:
         oracle_ratio = {"t_max": max(te / max(1e-300, (g[0] - GATE_FLOOR) / 1.5) for (te, _), g in zip(errs, gate)),
@@ -698,6 +711,7 @@ def main():
                    "errors_rank0": {"t_max": max(e[0] for e in errs), "c_max": max(e[1] for e in errs)},
                    "errors_over_oracle": oracle_ratio},
         "roofline": {**roofline(args.precision, achieved, traffic, launches, stats, prof_ms),
+                     "tensor_pipe_active_ncu": pipe,
                      "measured_in": f"{prof_steps} profiled steps after the timed region (events around each "
                                     f"product launch on the context stream)"},
         "cpu_baseline": cpu,

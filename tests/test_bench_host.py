@@ -52,6 +52,9 @@ def test_committed_traffic_figure_is_read(bench):
             entries[tuple(parts[:3])] = float(parts[3])
     # the bench's default workload (C3) at its default arithmetic: traffic of the current kernel
     assert entries[("toeplitz", "C3", "bf16x3")] > 0
+    traffic, pipe = bench.committed_counters("C3", "bf16x3")
+    assert traffic == entries[("toeplitz", "C3", "bf16x3")]
+    assert pipe is not None and 0 < pipe["value"] <= 100
 
 
 def test_gate_is_per_problem(bench):
